@@ -1,0 +1,183 @@
+/*
+ * glasma.h - C ABI of the GB300 (sm_103a) library for the data-parallel hot path
+ * of arXiv:2307.07999 (Avramescu, Baran, Greco, Ipp, Mueller, Ruggieri, "Heavy
+ * quark kappa and jet qhat transport coefficients in the Glasma early stage of
+ * heavy-ion collisions"):
+ *
+ *   - boost-invariant SU(3) Glasma fields on the transverse lattice, evolved by a
+ *     leapfrog of gauge links and chromo-electric fields built from plaquettes
+ *     and staples (Sec. 1, "Glasma", Eq. 1);
+ *   - test particles under Wong's equations with the colored particle-in-cell
+ *     method: each push gathers E and B at the particle's cell, advances x and p
+ *     and rotates the color charge Q with the links it crosses (Sec. 1,
+ *     "Probes in Glasma", Eq. 2);
+ *   - the momentum broadening <dp_i^2>(tau) = <p_i^2(tau) - p_i^2(tau_form)>
+ *     from which kappa and qhat follow by d/dtau (Sec. 2, Eq. 3).
+ *
+ * Units: physical inputs in GeV and fm; internally lattice units (a = 1, the
+ * coupling g absorbed into the fields).  Outputs of broadening_accumulate are
+ * in GeV^2 with tau in fm/c.
+ *
+ * Memory: the library never allocates device memory for field or particle
+ * state.  The caller passes one device workspace per context (size from the
+ * matching *_workspace_bytes call), 256-byte aligned, owned by the caller and
+ * kept alive until the context is destroyed.  Host buffers passed to the calls
+ * are caller-owned and only read or written during the call.
+ *
+ * Streams: every call is ordered on the CUDA stream given at creation (NULL =
+ * legacy default stream).  Calls that return data to the host synchronise that
+ * stream; the others only enqueue work.
+ *
+ * Errors: every call returns a glasma_status; no C++ exception crosses the ABI.
+ * glasma_last_error() returns a thread-local message for the last failure.
+ * A context whose call failed with GLASMA_ERR_CUDA should be destroyed.
+ */
+#ifndef GLASMA_H
+#define GLASMA_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GLASMA_OK = 0,
+    GLASMA_ERR_INVALID = -1,   /* bad argument, size or call order */
+    GLASMA_ERR_CUDA = -2,      /* a CUDA or cuFFT call failed */
+    GLASMA_ERR_NONFINITE = -3, /* a monitor found NaN/Inf */
+    GLASMA_ERR_TIMEOUT = -4,   /* a bounded device wait ran out */
+    GLASMA_ERR_NOCONV = -5,    /* the tau = 0+ link solve left links unconverged */
+    GLASMA_ERR_NOSPACE = -6    /* the workspace is smaller than required */
+} glasma_status;
+
+typedef enum { GLASMA_FP64 = 0, GLASMA_FP32 = 1 } glasma_precision;
+
+/* Glasma event (Sec. 1, "Glasma": MV model, the saturation-type scale g^2 mu is
+ * the only physical parameter besides the lattice). */
+typedef struct {
+    int32_t n;               /* transverse lattice sites per side (periodic n x n) */
+    int32_t n_sheets;        /* longitudinal color sheets of the MV charges */
+    double L_fm;             /* transverse box size; lattice spacing a = L / n */
+    double g2mu_GeV;         /* MV charge scale g^2 mu */
+    double m_ir_GeV;         /* infrared regulator of the Poisson solve */
+    double dtau_over_a;      /* leapfrog step in units of a (1/8) */
+    double tau_end_fm;       /* evolution end; n_steps = ceil(tau_end / dtau) */
+    int32_t precision;       /* glasma_precision of the evolution */
+    int32_t reunit_every;    /* FP64 Gram-Schmidt of the links every k steps (0: never) */
+    int32_t expanding;       /* 1: boost-invariant Milne evolution; 0: static box (tests) */
+    int32_t newton_max_iter; /* tau = 0+ link solve: iteration cap per attempt */
+    double newton_tol;       /* tau = 0+ link solve: residual ||r||_2 target */
+    uint64_t seed;           /* Philox key of the MV charges */
+} glasma_params;
+
+/* Test-particle ensemble (Sec. 2, toy-model initialisation: uniform in the
+ * transverse plane, eta = 0, fixed initial momentum, formed at tau_form). */
+typedef struct {
+    int32_t n_particles;
+    int32_t init_kind;       /* 0: |p_T| uniform in [p_min, p_max], isotropic azimuth;
+                                1: along +x with |p| uniform in [p_min, p_max] */
+    double mass_GeV;         /* 0 allowed (massless partons) */
+    double tau_form_fm;      /* activation step = round(tau_form / dtau) */
+    double p_min_GeV, p_max_GeV;
+    double q2, q3;           /* Casimirs of Q (4 and 10/3 for <QQ> = 1/2, <QQQ> = d/4) */
+    int32_t bin_every;       /* counting sort of the particles by cell every k steps (0: never) */
+    uint64_t seed;           /* Philox key of positions, momenta and Haar rotations */
+} cpic_params;
+
+typedef struct glasma_ctx glasma_ctx;
+typedef struct cpic_ctx cpic_ctx;
+typedef struct glasma_batch glasma_batch;
+
+/* ------------------------------------------------------------------ fields */
+
+/* Device workspace needed by glasma_create for these parameters (bytes), or a
+ * negative glasma_status if the parameters are invalid. */
+int64_t glasma_workspace_bytes(const glasma_params* p);
+
+/* Creates a field context on the current CUDA device.  workspace: device
+ * pointer (>= glasma_workspace_bytes(p) bytes, 256-byte aligned); stream: a
+ * cudaStream_t or NULL.  The state is undefined until glasma_init or
+ * glasma_init_from_host. */
+glasma_status glasma_create(const glasma_params* p, void* workspace, int64_t workspace_bytes,
+                            void* stream, glasma_ctx** out);
+
+/* MV initial conditions on the device (Sec. 1, Eq. 1 and the tau = 0+ matching),
+ * leaving the state at step 1 (U, phi at tau = dtau; E = 0, pi = pi(0) at dtau/2).
+ * Returns GLASMA_ERR_NOCONV if some links did not reach newton_tol (the state
+ * is still usable; glasma_ic_stats reports how many). Synchronises. */
+glasma_status glasma_init(glasma_ctx* g);
+
+/* Newton statistics of the last glasma_init: failures, mean and max iterations. */
+glasma_status glasma_ic_stats(const glasma_ctx* g, int64_t* failures, double* mean_iter,
+                              int32_t* max_iter);
+
+/* Loads a state from host memory in the canonical layout, site s = x + n*y:
+ *   U   double[n*n][2][3][3][2]  (links U_x, U_y, complex row-major, re/im)
+ *   E   double[n*n][2][8]        (E_x^a, E_y^a at tau_{step-1/2})
+ *   phi double[n*n][8], pi double[n*n][8]
+ * step: the leapfrog index of the state (U, phi at tau = step*dtau). Synchronises. */
+glasma_status glasma_init_from_host(glasma_ctx* g, const double* U, const double* E,
+                                    const double* phi, const double* pi, int32_t step);
+
+/* Copies the current state to host memory in the canonical layout (any pointer
+ * may be NULL to skip that field) and returns its step. Synchronises. */
+glasma_status glasma_get_state(glasma_ctx* g, double* U, double* E, double* phi, double* pi,
+                               int32_t* step);
+
+/* Advances the fields by n_steps leapfrog steps (kick at tau_n, drift with
+ * tau_{n+1/2}); enqueue only. */
+glasma_status glasma_step(glasma_ctx* g, int32_t n_steps);
+
+/* FP64 monitors of the current state (synchronises):
+ *   out[0] Gauss-law violation relative to the scale of its terms
+ *   out[1..4] eps_E,T, eps_B,T, eps_E,L, eps_B,L (lattice units, E and pi at tau_{n-1/2})
+ *   out[5] max link unitarity deviation, out[6] tau (lattice units), out[7] nonfinite count */
+glasma_status glasma_diagnostics(glasma_ctx* g, double out[8]);
+
+void glasma_destroy(glasma_ctx* g);
+
+/* ------------------------------------------------------------------ particles */
+
+int64_t cpic_workspace_bytes(const glasma_params* gp, const cpic_params* p);
+
+/* Creates a particle ensemble bound to the field context g (which must outlive it). */
+glasma_status cpic_create(glasma_ctx* g, const cpic_params* p, void* workspace,
+                          int64_t workspace_bytes, cpic_ctx** out);
+
+/* Philox initial state (Sec. 1: Q0 in the Cartan subalgebra with the given
+ * Casimirs, Q = U Q0 U^dag with Haar U; Sec. 2: toy-model positions and momenta). */
+glasma_status cpic_init(cpic_ctx* c);
+
+/* Loads particle states from host (double[n_particles] each; Q double[n][8]; p0
+ * double[n][3] = lab momentum at formation; x, y continuous in [0, n)). */
+glasma_status cpic_init_from_host(cpic_ctx* c, const double* x, const double* y,
+                                  const double* eta, const double* px, const double* py,
+                                  const double* peta, const double* Q, const double* p0);
+
+/* Copies particle states to host in the original particle order (NULL skips). */
+glasma_status cpic_get_particles(cpic_ctx* c, double* x, double* y, double* eta, double* px,
+                                 double* py, double* peta, double* Q);
+
+/* Coupled step: n_steps x (field step; if tau_n >= tau_form, push every particle
+ * with the fields of tau_n and add its broadening terms to the row of tau_{n+1}).
+ * Enqueue only. */
+glasma_status cpic_push(cpic_ctx* c, int32_t n_steps);
+
+/* Broadening table (synchronises): rows r = 0..n-1 from the first pushed step (tau_form,
+ * or the field step at particle initialisation if later) to the current
+ * step, each {tau_fm, <dp_x^2>, <dp_y^2>, <dp_z^2> (GeV^2), particle count},
+ * p_z the lab longitudinal momentum.  cap_rows: rows available in host_out. */
+glasma_status broadening_accumulate(cpic_ctx* c, double* host_out, int64_t cap_rows,
+                                    int64_t* n_rows);
+
+/* Maximum drift of the Casimirs q2, q3 over all particles (synchronises). */
+glasma_status cpic_casimir_drift(cpic_ctx* c, double out[2]);
+
+void cpic_destroy(cpic_ctx* c);
+
+const char* glasma_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

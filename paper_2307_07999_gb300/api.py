@@ -1,0 +1,184 @@
+"""Thin Python surface over the C ABI: same names, argument marshalling only.
+
+Device workspaces come from PyTorch (torch.empty on the CUDA device) and the
+CUDA stream is torch's current stream unless one is given.  All compute runs
+in libglasma.so.
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import CpicParams, GlasmaParams, check, lib
+
+HBARC = 0.1973269804  # GeV fm
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes, device):
+    # 256-byte aligned device buffer owned by the caller (PyTorch's caching allocator)
+    t = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
+    off = (-t.data_ptr()) % 256
+    return t, t.data_ptr() + off
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# ------------------------------------------------------------------ C-named calls
+def glasma_create(params, workspace_ptr, nbytes, stream=None):
+    h = C.c_void_p()
+    check(lib().glasma_create(C.byref(params), C.c_void_p(workspace_ptr), nbytes, _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def glasma_init(handle):
+    return lib().glasma_init(handle)
+
+
+def glasma_step(handle, n_steps):
+    check(lib().glasma_step(handle, n_steps))
+
+
+def cpic_create(ghandle, params, workspace_ptr, nbytes):
+    h = C.c_void_p()
+    check(lib().cpic_create(ghandle, C.byref(params), C.c_void_p(workspace_ptr), nbytes, C.byref(h)))
+    return h
+
+
+def cpic_init(handle):
+    check(lib().cpic_init(handle))
+
+
+def cpic_push(handle, n_steps):
+    check(lib().cpic_push(handle, n_steps))
+
+
+def broadening_accumulate(handle, cap):
+    out = np.zeros((cap, 5))
+    n = C.c_int64()
+    check(lib().broadening_accumulate(handle, _dp(out), cap, C.byref(n)))
+    return out[: n.value]
+
+
+# ------------------------------------------------------------------ owning wrappers
+class Glasma:
+    """A field context with its PyTorch-owned workspace."""
+
+    def __init__(self, n, L_fm, g2mu_GeV=2.0, m_ir_GeV=0.2, n_sheets=10, dtau_over_a=0.125, tau_end_fm=1.0,
+                 precision=0, reunit_every=0, expanding=1, seed=1, newton_max_iter=100, newton_tol=1e-12,
+                 device="cuda", stream=None):
+        self.params = GlasmaParams(n, n_sheets, L_fm, g2mu_GeV, m_ir_GeV, dtau_over_a, tau_end_fm, precision,
+                                   reunit_every, expanding, newton_max_iter, newton_tol, seed)
+        nb = lib().glasma_workspace_bytes(C.byref(self.params))
+        check(0 if nb >= 0 else nb)
+        self._ws, ptr = _workspace(nb, device)
+        self.handle = glasma_create(self.params, ptr, nb, stream)
+        self.n = n
+        self.a_fm = L_fm / n
+        self.dtau = dtau_over_a
+
+    def init(self):
+        """MV initial conditions on the device; returns (failures, mean_iter, max_iter)."""
+        st = lib().glasma_init(self.handle)
+        if st not in (0, -5):
+            check(st)
+        return self.ic_stats()
+
+    def ic_stats(self):
+        f, m, x = C.c_int64(), C.c_double(), C.c_int32()
+        check(lib().glasma_ic_stats(self.handle, C.byref(f), C.byref(m), C.byref(x)))
+        return f.value, m.value, x.value
+
+    def set_state(self, U, E, phi, pi, step):
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        E, phi, pi = (np.ascontiguousarray(a, dtype=np.float64) for a in (E, phi, pi))
+        check(lib().glasma_init_from_host(self.handle, _dp(U), _dp(E), _dp(phi), _dp(pi), step))
+
+    def get_state(self):
+        ns = self.n * self.n
+        U = np.zeros((ns, 2, 3, 3), dtype=np.complex128)
+        E = np.zeros((ns, 2, 8))
+        phi = np.zeros((ns, 8))
+        pi = np.zeros((ns, 8))
+        st = C.c_int32()
+        check(lib().glasma_get_state(self.handle, _dp(U), _dp(E), _dp(phi), _dp(pi), C.byref(st)))
+        return U, E, phi, pi, st.value
+
+    def step(self, n_steps=1):
+        glasma_step(self.handle, n_steps)
+
+    def diagnostics(self):
+        out = np.zeros(8)
+        st = lib().glasma_diagnostics(self.handle, _dp(out))
+        if st not in (0, -3):
+            check(st)
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib().glasma_destroy(h)
+            self.handle = None
+
+
+class CPIC:
+    """A particle ensemble bound to a Glasma context."""
+
+    def __init__(self, glasma, n_particles, mass_GeV, tau_form_fm, p_min_GeV=0.0, p_max_GeV=0.0, init_kind=0,
+                 q2=4.0, q3=10.0 / 3.0, bin_every=0, seed=2, device="cuda"):
+        self.glasma = glasma
+        self.params = CpicParams(n_particles, init_kind, mass_GeV, tau_form_fm, p_min_GeV, p_max_GeV, q2, q3,
+                                 bin_every, seed)
+        nb = lib().cpic_workspace_bytes(C.byref(glasma.params), C.byref(self.params))
+        check(0 if nb >= 0 else nb)
+        self._ws, ptr = _workspace(nb, device)
+        self.handle = cpic_create(glasma.handle, self.params, ptr, nb)
+        self.np = n_particles
+
+    def init(self):
+        cpic_init(self.handle)
+
+    def set_particles(self, x, y, eta, px, py, peta, Q, p0):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, eta, px, py, peta, Q, p0)]
+        check(lib().cpic_init_from_host(self.handle, *[_dp(a) for a in arrs]))
+
+    def get_particles(self):
+        n = self.np
+        out = [np.zeros(n) for _ in range(6)] + [np.zeros((n, 8))]
+        check(lib().cpic_get_particles(self.handle, *[_dp(a) for a in out]))
+        return dict(zip(("x", "y", "eta", "px", "py", "peta", "Q"), out))
+
+    def push(self, n_steps=1):
+        cpic_push(self.handle, n_steps)
+
+    def broadening(self):
+        return broadening_accumulate(self.handle, 1 << 16)
+
+    def casimir_drift(self):
+        out = np.zeros(2)
+        check(lib().cpic_casimir_drift(self.handle, _dp(out)))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib().cpic_destroy(h)
+            self.handle = None
+
+
+def kappa_qhat(table):
+    """d/dtau of the broadening table (Eq. 3): central differences inside, one-sided
+    at the ends.  table rows {tau_fm, <dpx^2>, <dpy^2>, <dpz^2>, count}; returns
+    rows {tau_fm, d<dpx^2>/dtau, d<dpy^2>/dtau, d<dpz^2>/dtau} in GeV^2/fm."""
+    t = table[:, 0]
+    out = np.zeros((len(t), 4))
+    out[:, 0] = t
+    if len(t) >= 2:
+        out[:, 1:] = np.gradient(table[:, 1:4], t, axis=0, edge_order=1)
+    return out

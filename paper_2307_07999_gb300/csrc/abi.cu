@@ -1,0 +1,422 @@
+// C ABI of the library (declared in include/glasma.h).  Host orchestration
+// only: every step of the method runs in the kernels of the kernels_*.cu files.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/glasma.h"
+#include "internal.h"
+
+using namespace glasma;
+
+static thread_local char g_err[512] = "";
+static glasma_status fail(glasma_status s, const char* fmt, const char* a = "") {
+    snprintf(g_err, sizeof(g_err), fmt, a);
+    return s;
+}
+static glasma_status cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_err, sizeof(g_err), "%s: %s", where, cudaGetErrorString(e));
+    return GLASMA_ERR_CUDA;
+}
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+    } while (0)
+
+extern "C" const char* glasma_last_error(void) { return g_err; }
+
+static const double HBARC = 0.1973269804;  // GeV fm
+
+// device workspace bump allocator
+struct Arena {
+    char* base;
+    size_t size, off;
+    void* take(size_t b) {
+        off = align256(off);
+        if (off + b > size) return nullptr;
+        void* p = base + off;
+        off += b;
+        return p;
+    }
+};
+
+struct glasma_ctx {
+    glasma_params p;
+    int n;
+    size_t ns;
+    int prec;
+    size_t rs;
+    void* buf[2];
+    int cur;
+    int step;
+    int n_steps;
+    double a_fm, a_gev, dtau;
+    cudaStream_t st;
+    double* mon;
+    void* ic_base;
+    size_t fft_work;
+    long long ic_fails;
+    double ic_mean;
+    int ic_max;
+};
+
+static glasma_status check_params(const glasma_params* p) {
+    if (!p) return fail(GLASMA_ERR_INVALID, "null params");
+    if (p->n < 2 || p->n > 16384) return fail(GLASMA_ERR_INVALID, "n must be in [2, 16384]");
+    if (!(p->L_fm > 0) || !(p->dtau_over_a > 0) || p->dtau_over_a > 1.0)
+        return fail(GLASMA_ERR_INVALID, "L_fm > 0 and 0 < dtau_over_a <= 1 required");
+    if (p->precision != GLASMA_FP64 && p->precision != GLASMA_FP32) return fail(GLASMA_ERR_INVALID, "bad precision");
+    if (p->n_sheets < 1 || p->n_sheets > 4096) return fail(GLASMA_ERR_INVALID, "n_sheets out of range");
+    if (!(p->tau_end_fm > 0)) return fail(GLASMA_ERR_INVALID, "tau_end_fm must be > 0");
+    return GLASMA_OK;
+}
+static size_t field_buf_bytes(const glasma_params* p) {
+    const size_t rs = p->precision == GLASMA_FP32 ? 4 : 8;
+    return align256((size_t)N_FIELD_PLANES * (size_t)p->n * p->n * rs);
+}
+
+extern "C" int64_t glasma_workspace_bytes(const glasma_params* p) {
+    glasma_status s = check_params(p);
+    if (s != GLASMA_OK) return s;
+    const char* err = "";
+    const size_t work = ic_fft_work_bytes(p->n, &err);
+    if (work == (size_t)-1) return fail(GLASMA_ERR_CUDA, "%s", err);
+    return (int64_t)(2 * field_buf_bytes(p) + 256 + ic_scratch_bytes(p->n, work) + 1024);
+}
+
+extern "C" glasma_status glasma_create(const glasma_params* p, void* ws, int64_t ws_bytes, void* stream,
+                                       glasma_ctx** out) {
+    glasma_status s = check_params(p);
+    if (s != GLASMA_OK) return s;
+    if (!ws || !out || ((uintptr_t)ws & 255)) return fail(GLASMA_ERR_INVALID, "workspace must be non-null, 256-byte aligned");
+    const int64_t need = glasma_workspace_bytes(p);
+    if (need < 0) return (glasma_status)need;
+    if (ws_bytes < need) return fail(GLASMA_ERR_NOSPACE, "workspace too small");
+    glasma_ctx* g = new (std::nothrow) glasma_ctx();
+    if (!g) return fail(GLASMA_ERR_INVALID, "host allocation failed");
+    g->p = *p;
+    g->n = p->n;
+    g->ns = (size_t)p->n * p->n;
+    g->prec = p->precision;
+    g->rs = g->prec ? 4 : 8;
+    Arena A{(char*)ws, (size_t)ws_bytes, 0};
+    g->buf[0] = A.take(field_buf_bytes(p));
+    g->buf[1] = A.take(field_buf_bytes(p));
+    g->mon = (double*)A.take(256);
+    const char* err = "";
+    g->fft_work = ic_fft_work_bytes(p->n, &err);
+    g->ic_base = A.take(ic_scratch_bytes(p->n, g->fft_work));
+    if (!g->buf[0] || !g->buf[1] || !g->mon || !g->ic_base) { delete g; return fail(GLASMA_ERR_NOSPACE, "workspace too small"); }
+    g->cur = 0;
+    g->step = -1;
+    g->a_fm = p->L_fm / p->n;
+    g->a_gev = g->a_fm / HBARC;
+    g->dtau = p->dtau_over_a;
+    g->n_steps = (int)ceil(p->tau_end_fm / (g->dtau * g->a_fm) - 1e-9);
+    g->st = (cudaStream_t)stream;
+    *out = g;
+    return GLASMA_OK;
+}
+
+extern "C" void glasma_destroy(glasma_ctx* g) { delete g; }
+
+extern "C" glasma_status glasma_init(glasma_ctx* g) {
+    if (!g) return fail(GLASMA_ERR_INVALID, "null context");
+    if (!g->p.expanding) return fail(GLASMA_ERR_INVALID, "MV initial conditions need the expanding evolution");
+    const ICScratch sc = ic_layout(g->ic_base, g->n, g->fft_work);
+    const char* err = "";
+    const int tol_it = g->p.newton_max_iter > 0 ? g->p.newton_max_iter : 100;
+    const double tol = g->p.newton_tol > 0 ? g->p.newton_tol : 1e-12;
+    int rc = ic_run(g->prec, g->n, g->p.n_sheets, g->p.g2mu_GeV * g->a_gev, g->p.m_ir_GeV * g->a_gev, g->p.seed,
+                    g->dtau, tol, tol_it, sc, g->buf[0], g->st, &g->ic_fails, &g->ic_mean, &g->ic_max, &err);
+    if (rc == -6) return fail(GLASMA_ERR_NOSPACE, "%s", err);
+    if (rc != 0) return fail(GLASMA_ERR_CUDA, "%s", err);
+    g->cur = 0;
+    g->step = 1;
+    return g->ic_fails ? fail(GLASMA_ERR_NOCONV, "some tau=0+ links did not converge") : GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_ic_stats(const glasma_ctx* g, int64_t* failures, double* mean_iter, int32_t* max_iter) {
+    if (!g) return fail(GLASMA_ERR_INVALID, "null context");
+    if (failures) *failures = g->ic_fails;
+    if (mean_iter) *mean_iter = g->ic_mean;
+    if (max_iter) *max_iter = g->ic_max;
+    return GLASMA_OK;
+}
+
+// canonical host arrays pass through the IC scratch region as a staging area
+extern "C" glasma_status glasma_init_from_host(glasma_ctx* g, const double* U, const double* E, const double* phi,
+                                               const double* pi, int32_t step) {
+    if (!g || !U || !E || !phi || !pi) return fail(GLASMA_ERR_INVALID, "null argument");
+    if (step < 1 && g->p.expanding) return fail(GLASMA_ERR_INVALID, "expanding evolution needs step >= 1");
+    const size_t ns = g->ns;
+    double* d = (double*)g->ic_base;  // needs 36+16+8+8 = 68 doubles per site (< IC scratch)
+    double *dU = d, *dE = d + 36 * ns, *dphi = dE + 16 * ns, *dpi = dphi + 8 * ns;
+    CK(cudaMemcpyAsync(dU, U, 36 * ns * 8, cudaMemcpyHostToDevice, g->st));
+    CK(cudaMemcpyAsync(dE, E, 16 * ns * 8, cudaMemcpyHostToDevice, g->st));
+    CK(cudaMemcpyAsync(dphi, phi, 8 * ns * 8, cudaMemcpyHostToDevice, g->st));
+    CK(cudaMemcpyAsync(dpi, pi, 8 * ns * 8, cudaMemcpyHostToDevice, g->st));
+    CK(launch_state_from_canonical(g->prec, dU, dE, dphi, dpi, g->buf[0], g->n, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    g->cur = 0;
+    g->step = step;
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_get_state(glasma_ctx* g, double* U, double* E, double* phi, double* pi,
+                                          int32_t* step) {
+    if (!g) return fail(GLASMA_ERR_INVALID, "null context");
+    if (g->step < 0) return fail(GLASMA_ERR_INVALID, "state not initialised");
+    const size_t ns = g->ns;
+    double* d = (double*)g->ic_base;
+    double *dU = d, *dE = d + 36 * ns, *dphi = dE + 16 * ns, *dpi = dphi + 8 * ns;
+    CK(launch_state_to_canonical(g->prec, g->buf[g->cur], U ? dU : nullptr, E ? dE : nullptr, phi ? dphi : nullptr,
+                                 pi ? dpi : nullptr, g->n, g->st));
+    if (U) CK(cudaMemcpyAsync(U, dU, 36 * ns * 8, cudaMemcpyDeviceToHost, g->st));
+    if (E) CK(cudaMemcpyAsync(E, dE, 16 * ns * 8, cudaMemcpyDeviceToHost, g->st));
+    if (phi) CK(cudaMemcpyAsync(phi, dphi, 8 * ns * 8, cudaMemcpyDeviceToHost, g->st));
+    if (pi) CK(cudaMemcpyAsync(pi, dpi, 8 * ns * 8, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    if (step) *step = g->step;
+    return GLASMA_OK;
+}
+
+static glasma_status one_field_step(glasma_ctx* g) {
+    const int reunit = g->p.reunit_every > 0 && ((g->step + 1) % g->p.reunit_every == 0);
+    const StepHost a = step_coeffs(g->buf[g->cur], g->buf[g->cur ^ 1], g->n, g->step, g->dtau, g->p.expanding, reunit);
+    CK(launch_field_step(g->prec, a, g->st));
+    g->cur ^= 1;
+    g->step++;
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_step(glasma_ctx* g, int32_t n_steps) {
+    if (!g || n_steps < 0) return fail(GLASMA_ERR_INVALID, "bad arguments");
+    if (g->step < 0) return fail(GLASMA_ERR_INVALID, "state not initialised");
+    if (g->p.expanding && g->step < 1) return fail(GLASMA_ERR_INVALID, "expanding step needs tau > 0");
+    for (int k = 0; k < n_steps; k++) {
+        glasma_status s = one_field_step(g);
+        if (s != GLASMA_OK) return s;
+    }
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_diagnostics(glasma_ctx* g, double out[8]) {
+    if (!g || !out) return fail(GLASMA_ERR_INVALID, "bad arguments");
+    if (g->step < 0) return fail(GLASMA_ERR_INVALID, "state not initialised");
+    const double tau = g->step * g->dtau;
+    CK(launch_monitors(g->prec, g->buf[g->cur], g->n, g->p.expanding ? tau : 1.0, g->mon, g->st));
+    double m[8];
+    CK(cudaMemcpyAsync(m, g->mon, sizeof(m), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    const double ns = (double)g->ns;
+    out[0] = m[1] > 0 ? sqrt(m[0] / m[1]) : sqrt(m[0]);
+    out[1] = m[2] / ns;
+    out[2] = m[3] / ns;
+    out[3] = m[4] / ns;
+    out[4] = m[5] / ns;
+    out[5] = m[6];
+    out[6] = tau;
+    out[7] = m[7];
+    return m[7] > 0 ? fail(GLASMA_ERR_NONFINITE, "nonfinite field values") : GLASMA_OK;
+}
+
+// ------------------------------------------------------------------ particles
+struct cpic_ctx {
+    glasma_ctx* g;
+    cpic_params p;
+    int np;
+    int n_form;
+    PartHost P[2];
+    int pcur;
+    double* acc;     // [n_steps + 1][4]
+    int acc_rows;
+    int* sort_ws;
+    double* stage;   // 17 * np doubles
+    double* cas;     // 2 doubles
+    double mass;
+    int since_sort;
+    int first_step;  // first pushed step: max(n_form, field step at particle initialisation)
+};
+
+static glasma_status check_cpic(const cpic_params* p) {
+    if (!p) return fail(GLASMA_ERR_INVALID, "null params");
+    if (p->n_particles < 0) return fail(GLASMA_ERR_INVALID, "n_particles < 0");
+    if (p->mass_GeV < 0 || p->tau_form_fm < 0 || p->p_min_GeV < 0 || p->p_max_GeV < p->p_min_GeV)
+        return fail(GLASMA_ERR_INVALID, "bad mass, tau_form or momentum range");
+    if (p->init_kind != 0 && p->init_kind != 1) return fail(GLASMA_ERR_INVALID, "bad init_kind");
+    return GLASMA_OK;
+}
+static int total_steps(const glasma_params* gp) {
+    const double a_fm = gp->L_fm / gp->n;
+    return (int)ceil(gp->tau_end_fm / (gp->dtau_over_a * a_fm) - 1e-9);
+}
+
+extern "C" int64_t cpic_workspace_bytes(const glasma_params* gp, const cpic_params* p) {
+    glasma_status s = check_params(gp);
+    if (s != GLASMA_OK) return s;
+    s = check_cpic(p);
+    if (s != GLASMA_OK) return s;
+    const int np = p->n_particles;
+    const size_t ncell = (size_t)gp->n * gp->n;
+    return (int64_t)(2 * part_bytes(np, gp->precision) + align256(((size_t)total_steps(gp) + 2) * 4 * 8) +
+                     align256(sort_scratch_ints((int)ncell) * 4) + align256((size_t)17 * np * 8) + 256 + 2048);
+}
+
+extern "C" glasma_status cpic_create(glasma_ctx* g, const cpic_params* p, void* ws, int64_t ws_bytes, cpic_ctx** out) {
+    if (!g || !out) return fail(GLASMA_ERR_INVALID, "null argument");
+    glasma_status s = check_cpic(p);
+    if (s != GLASMA_OK) return s;
+    if (!ws || ((uintptr_t)ws & 255)) return fail(GLASMA_ERR_INVALID, "workspace must be non-null, 256-byte aligned");
+    if (ws_bytes < cpic_workspace_bytes(&g->p, p)) return fail(GLASMA_ERR_NOSPACE, "workspace too small");
+    cpic_ctx* c = new (std::nothrow) cpic_ctx();
+    if (!c) return fail(GLASMA_ERR_INVALID, "host allocation failed");
+    c->g = g;
+    c->p = *p;
+    c->np = p->n_particles;
+    Arena A{(char*)ws, (size_t)ws_bytes, 0};
+    const size_t pb = part_bytes(c->np, g->prec);
+    c->P[0] = part_layout(A.take(pb), c->np, g->prec);
+    c->P[1] = part_layout(A.take(pb), c->np, g->prec);
+    c->acc_rows = g->n_steps + 2;
+    c->acc = (double*)A.take((size_t)c->acc_rows * 4 * 8);
+    c->sort_ws = (int*)A.take(sort_scratch_ints((int)g->ns) * 4);
+    c->stage = (double*)A.take((size_t)17 * c->np * 8 + 8);
+    c->cas = (double*)A.take(256);
+    c->pcur = 0;
+    c->n_form = (int)lround(p->tau_form_fm / (g->dtau * g->a_fm));
+    if (c->n_form < 1) c->n_form = 1;
+    c->mass = p->mass_GeV * g->a_gev;
+    c->since_sort = 0;
+    c->first_step = c->n_form;
+    *out = c;
+    return GLASMA_OK;
+}
+extern "C" void cpic_destroy(cpic_ctx* c) { delete c; }
+
+extern "C" glasma_status cpic_init(cpic_ctx* c) {
+    if (!c) return fail(GLASMA_ERR_INVALID, "null context");
+    glasma_ctx* g = c->g;
+    CK(launch_part_init(g->prec, c->P[0], c->np, g->n, c->p.init_kind, c->p.p_min_GeV * g->a_gev,
+                        c->p.p_max_GeV * g->a_gev, c->p.q2, c->p.q3, c->p.seed, c->mass, g->st));
+    CK(cudaMemsetAsync(c->acc, 0, (size_t)c->acc_rows * 4 * 8, g->st));
+    c->pcur = 0;
+    c->first_step = g->step > c->n_form ? g->step : c->n_form;
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status cpic_init_from_host(cpic_ctx* c, const double* x, const double* y, const double* eta,
+                                             const double* px, const double* py, const double* peta, const double* Q,
+                                             const double* p0) {
+    if (!c || !x || !y || !eta || !px || !py || !peta || !Q || !p0) return fail(GLASMA_ERR_INVALID, "null argument");
+    glasma_ctx* g = c->g;
+    const size_t np = c->np;
+    std::vector<double> h(17 * np);
+    memcpy(h.data(), x, np * 8);
+    memcpy(h.data() + np, y, np * 8);
+    memcpy(h.data() + 2 * np, eta, np * 8);
+    memcpy(h.data() + 3 * np, px, np * 8);
+    memcpy(h.data() + 4 * np, py, np * 8);
+    memcpy(h.data() + 5 * np, peta, np * 8);
+    for (size_t j = 0; j < np; j++) {
+        for (int a = 0; a < 8; a++) h[(6 + a) * np + j] = Q[8 * j + a];
+        for (int k = 0; k < 3; k++) h[(14 + k) * np + j] = p0[3 * j + k];
+    }
+    CK(cudaMemcpyAsync(c->stage, h.data(), 17 * np * 8, cudaMemcpyHostToDevice, g->st));
+    CK(launch_part_from_canonical(g->prec, c->P[0], c->np, g->n, c->stage, g->st));
+    CK(cudaMemsetAsync(c->acc, 0, (size_t)c->acc_rows * 4 * 8, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    c->pcur = 0;
+    c->first_step = g->step > c->n_form ? g->step : c->n_form;
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status cpic_get_particles(cpic_ctx* c, double* x, double* y, double* eta, double* px, double* py,
+                                            double* peta, double* Q) {
+    if (!c) return fail(GLASMA_ERR_INVALID, "null context");
+    glasma_ctx* g = c->g;
+    const size_t np = c->np;
+    CK(launch_part_to_canonical(g->prec, c->P[c->pcur], c->np, g->n, c->stage, g->st));
+    std::vector<double> h(14 * np);
+    CK(cudaMemcpyAsync(h.data(), c->stage, 14 * np * 8, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    double* outs[6] = {x, y, eta, px, py, peta};
+    for (int k = 0; k < 6; k++)
+        if (outs[k]) memcpy(outs[k], h.data() + k * np, np * 8);
+    if (Q)
+        for (size_t j = 0; j < np; j++)
+            for (int a = 0; a < 8; a++) Q[8 * j + a] = h[(6 + a) * np + j];
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status cpic_push(cpic_ctx* c, int32_t n_steps) {
+    if (!c || n_steps < 0) return fail(GLASMA_ERR_INVALID, "bad arguments");
+    glasma_ctx* g = c->g;
+    if (g->step < 1) return fail(GLASMA_ERR_INVALID, "field state not initialised");
+    for (int k = 0; k < n_steps; k++) {
+        if (g->step + 1 >= c->acc_rows) return fail(GLASMA_ERR_INVALID, "beyond tau_end");
+        const int n = g->step;
+        const void* fo = g->buf[g->cur];
+        glasma_status s = one_field_step(g);
+        if (s != GLASMA_OK) return s;
+        if (n >= c->first_step && c->np > 0) {
+            const double tn = n * g->dtau, th = (n + 0.5) * g->dtau;
+            PushHost a;
+            a.fo = fo;
+            a.fn = g->buf[g->cur];
+            a.n = g->n;
+            a.np = c->np;
+            a.dtau = g->dtau;
+            a.te = g->p.expanding ? tn : 1.0;
+            a.ichr = g->p.expanding ? 1.0 / tn : 0.0;
+            a.teh = g->p.expanding ? th : 1.0;
+            a.mass = c->mass;
+            a.expanding = g->p.expanding;
+            a.acc = c->acc + 4 * (size_t)(n + 1);
+            CK(launch_push(g->prec, a, c->P[c->pcur], g->st));
+            if (c->p.bin_every > 0 && ++c->since_sort >= c->p.bin_every) {
+                int* cnt = c->sort_ws;
+                int* start = cnt + g->ns;
+                int* tot = start + g->ns;
+                CK(launch_sort(g->prec, c->P[c->pcur], c->P[c->pcur ^ 1], c->np, (int)g->ns, cnt, start, tot, g->st));
+                c->pcur ^= 1;
+                c->since_sort = 0;
+            }
+        }
+    }
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status broadening_accumulate(cpic_ctx* c, double* out, int64_t cap, int64_t* n_rows) {
+    if (!c || !out || !n_rows) return fail(GLASMA_ERR_INVALID, "null argument");
+    glasma_ctx* g = c->g;
+    std::vector<double> h((size_t)c->acc_rows * 4);
+    CK(cudaMemcpyAsync(h.data(), c->acc, h.size() * 8, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    const double conv = 1.0 / (g->a_gev * g->a_gev);  // lattice momentum^2 -> GeV^2
+    int64_t k = 0;
+    for (int r = c->first_step; r <= g->step && r < c->acc_rows; r++) {
+        if (k >= cap) return fail(GLASMA_ERR_NOSPACE, "host_out too small");
+        double* o = out + 5 * k;
+        const double cnt = r == c->first_step ? (double)c->np : h[4 * r + 3];
+        o[0] = r * g->dtau * g->a_fm;
+        for (int i = 0; i < 3; i++) o[1 + i] = (r == c->first_step || cnt <= 0) ? 0.0 : h[4 * r + i] / cnt * conv;
+        o[4] = cnt;
+        k++;
+    }
+    *n_rows = k;
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status cpic_casimir_drift(cpic_ctx* c, double out[2]) {
+    if (!c || !out) return fail(GLASMA_ERR_INVALID, "null argument");
+    glasma_ctx* g = c->g;
+    CK(launch_casimir_drift(g->prec, c->P[c->pcur], c->np, c->p.q2, c->p.q3, c->cas, g->st));
+    CK(cudaMemcpyAsync(out, c->cas, 16, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return GLASMA_OK;
+}

@@ -1,0 +1,88 @@
+// Host-side launchers shared by the translation units of the library (no
+// device code here).  prec: 0 = FP64 evolution, 1 = FP32 evolution.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace glasma {
+
+constexpr int N_FIELD_PLANES = 56;
+constexpr int N_PART_REAL_PLANES = 17;  // ox oy eta p0x p0y p0z dpx dpy peta Q[8]
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// ---------------- fields
+struct StepHost {
+    const void* src;
+    void* dst;
+    int n;
+    double tb, tp, dtau, ue, pe;
+    int reunit;
+};
+// leapfrog coefficients of step n (state at tau_n = n dtau)
+StepHost step_coeffs(const void* src, void* dst, int n, int step, double dtau, int expanding, int reunit);
+cudaError_t launch_field_step(int prec, const StepHost& a, cudaStream_t st);
+// batched: args[n_ev], items[n_items] (device arrays), one CTA per item
+cudaError_t launch_field_step_batched(int prec, const void* args_dev, const void* items_dev, int n_items,
+                                      cudaStream_t st);
+int field_tile_x(int prec);
+int field_tile_y(int prec);
+size_t step_args_size(int prec);
+void pack_step_args(int prec, const StepHost& a, void* out);
+
+// canonical host layout <-> device planes
+cudaError_t launch_state_from_canonical(int prec, const double* dU, const double* dE, const double* dphi,
+                                        const double* dpi, void* buf, int n, cudaStream_t st);
+cudaError_t launch_state_to_canonical(int prec, const void* buf, double* dU, double* dE, double* dphi,
+                                      double* dpi, int n, cudaStream_t st);
+// monitors into mon[0..7] (zeroed here)
+cudaError_t launch_monitors(int prec, const void* buf, int n, double tau_e, double* mon, cudaStream_t st);
+
+// ---------------- particles
+struct PartHost {
+    int* cell; int* pid;
+    void* planes;  // N_PART_REAL_PLANES planes of np reals, plane stride pstride (elements)
+    size_t pstride;
+};
+PartHost part_layout(void* base, int np, int prec);
+size_t part_bytes(int np, int prec);
+struct PushHost {
+    const void* fo; const void* fn;
+    int n, np;
+    double dtau, te, ichr, teh, mass;
+    int expanding;
+    double* acc;
+};
+cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st);
+cudaError_t launch_sort(int prec, const PartHost& a, const PartHost& b, int np, int ncell, int* count,
+                        int* start, int* totals, cudaStream_t st);
+size_t sort_scratch_ints(int ncell);
+cudaError_t launch_part_init(int prec, const PartHost& P, int np, int n, int kind, double pmin, double pmax,
+                             double q2, double q3, uint64_t seed, double mass, cudaStream_t st);
+cudaError_t launch_part_from_canonical(int prec, const PartHost& P, int np, int n, const double* d /*[11+8][np]*/,
+                                       cudaStream_t st);
+cudaError_t launch_part_to_canonical(int prec, const PartHost& P, int np, int n,
+                                     double* d /*[6+8][np], original order*/, cudaStream_t st);
+cudaError_t launch_casimir_drift(int prec, const PartHost& P, int np, double q2, double q3, double* out2,
+                                 cudaStream_t st);
+
+// ---------------- initial conditions (FP64 scratch)
+struct ICScratch {
+    double* V1; double* V2;   // [ns][18]
+    double* fft;              // complex [8][ns]
+    double* U;                // [ns][2][18]
+    double* pi0;              // [ns][8]
+    int* iters;               // [2 ns]
+    double* res;              // [2 ns]
+    void* fft_work; size_t fft_work_bytes;
+};
+size_t ic_scratch_bytes(int n, size_t fft_work_bytes);
+ICScratch ic_layout(void* base, int n, size_t fft_work_bytes);
+// full MV pipeline; writes the state at step 1 into buf; fails/iters summary into host ints
+int ic_run(int prec, int n, int n_sheets, double g2mua, double m_ir_a, uint64_t seed, double dtau, double tol,
+           int max_iter, const ICScratch& s, void* buf, cudaStream_t st, long long* fails, double* mean_it,
+           int* max_it, const char** err);
+size_t ic_fft_work_bytes(int n, const char** err);
+
+}  // namespace glasma
