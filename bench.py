@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the Glasma + CPIC hot path on GB300.
+
+Workload (one "step"): 64 Glasma events of uneven lattices (16 each of 128^2,
+256^2, 384^2, 512^2; L = 10 fm; g^2 mu ~ U[1.5, 2.5] GeV), each with 10k charm
+quarks, evolved in FP32 (FP64 accumulators) from tau = dtau to tau = 1 fm/c:
+a full run of the batch, every event to its own step count (103..410).
+Metric: site-updates/s (value) and particle-steps/s, whole job over N GPUs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode graph|persistent|eager|per_event]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+N > 1: launched by torchrun, one rank per GPU; each rank runs an independent
+replica batch (different event seeds), no data-path collective ("weak").
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Glasma site-updates/s & Wong particle-steps/s on 1 GB300 vs plain, at fixed tol"
+WORKLOAD = ("64 MV events, 16 each of 128^2/256^2/384^2/512^2 (L=10 fm, g2mu~U[1.5,2.5] GeV), "
+            "10k charm/event, FP32 fields+particles with FP64 accumulators, tau 0->1 fm/c")
+BYTES_PER_SITE = 448  # algorithmic bytes of one FP32 site-update (12-real links, read + write once)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="auto", choices=["auto", "graph", "persistent", "eager", "per_event"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- peaks, traffic
+def measured_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("su3.cuh", "field.cuh", "kernels_field.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2307_07999_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_site():
+    """DRAM bytes per site of the field kernel from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "field_step_fp32_ncu.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram_bytes_per_site:\s*([0-9.]+)", txt)
+    if not m or not b or m.group(1) != kernel_source_hash():
+        return None
+    return float(b.group(1))
+
+
+# ---------------------------------------------------------------- CPU baseline: the FP64 oracle
+def oracle_sample(budget_s=15.0, rank=0):
+    """The oracle as it stands on a bounded sample of the workload: one 256^2 event of
+    the batch with its 10k charm quarks, coupled steps from tau_form until the budget
+    is spent.  Returns site-updates/s, particle-steps/s and the sample description."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2307_07999_gb300 import workloads as W
+
+    evs, pps = W.batched_uneven(rank=rank)
+    e = 16  # first 256^2 event
+    gp, pp = evs[e], pps[e]
+    n = gp.n
+    a_fm = gp.L_fm / n
+    a = a_fm / W.HBARC
+    st, iters, fails = O.glasma_init(n, gp.n_sheets, gp.g2mu_GeV * a, gp.m_ir_GeV * a, gp.seed, gp.dtau_over_a)
+    P = O.particles_init(pp.n_particles, n, pp.mass_GeV * a, 0, 0.0, pp.p_max_GeV * a, pp.seed)
+    n_form = int(round(pp.tau_form_fm / (gp.dtau_over_a * a_fm)))
+    while st.step < n_form:
+        st = O.field_step(st, gp.dtau_over_a)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s and steps < 400:
+        nx = O.field_step(st, gp.dtau_over_a)
+        O.push(P, st, nx, gp.dtau_over_a, pp.mass_GeV * a)
+        st = nx
+        steps += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {
+        "site_updates_per_s": n * n * steps / dt,
+        "particle_steps_per_s": pp.n_particles * steps / dt,
+        "cores": cores,
+        "sample": f"one {n}^2 event of the batch + its {pp.n_particles} charm quarks, {steps} coupled FP64 steps "
+                  f"from tau_form ({dt:.1f} s)",
+        "seconds": dt,
+    }
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    per_step = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(budget_s=8.0)
+        if i >= args.warmup:
+            per_step.append(r)
+        last = r
+    v = statistics.mean(r["site_updates_per_s"] for r in per_step)
+    ps = statistics.mean(r["particle_steps_per_s"] for r in per_step)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "site-updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(r["seconds"] for r in per_step),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "particle_steps_per_s": ps,
+        "config": {"workload": WORKLOAD, "oracle_sample": last["sample"]},
+        "cpu_baseline": {"value": v, "unit": "site-updates/s", "cores": last["cores"], "kind": "oracle",
+                         "sample": last["sample"]},
+        "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_2307_07999_gb300 as G
+    from paper_2307_07999_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    evs, pps = W.batched_uneven(rank=rank)
+    with torch.cuda.stream(stream):
+        B = G.Batch(evs, pps, device=dev, stream=stream)
+        ic_fail = B.init()
+    su, ps = B.work()
+
+    def timed(mode, K, W_):
+        for _ in range(W_):
+            B.run(mode)
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            B.run(mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        return e0.elapsed_time(e1) / K
+
+    modes = ["graph", "persistent"] if args.mode == "auto" else [args.mode]
+    best = None
+    for m in modes:
+        try:
+            t = timed(m, 1, 1)
+        except G.GlasmaError as ex:
+            print(f"mode {m} unavailable: {ex}", file=sys.stderr)
+            continue
+        if best is None or t < best[1]:
+            best = (m, t)
+    mode = best[0]
+
+    clk = ClockSampler(local)
+    clk.start()
+    ms = timed(mode, args.steps, args.warmup)
+    clocks = clk.stop()
+    ms = max_over_ranks(ms, ws)
+    value = su * ws / (ms / 1000.0)
+    pvalue = ps * ws / (ms / 1000.0)
+    launches = B.launches(mode) * args.steps
+
+    # per-kernel durations (CUDA events around every launch, on the batch stream)
+    prof = B.profile()
+    field_ms_per_launch = prof["field_ms"] / prof["field_launches"]
+    sites_per_launch = prof["field_sites"] / prof["field_launches"]
+    achieved = BYTES_PER_SITE * sites_per_launch / (field_ms_per_launch / 1000.0) / 1e9
+    peak, peak_kind = measured_peak()
+    tps = ncu_traffic_per_site()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tps * sites_per_launch if tps else None), "kernel": "k_field_step_batched<float>",
+                "peak_kind": f"{peak_kind} HBM copy (burst)",
+                "share_of_step": prof["field_ms"] / (prof["field_ms"] + prof["push_ms"]),
+                "push_ms_per_run": prof["push_ms"]}
+
+    # plain one-event-per-launch GPU path on the same GPU
+    plain = None
+    if not args.no_plain:
+        pms = timed("per_event", 1, 1)
+        plain = {"value": su / (pms / 1000.0), "unit": "site-updates/s", "ms_per_step": pms,
+                 "speedup_of_batched": pms / ms}
+
+    # end to end through the public API: H2D of the initial state from pinned host memory,
+    # the run, D2H of every event's broadening table, each step
+    nbytes = B.state_bytes()
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    B.export_state(host)
+    for _ in range(1):
+        B.import_state(host)
+        B.run(mode)
+        tabs = [B.broadening(e) for e in range(B.E)]
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        B.import_state(host)
+        B.run(mode)
+        tabs = [B.broadening(e) for e in range(B.E)]
+        d2h = sum(t.nbytes for t in tabs)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0 / args.steps, ws)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(budget_s=15.0)
+        cpu = {"value": r["site_updates_per_s"], "unit": "site-updates/s", "cores": r["cores"], "kind": "oracle",
+               "sample": r["sample"], "particle_steps_per_s": r["particle_steps_per_s"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "particle_steps_per_s": pvalue,
+            "config": {"workload": WORKLOAD, "mode": mode, "site_updates_per_step": su,
+                       "particle_steps_per_step": ps, "l2": "inputs larger than L2 (3.5 GB of field state)",
+                       "ic_unconverged_links": ic_fail, "parallelism": f"{ws} independent replica batch(es)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "plain_one_event_per_launch": plain,
+            "e2e": {"value": su * ws / (e2e_ms / 1000.0), "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -175,6 +175,55 @@ glasma_status cpic_casimir_drift(cpic_ctx* c, double out[2]);
 
 void cpic_destroy(cpic_ctx* c);
 
+/* ------------------------------------------------------------------ event batches
+ * Many events of uneven lattice sizes, each with its own particle ensemble,
+ * advanced together; <dp_i^2> averages over particles and events (Sec. 2). */
+
+typedef enum {
+    GLASMA_BATCH_GRAPH = 0,      /* per step: one field launch over all active events' tiles and one
+                                    push launch over their particles, the whole run one CUDA graph */
+    GLASMA_BATCH_PERSISTENT = 1, /* one persistent cooperative kernel, bounded grid barrier per phase */
+    GLASMA_BATCH_PER_EVENT = 2,  /* plain loop: one event after the other, one launch per kernel */
+    GLASMA_BATCH_EAGER = 3       /* the launches of GLASMA_BATCH_GRAPH issued without a graph */
+} glasma_batch_mode;
+
+/* Workspace for n_events events: ev[i], pp[i] give event i (all with the same
+ * precision and expanding = 1). */
+int64_t glasma_batch_workspace_bytes(const glasma_params* ev, const cpic_params* pp, int32_t n_events);
+glasma_status glasma_batch_create(const glasma_params* ev, const cpic_params* pp, int32_t n_events,
+                                  void* workspace, int64_t workspace_bytes, void* stream,
+                                  glasma_batch** out);
+/* MV initial conditions and particles of every event (kept as the restart
+ * state of each run); ic_failures: unconverged tau = 0+ links. Synchronises. */
+glasma_status glasma_batch_init(glasma_batch* b, int64_t* ic_failures);
+/* One run: every event from its initial state to its own tau_end (enqueue only).
+ * GLASMA_BATCH_GRAPH needs a created stream (not NULL / the legacy default stream). */
+glasma_status glasma_batch_run(glasma_batch* b, int32_t mode);
+/* Site-updates and particle-steps of one run. */
+glasma_status glasma_batch_work(const glasma_batch* b, int64_t* site_updates, int64_t* particle_steps);
+/* Broadening table of event i after a run (rows as in broadening_accumulate). */
+glasma_status glasma_batch_broadening(glasma_batch* b, int32_t event, double* host_out, int64_t cap_rows,
+                                      int64_t* n_rows);
+/* Monitors of event i's final state (as glasma_diagnostics). */
+glasma_status glasma_batch_diagnostics(glasma_batch* b, int32_t event, double out[8]);
+/* Raw initial state of all events (device layout, event order): size, copy out,
+ * copy in (the next glasma_batch_run starts from it).  A checkpoint of the
+ * batch's starting point; export synchronises, import only enqueues. */
+int64_t glasma_batch_state_bytes(const glasma_batch* b);
+glasma_status glasma_batch_export_state(glasma_batch* b, void* host, int64_t bytes);
+glasma_status glasma_batch_import_state(glasma_batch* b, const void* host, int64_t bytes);
+/* One run with the launches of GLASMA_BATCH_GRAPH issued eagerly, each bracketed
+ * by CUDA events on the batch stream: total field-kernel and push-kernel time
+ * (ms), launches, and the sites covered by the field launches. Synchronises. */
+glasma_status glasma_batch_profile(glasma_batch* b, double* field_ms, int64_t* field_launches,
+                                   int64_t* field_sites, double* push_ms, int64_t* push_launches);
+/* Particles of event i (original order; double[n] each, Q double[n][8]; NULL skips). */
+glasma_status glasma_batch_get_particles(glasma_batch* b, int32_t event, double* x, double* y, double* eta,
+                                         double* px, double* py, double* peta, double* Q);
+/* Kernel launches of one run in the given mode. */
+int64_t glasma_batch_launches(const glasma_batch* b, int32_t mode);
+void glasma_batch_destroy(glasma_batch* b);
+
 const char* glasma_last_error(void);
 
 #ifdef __cplusplus

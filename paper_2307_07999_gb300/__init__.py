@@ -18,6 +18,7 @@ from ._lib import (  # noqa: F401
 )
 from .api import (  # noqa: F401
     CPIC,
+    Batch,
     Glasma,
     HBARC,
     broadening_accumulate,

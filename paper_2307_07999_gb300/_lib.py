@@ -8,6 +8,11 @@ LIB_PATH = os.path.join(HERE, "libglasma.so")
 GLASMA_FP64 = 0
 GLASMA_FP32 = 1
 
+GLASMA_BATCH_GRAPH = 0
+GLASMA_BATCH_PERSISTENT = 1
+GLASMA_BATCH_PER_EVENT = 2
+GLASMA_BATCH_EAGER = 3
+
 STATUS = {
     0: "GLASMA_OK",
     -1: "GLASMA_ERR_INVALID",
@@ -83,6 +88,21 @@ SIGNATURES = {
     "broadening_accumulate": (C.c_int, [_p, _p, _i64, C.POINTER(_i64)]),
     "cpic_casimir_drift": (C.c_int, [_p, _p]),
     "cpic_destroy": (None, [_p]),
+    "glasma_batch_workspace_bytes": (_i64, [C.POINTER(GlasmaParams), C.POINTER(CpicParams), _i32]),
+    "glasma_batch_create": (C.c_int, [C.POINTER(GlasmaParams), C.POINTER(CpicParams), _i32, _p, _i64, _p, _pp]),
+    "glasma_batch_init": (C.c_int, [_p, C.POINTER(_i64)]),
+    "glasma_batch_run": (C.c_int, [_p, _i32]),
+    "glasma_batch_work": (C.c_int, [_p, C.POINTER(_i64), C.POINTER(_i64)]),
+    "glasma_batch_broadening": (C.c_int, [_p, _i32, _p, _i64, C.POINTER(_i64)]),
+    "glasma_batch_diagnostics": (C.c_int, [_p, _i32, _p]),
+    "glasma_batch_state_bytes": (_i64, [_p]),
+    "glasma_batch_export_state": (C.c_int, [_p, _p, _i64]),
+    "glasma_batch_import_state": (C.c_int, [_p, _p, _i64]),
+    "glasma_batch_profile": (C.c_int, [_p, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_d),
+                                       C.POINTER(_i64)]),
+    "glasma_batch_launches": (_i64, [_p, _i32]),
+    "glasma_batch_get_particles": (C.c_int, [_p, _i32] + [_p] * 7),
+    "glasma_batch_destroy": (None, [_p]),
     "glasma_last_error": (C.c_char_p, []),
 }
 

@@ -172,6 +172,84 @@ class CPIC:
             self.handle = None
 
 
+class Batch:
+    """Many events (each a GlasmaParams + CpicParams pair) advanced together."""
+
+    MODES = {"graph": 0, "persistent": 1, "per_event": 2, "eager": 3}
+
+    def __init__(self, events, particles, device="cuda", stream=None):
+        # a created stream of our own: the legacy default stream cannot be captured into a graph
+        if stream is None:
+            stream = torch.cuda.Stream(device=device)
+        self.stream = stream
+        E = len(events)
+        self.ev = (GlasmaParams * E)(*events)
+        self.pp = (CpicParams * E)(*particles)
+        nb = lib().glasma_batch_workspace_bytes(self.ev, self.pp, E)
+        check(0 if nb >= 0 else nb)
+        self._ws, ptr = _workspace(nb, device)
+        self.workspace_bytes = nb
+        h = C.c_void_p()
+        check(lib().glasma_batch_create(self.ev, self.pp, E, C.c_void_p(ptr), nb, _stream_ptr(stream), C.byref(h)))
+        self.handle = h
+        self.E = E
+
+    def init(self):
+        f = C.c_int64()
+        check(lib().glasma_batch_init(self.handle, C.byref(f)))
+        return f.value
+
+    def run(self, mode="graph"):
+        check(lib().glasma_batch_run(self.handle, self.MODES[mode]))
+
+    def work(self):
+        a, b = C.c_int64(), C.c_int64()
+        check(lib().glasma_batch_work(self.handle, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def broadening(self, event):
+        out = np.zeros((1 << 14, 5))
+        n = C.c_int64()
+        check(lib().glasma_batch_broadening(self.handle, event, _dp(out), out.shape[0], C.byref(n)))
+        return out[: n.value]
+
+    def diagnostics(self, event):
+        out = np.zeros(8)
+        check(lib().glasma_batch_diagnostics(self.handle, event, _dp(out)))
+        return out
+
+    def get_particles(self, event):
+        n = self.pp[event].n_particles
+        out = [np.zeros(n) for _ in range(6)] + [np.zeros((n, 8))]
+        check(lib().glasma_batch_get_particles(self.handle, event, *[_dp(a) for a in out]))
+        return dict(zip(("x", "y", "eta", "px", "py", "peta", "Q"), out))
+
+    def state_bytes(self):
+        return lib().glasma_batch_state_bytes(self.handle)
+
+    def export_state(self, host_tensor):
+        check(lib().glasma_batch_export_state(self.handle, C.c_void_p(host_tensor.data_ptr()), host_tensor.numel()))
+
+    def import_state(self, host_tensor):
+        check(lib().glasma_batch_import_state(self.handle, C.c_void_p(host_tensor.data_ptr()), host_tensor.numel()))
+
+    def profile(self):
+        fm, pm = C.c_double(), C.c_double()
+        fl, fs, pl = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().glasma_batch_profile(self.handle, C.byref(fm), C.byref(fl), C.byref(fs), C.byref(pm), C.byref(pl)))
+        return dict(field_ms=fm.value, field_launches=fl.value, field_sites=fs.value, push_ms=pm.value,
+                    push_launches=pl.value)
+
+    def launches(self, mode="graph"):
+        return lib().glasma_batch_launches(self.handle, self.MODES[mode])
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib().glasma_batch_destroy(h)
+            self.handle = None
+
+
 def kappa_qhat(table):
     """d/dtau of the broadening table (Eq. 3): central differences inside, one-sided
     at the ends.  table rows {tau_fm, <dpx^2>, <dpy^2>, <dpz^2>, count}; returns

@@ -28,6 +28,7 @@ static glasma_status cuda_fail(cudaError_t e, const char* where) {
     } while (0)
 
 extern "C" const char* glasma_last_error(void) { return g_err; }
+void glasma_set_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
 static const double HBARC = 0.1973269804;  // GeV fm
 

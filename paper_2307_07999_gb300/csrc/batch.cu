@@ -1,0 +1,541 @@
+// Many Glasma events of uneven lattice sizes, each with its own particle
+// ensemble, advanced together (the event average of Sec. 2, "Quantifying the
+// effect of Glasma", of arXiv:2307.07999 taken over independent events).
+//
+// Events are ordered by their step count (descending); iteration k advances
+// every event whose step k+1 is below its own n_steps, so the active events,
+// their field tiles and their particle blocks are always prefixes of fixed
+// tables.  The per-step arguments (tau-dependent coefficients, ping-pong
+// buffers, accumulator rows) are precomputed per iteration, so one run is a
+// fixed sequence of launches that is captured once into a CUDA graph.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/glasma.h"
+#include "batch.h"
+#include "internal.h"
+
+using namespace glasma;
+
+static thread_local char b_err[512] = "";
+const char* glasma_batch_error() { return b_err; }
+
+static glasma_status bfail(glasma_status s, const char* msg) {
+    snprintf(b_err, sizeof(b_err), "%s", msg);
+    glasma_set_error(b_err);
+    return s;
+}
+static glasma_status bcuda(cudaError_t e, const char* where) {
+    snprintf(b_err, sizeof(b_err), "%s: %s", where, cudaGetErrorString(e));
+    glasma_set_error(b_err);
+    return GLASMA_ERR_CUDA;
+}
+#define BCK(call)                                          \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return bcuda(e_, #call);    \
+    } while (0)
+
+static const double HBARC_B = 0.1973269804;
+
+static int steps_of(const glasma_params& p) {
+    const double a_fm = p.L_fm / p.n;
+    return (int)ceil(p.tau_end_fm / (p.dtau_over_a * a_fm) - 1e-9);
+}
+static size_t fbytes(const glasma_params& p) {
+    return align256((size_t)N_FIELD_PLANES * (size_t)p.n * p.n * (p.precision ? 4 : 8));
+}
+
+struct Layout {
+    size_t fields, parts, accs, tables, scratch, total;
+};
+
+static Layout layout(const glasma_params* ev, const cpic_params* pp, int E, size_t fft_work) {
+    Layout L{};
+    int nmax = 0, smax = 0;
+    size_t npmax = 0;
+    for (int e = 0; e < E; e++) {
+        L.fields += 3 * fbytes(ev[e]);
+        L.parts += 2 * part_bytes(pp[e].n_particles, ev[e].precision);
+        L.accs += align256(((size_t)steps_of(ev[e]) + 2) * 4 * 8);
+        nmax = std::max(nmax, ev[e].n);
+        smax = std::max(smax, steps_of(ev[e]));
+        npmax = std::max(npmax, (size_t)pp[e].n_particles);
+    }
+    const int prec = ev[0].precision;
+    L.tables = align256((size_t)smax * E * step_args_size(prec)) + align256((size_t)smax * E * push_args_size(prec)) +
+               align256((size_t)4 << 20) + align256((size_t)4 << 20);
+    const size_t ic = ic_scratch_bytes(nmax, fft_work);
+    const size_t srt = align256(sort_scratch_ints(nmax * nmax) * 4);
+    L.scratch = std::max(ic, srt) + 256;
+    L.total = L.fields + L.parts + L.accs + L.tables + L.scratch + 16 * 256 * (size_t)E + 4096;
+    return L;
+}
+
+static glasma_status check_batch(const glasma_params* ev, const cpic_params* pp, int E) {
+    if (!ev || !pp || E < 1 || E > 65536) return bfail(GLASMA_ERR_INVALID, "bad event list");
+    for (int e = 0; e < E; e++) {
+        if (ev[e].precision != ev[0].precision || ev[e].expanding != 1)
+            return bfail(GLASMA_ERR_INVALID, "all events need the same precision and the expanding evolution");
+        if (ev[e].n < 2 || ev[e].n > 16384 || !(ev[e].L_fm > 0) || !(ev[e].dtau_over_a > 0) || ev[e].dtau_over_a > 1 ||
+            ev[e].n_sheets < 1 || !(ev[e].tau_end_fm > 0))
+            return bfail(GLASMA_ERR_INVALID, "bad event parameters");
+        if (pp[e].n_particles < 0 || pp[e].mass_GeV < 0 || pp[e].tau_form_fm < 0 || pp[e].p_max_GeV < pp[e].p_min_GeV ||
+            (pp[e].init_kind != 0 && pp[e].init_kind != 1))
+            return bfail(GLASMA_ERR_INVALID, "bad particle parameters");
+    }
+    return GLASMA_OK;
+}
+
+extern "C" int64_t glasma_batch_workspace_bytes(const glasma_params* ev, const cpic_params* pp, int32_t E) {
+    glasma_status s = check_batch(ev, pp, E);
+    if (s != GLASMA_OK) return s;
+    int nmax = 0;
+    for (int e = 0; e < E; e++) nmax = std::max(nmax, ev[e].n);
+    const char* err = "";
+    const size_t work = ic_fft_work_bytes(nmax, &err);
+    if (work == (size_t)-1) return bfail(GLASMA_ERR_CUDA, err);
+    return (int64_t)layout(ev, pp, E, work).total;
+}
+
+struct Arena2 {
+    char* base;
+    size_t size, off;
+    void* take(size_t b) {
+        off = align256(off);
+        if (off + b > size) return nullptr;
+        void* p = base + off;
+        off += b;
+        return p;
+    }
+};
+
+extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic_params* pp, int32_t E, void* ws,
+                                             int64_t ws_bytes, void* stream, glasma_batch** out) {
+    glasma_status s = check_batch(ev, pp, E);
+    if (s != GLASMA_OK) return s;
+    if (!ws || !out || ((uintptr_t)ws & 255)) return bfail(GLASMA_ERR_INVALID, "workspace must be non-null, 256-byte aligned");
+    const int64_t need = glasma_batch_workspace_bytes(ev, pp, E);
+    if (need < 0) return (glasma_status)need;
+    if (ws_bytes < need) return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
+    glasma_batch* b = new (std::nothrow) glasma_batch();
+    if (!b) return bfail(GLASMA_ERR_INVALID, "host allocation failed");
+    b->prec = ev[0].precision;
+    b->st = (cudaStream_t)stream;
+    b->E = E;
+    int nmax = 0;
+    for (int e = 0; e < E; e++) nmax = std::max(nmax, ev[e].n);
+    const char* err = "";
+    b->fft_work = ic_fft_work_bytes(nmax, &err);
+    b->nmax = nmax;
+    // order: step count descending (stable), so active events are prefixes
+    std::vector<int> ord(E);
+    for (int e = 0; e < E; e++) ord[e] = e;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return steps_of(ev[a]) > steps_of(ev[c]); });
+    b->pos.assign(E, 0);
+    Arena2 A{(char*)ws, (size_t)ws_bytes, 0};
+    b->ev.resize(E);
+    for (int i = 0; i < E; i++) {
+        const int e = ord[i];
+        b->pos[e] = i;
+        BatchEvent& x = b->ev[i];
+        x.gp = ev[e];
+        x.pp = pp[e];
+        x.id = e;
+        x.n = ev[e].n;
+        x.ns = (size_t)x.n * x.n;
+        x.n_steps = steps_of(ev[e]);
+        x.a_fm = ev[e].L_fm / x.n;
+        x.a_gev = x.a_fm / HBARC_B;
+        x.dtau = ev[e].dtau_over_a;
+        x.np = pp[e].n_particles;
+        x.n_form = std::max(1, (int)lround(pp[e].tau_form_fm / (x.dtau * x.a_fm)));
+        x.mass = pp[e].mass_GeV * x.a_gev;
+        x.buf[0] = A.take(fbytes(ev[e]));
+        x.buf[1] = A.take(fbytes(ev[e]));
+        x.init_buf = A.take(fbytes(ev[e]));
+        const size_t pb = part_bytes(x.np, b->prec);
+        x.part_bytes = pb;
+        x.part_base = A.take(pb);
+        x.part_init = A.take(pb);
+        x.P = part_layout(x.part_base, x.np, b->prec);
+        x.acc_rows = x.n_steps + 2;
+        x.acc = (double*)A.take((size_t)x.acc_rows * 4 * 8);
+        x.mon = (double*)A.take(256);
+        if (!x.buf[0] || !x.buf[1] || !x.init_buf || !x.part_base || !x.part_init || !x.acc || !x.mon) {
+            delete b;
+            return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
+        }
+    }
+    b->max_iter = 0;
+    for (auto& x : b->ev) b->max_iter = std::max(b->max_iter, x.n_steps - 1);
+    b->step_args = A.take(align256((size_t)std::max(1, b->max_iter) * E * step_args_size(b->prec)));
+    b->push_args = A.take(align256((size_t)std::max(1, b->max_iter) * E * push_args_size(b->prec)));
+    b->tiles_dev = A.take((size_t)4 << 20);
+    b->pitems_dev = A.take((size_t)4 << 20);
+    b->scratch = A.take(std::max(ic_scratch_bytes(nmax, b->fft_work), align256(sort_scratch_ints(nmax * nmax) * 4)));
+    if (!b->step_args || !b->push_args || !b->tiles_dev || !b->pitems_dev || !b->scratch) {
+        delete b;
+        return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
+    }
+    *out = b;
+    return GLASMA_OK;
+}
+
+// tables of per-iteration arguments, tile items and particle-block items
+static glasma_status build_tables(glasma_batch* b) {
+    const int E = b->E, K = std::max(1, b->max_iter);
+    const int tx = field_tile_x(b->prec), ty = field_tile_y(b->prec);
+    std::vector<TileItemH> tiles;
+    std::vector<PushItemH> pits;
+    b->tiles_upto.assign(E + 1, 0);
+    b->pitems_upto.assign(E + 1, 0);
+    for (int i = 0; i < E; i++) {
+        const BatchEvent& x = b->ev[i];
+        for (int y0 = 0; y0 < x.n; y0 += ty)
+            for (int x0 = 0; x0 < x.n; x0 += tx) tiles.push_back({i, x0, y0});
+        for (int j0 = 0; j0 < x.np; j0 += 256) pits.push_back({i, j0});
+        b->tiles_upto[i + 1] = (int)tiles.size();
+        b->pitems_upto[i + 1] = (int)pits.size();
+    }
+    if (tiles.size() * sizeof(TileItemH) > ((size_t)4 << 20) || pits.size() * sizeof(PushItemH) > ((size_t)4 << 20))
+        return bfail(GLASMA_ERR_NOSPACE, "item tables exceed their reserve");
+    BCK(cudaMemcpyAsync(b->tiles_dev, tiles.data(), tiles.size() * sizeof(TileItemH), cudaMemcpyHostToDevice, b->st));
+    BCK(cudaMemcpyAsync(b->pitems_dev, pits.data(), pits.size() * sizeof(PushItemH), cudaMemcpyHostToDevice, b->st));
+    const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
+    std::vector<char> hs((size_t)K * E * sa, 0), hp((size_t)K * E * pa, 0);
+    b->active.assign(K, 0);
+    for (int k = 0; k < K; k++) {
+        const int s = k + 1;  // every event starts at step 1
+        int act = 0;
+        for (int i = 0; i < E; i++) {
+            const BatchEvent& x = b->ev[i];
+            const bool on = s < x.n_steps;
+            if (on) act = i + 1;
+            const void* src = x.buf[k & 1];
+            void* dst = x.buf[(k + 1) & 1];
+            const int reunit = x.gp.reunit_every > 0 && ((s + 1) % x.gp.reunit_every == 0);
+            const StepHost st = step_coeffs(src, dst, x.n, s, x.dtau, 1, reunit);
+            pack_step_args(b->prec, st, hs.data() + ((size_t)k * E + i) * sa);
+            PushHost ph;
+            ph.fo = src; ph.fn = dst; ph.n = x.n; ph.np = x.np; ph.dtau = x.dtau;
+            ph.te = s * x.dtau; ph.ichr = 1.0 / (s * x.dtau); ph.teh = (s + 0.5) * x.dtau; ph.mass = x.mass;
+            ph.expanding = 1;
+            ph.acc = (on && s >= x.n_form) ? x.acc + 4 * (size_t)(s + 1) : nullptr;
+            pack_push_args(b->prec, ph, x.P, hp.data() + ((size_t)k * E + i) * pa);
+        }
+        b->active[k] = act;
+    }
+    // first launch outside any stream capture sets the kernels' shared-memory attribute
+    BCK(launch_field_step_batched(b->prec, nullptr, nullptr, 0, b->st));
+    BCK(cudaMemcpyAsync(b->step_args, hs.data(), hs.size(), cudaMemcpyHostToDevice, b->st));
+    BCK(cudaMemcpyAsync(b->push_args, hp.data(), hp.size(), cudaMemcpyHostToDevice, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_batch_init(glasma_batch* b, int64_t* ic_failures) {
+    if (!b) return bfail(GLASMA_ERR_INVALID, "null batch");
+    long long fails_total = 0;
+    for (auto& x : b->ev) {
+        const ICScratch sc = ic_layout(b->scratch, x.n, b->fft_work);
+        const char* err = "";
+        long long f = 0;
+        double m = 0;
+        int mx = 0;
+        const int it = x.gp.newton_max_iter > 0 ? x.gp.newton_max_iter : 100;
+        const double tol = x.gp.newton_tol > 0 ? x.gp.newton_tol : 1e-12;
+        int rc = ic_run(b->prec, x.n, x.gp.n_sheets, x.gp.g2mu_GeV * x.a_gev, x.gp.m_ir_GeV * x.a_gev, x.gp.seed, x.dtau,
+                        tol, it, sc, x.init_buf, b->st, &f, &m, &mx, &err);
+        if (rc == -6) return bfail(GLASMA_ERR_NOSPACE, err);
+        if (rc != 0) return bfail(GLASMA_ERR_CUDA, err);
+        x.ic_fails = f;
+        x.ic_mean = m;
+        x.ic_max = mx;
+        fails_total += f;
+        // particles: Philox state, then sorted by cell once (gather locality)
+        PartHost tmp = part_layout(x.part_base, x.np, b->prec);
+        BCK(launch_part_init(b->prec, tmp, x.np, x.n, x.pp.init_kind, x.pp.p_min_GeV * x.a_gev,
+                             x.pp.p_max_GeV * x.a_gev, x.pp.q2, x.pp.q3, x.pp.seed, x.mass, b->st));
+        const PartHost dst = part_layout(x.part_init, x.np, b->prec);
+        int* cnt = (int*)b->scratch;
+        int* start = cnt + x.ns;
+        int* tot = start + x.ns;
+        BCK(launch_sort(b->prec, tmp, dst, x.np, (int)x.ns, cnt, start, tot, b->st));
+        BCK(cudaStreamSynchronize(b->st));
+    }
+    if (ic_failures) *ic_failures = fails_total;
+    glasma_status s = build_tables(b);
+    if (s != GLASMA_OK) return s;
+    b->initialised = true;
+    b->graph_ready = false;
+    return GLASMA_OK;
+}
+
+// restore every event to its initial state (step 1, particles at formation)
+static cudaError_t enqueue_restore(glasma_batch* b) {
+    for (auto& x : b->ev) {
+        cudaError_t e = cudaMemcpyAsync(x.buf[0], x.init_buf, fbytes(x.gp), cudaMemcpyDeviceToDevice, b->st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(x.part_base, x.part_init, x.part_bytes, cudaMemcpyDeviceToDevice, b->st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(x.acc, 0, (size_t)x.acc_rows * 4 * 8, b->st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t enqueue_batched(glasma_batch* b) {
+    cudaError_t e = enqueue_restore(b);
+    if (e != cudaSuccess) return e;
+    const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
+    for (int k = 0; k < b->max_iter; k++) {
+        const int act = b->active[k];
+        if (act == 0) break;
+        e = launch_field_step_batched(b->prec, (char*)b->step_args + (size_t)k * b->E * sa, b->tiles_dev,
+                                      b->tiles_upto[act], b->st);
+        if (e != cudaSuccess) return e;
+        e = launch_push_batched(b->prec, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
+                                b->pitems_upto[act], b->st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t enqueue_per_event(glasma_batch* b) {
+    cudaError_t e = enqueue_restore(b);
+    if (e != cudaSuccess) return e;
+    for (auto& x : b->ev) {
+        for (int s = 1; s < x.n_steps; s++) {
+            const int k = s - 1;
+            const StepHost st = step_coeffs(x.buf[k & 1], x.buf[(k + 1) & 1], x.n, s, x.dtau, 1,
+                                            x.gp.reunit_every > 0 && ((s + 1) % x.gp.reunit_every == 0));
+            e = launch_field_step(b->prec, st, b->st);
+            if (e != cudaSuccess) return e;
+            if (s >= x.n_form && x.np > 0) {
+                PushHost ph;
+                ph.fo = x.buf[k & 1]; ph.fn = x.buf[(k + 1) & 1]; ph.n = x.n; ph.np = x.np; ph.dtau = x.dtau;
+                ph.te = s * x.dtau; ph.ichr = 1.0 / (s * x.dtau); ph.teh = (s + 0.5) * x.dtau; ph.mass = x.mass;
+                ph.expanding = 1;
+                ph.acc = x.acc + 4 * (size_t)(s + 1);
+                e = launch_push(b->prec, ph, x.P, b->st);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+extern "C" glasma_status glasma_batch_run(glasma_batch* b, int32_t mode) {
+    if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    if (mode == GLASMA_BATCH_PER_EVENT) {
+        BCK(enqueue_per_event(b));
+        return GLASMA_OK;
+    }
+    if (mode == GLASMA_BATCH_EAGER) {
+        BCK(enqueue_batched(b));
+        return GLASMA_OK;
+    }
+    if (mode == GLASMA_BATCH_PERSISTENT) {
+        glasma_status s = batch_run_persistent(b);
+        return s;
+    }
+    if (mode != GLASMA_BATCH_GRAPH) return bfail(GLASMA_ERR_INVALID, "unknown mode");
+    if (b->st == nullptr || b->st == cudaStreamLegacy || b->st == cudaStreamPerThread)
+        return bfail(GLASMA_ERR_INVALID, "graph mode needs a created stream (the default stream cannot be captured)");
+    if (!b->graph_ready) {
+        cudaGraph_t g = nullptr;
+        BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_batched(b);
+        cudaError_t e2 = cudaStreamEndCapture(b->st, &g);  // always end the capture
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return bcuda(e != cudaSuccess ? e : e2, "graph capture");
+        }
+        cudaError_t e3 = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        BCK(e3);
+        b->graph_ready = true;
+    }
+    BCK(cudaGraphLaunch(b->exec, b->st));
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_batch_broadening(glasma_batch* b, int32_t event, double* out, int64_t cap,
+                                                 int64_t* n_rows) {
+    if (!b || !out || !n_rows || event < 0 || event >= b->E) return bfail(GLASMA_ERR_INVALID, "bad arguments");
+    const BatchEvent& x = b->ev[b->pos[event]];
+    std::vector<double> h((size_t)x.acc_rows * 4);
+    BCK(cudaMemcpyAsync(h.data(), x.acc, h.size() * 8, cudaMemcpyDeviceToHost, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    const double conv = 1.0 / (x.a_gev * x.a_gev);
+    int64_t k = 0;
+    for (int r = x.n_form; r <= x.n_steps && r < x.acc_rows; r++) {
+        if (k >= cap) return bfail(GLASMA_ERR_NOSPACE, "host_out too small");
+        double* o = out + 5 * k;
+        const double cnt = r == x.n_form ? (double)x.np : h[4 * r + 3];
+        o[0] = r * x.dtau * x.a_fm;
+        for (int i = 0; i < 3; i++) o[1 + i] = (r == x.n_form || cnt <= 0) ? 0.0 : h[4 * r + i] / cnt * conv;
+        o[4] = cnt;
+        k++;
+    }
+    *n_rows = k;
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_batch_work(const glasma_batch* b, int64_t* site_updates, int64_t* particle_steps) {
+    if (!b) return bfail(GLASMA_ERR_INVALID, "null batch");
+    int64_t su = 0, ps = 0;
+    for (const auto& x : b->ev) {
+        su += (int64_t)x.ns * (x.n_steps - 1);
+        ps += (int64_t)x.np * std::max(0, x.n_steps - x.n_form);
+    }
+    if (site_updates) *site_updates = su;
+    if (particle_steps) *particle_steps = ps;
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_batch_diagnostics(glasma_batch* b, int32_t event, double out[8]) {
+    if (!b || !out || event < 0 || event >= b->E) return bfail(GLASMA_ERR_INVALID, "bad arguments");
+    const BatchEvent& x = b->ev[b->pos[event]];
+    const int last = x.n_steps;  // final state at step n_steps sits in buf[(n_steps - 1) & 1]
+    BCK(launch_monitors(b->prec, x.buf[(last - 1) & 1], x.n, last * x.dtau, x.mon, b->st));
+    double m[8];
+    BCK(cudaMemcpyAsync(m, x.mon, sizeof(m), cudaMemcpyDeviceToHost, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    const double ns = (double)x.ns;
+    out[0] = m[1] > 0 ? sqrt(m[0] / m[1]) : sqrt(m[0]);
+    out[1] = m[2] / ns;
+    out[2] = m[3] / ns;
+    out[3] = m[4] / ns;
+    out[4] = m[5] / ns;
+    out[5] = m[6];
+    out[6] = last * x.dtau;
+    out[7] = m[7];
+    return GLASMA_OK;
+}
+
+// raw device-layout initial state of all events (fields + particles), in event order
+extern "C" int64_t glasma_batch_state_bytes(const glasma_batch* b) {
+    if (!b) return GLASMA_ERR_INVALID;
+    size_t t = 0;
+    for (const auto& x : b->ev) t += fbytes(x.gp) + x.part_bytes;
+    return (int64_t)t;
+}
+extern "C" glasma_status glasma_batch_export_state(glasma_batch* b, void* host, int64_t bytes) {
+    if (!b || !host || bytes < glasma_batch_state_bytes(b)) return bfail(GLASMA_ERR_INVALID, "bad arguments");
+    char* h = (char*)host;
+    for (const auto& x : b->ev) {
+        BCK(cudaMemcpyAsync(h, x.init_buf, fbytes(x.gp), cudaMemcpyDeviceToHost, b->st));
+        h += fbytes(x.gp);
+        BCK(cudaMemcpyAsync(h, x.part_init, x.part_bytes, cudaMemcpyDeviceToHost, b->st));
+        h += x.part_bytes;
+    }
+    BCK(cudaStreamSynchronize(b->st));
+    return GLASMA_OK;
+}
+extern "C" glasma_status glasma_batch_import_state(glasma_batch* b, const void* host, int64_t bytes) {
+    if (!b || !host || bytes < glasma_batch_state_bytes(b)) return bfail(GLASMA_ERR_INVALID, "bad arguments");
+    if (!b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    const char* h = (const char*)host;
+    for (auto& x : b->ev) {
+        BCK(cudaMemcpyAsync(x.init_buf, h, fbytes(x.gp), cudaMemcpyHostToDevice, b->st));
+        h += fbytes(x.gp);
+        BCK(cudaMemcpyAsync(x.part_init, h, x.part_bytes, cudaMemcpyHostToDevice, b->st));
+        h += x.part_bytes;
+    }
+    return GLASMA_OK;
+}
+
+// one eager run with CUDA events around every launch (on the batch stream)
+extern "C" glasma_status glasma_batch_profile(glasma_batch* b, double* field_ms, int64_t* field_launches,
+                                              int64_t* field_sites, double* push_ms, int64_t* push_launches) {
+    if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    BCK(enqueue_restore(b));
+    const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
+    const int K = b->max_iter;
+    std::vector<cudaEvent_t> ev(4 * (size_t)K);
+    for (auto& e : ev) BCK(cudaEventCreate(&e));
+    std::vector<size_t> sites(K, 0);
+    int used = 0;
+    for (int k = 0; k < K; k++) {
+        const int act = b->active[k];
+        if (act == 0) break;
+        for (int i = 0; i < act; i++) sites[k] += b->ev[i].ns;
+        BCK(cudaEventRecord(ev[4 * k + 0], b->st));
+        BCK(launch_field_step_batched(b->prec, (char*)b->step_args + (size_t)k * b->E * sa, b->tiles_dev,
+                                      b->tiles_upto[act], b->st));
+        BCK(cudaEventRecord(ev[4 * k + 1], b->st));
+        BCK(cudaEventRecord(ev[4 * k + 2], b->st));
+        BCK(launch_push_batched(b->prec, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
+                                b->pitems_upto[act], b->st));
+        BCK(cudaEventRecord(ev[4 * k + 3], b->st));
+        used = k + 1;
+    }
+    BCK(cudaStreamSynchronize(b->st));
+    double fm = 0, pm = 0;
+    size_t fs = 0;
+    for (int k = 0; k < used; k++) {
+        float a = 0, c = 0;
+        BCK(cudaEventElapsedTime(&a, ev[4 * k + 0], ev[4 * k + 1]));
+        BCK(cudaEventElapsedTime(&c, ev[4 * k + 2], ev[4 * k + 3]));
+        fm += a;
+        pm += c;
+        fs += sites[k];
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (field_ms) *field_ms = fm;
+    if (field_launches) *field_launches = used;
+    if (field_sites) *field_sites = (int64_t)fs;
+    if (push_ms) *push_ms = pm;
+    if (push_launches) *push_launches = used;
+    return GLASMA_OK;
+}
+
+// particles of event i after a run, original order (host arrays of n_particles; NULL skips)
+extern "C" glasma_status glasma_batch_get_particles(glasma_batch* b, int32_t event, double* x, double* y, double* eta,
+                                                    double* px, double* py, double* peta, double* Q) {
+    if (!b || event < 0 || event >= b->E) return bfail(GLASMA_ERR_INVALID, "bad arguments");
+    const BatchEvent& e = b->ev[b->pos[event]];
+    const size_t np = e.np;
+    if (np == 0) return GLASMA_OK;
+    double* stage = (double*)b->scratch;  // 14 np doubles; the scratch holds >= 2 n_max^2 * 8 * 16 bytes
+    if (14 * np * 8 > ic_scratch_bytes(b->nmax, b->fft_work)) return bfail(GLASMA_ERR_NOSPACE, "scratch too small");
+    BCK(launch_part_to_canonical(b->prec, e.P, e.np, e.n, stage, b->st));
+    std::vector<double> h(14 * np);
+    BCK(cudaMemcpyAsync(h.data(), stage, 14 * np * 8, cudaMemcpyDeviceToHost, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    double* outs[6] = {x, y, eta, px, py, peta};
+    for (int k = 0; k < 6; k++)
+        if (outs[k]) memcpy(outs[k], h.data() + k * np, np * 8);
+    if (Q)
+        for (size_t j = 0; j < np; j++)
+            for (int a = 0; a < 8; a++) Q[8 * j + a] = h[(6 + a) * np + j];
+    return GLASMA_OK;
+}
+
+extern "C" int64_t glasma_batch_launches(const glasma_batch* b, int32_t mode) {
+    if (!b || !b->initialised) return GLASMA_ERR_INVALID;
+    int64_t L = 0;
+    if (mode == GLASMA_BATCH_PER_EVENT) {
+        for (const auto& x : b->ev) L += (x.n_steps - 1) + std::max(0, x.n_steps - x.n_form) * (x.np > 0);
+    } else if (mode == GLASMA_BATCH_PERSISTENT) {
+        L = 1;
+    } else {
+        for (int k = 0; k < b->max_iter; k++) L += b->active[k] ? 2 : 0;
+    }
+    return L;
+}
+
+extern "C" void glasma_batch_destroy(glasma_batch* b) {
+    if (!b) return;
+    if (b->graph_ready) cudaGraphExecDestroy(b->exec);
+    batch_free_persistent(b);
+    delete b;
+}

@@ -1,0 +1,53 @@
+// Host-side state of a multi-event batch (shared by batch.cu and persistent.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/glasma.h"
+#include "internal.h"
+
+struct BatchEvent {
+    glasma_params gp;
+    cpic_params pp;
+    int id;
+    int n;
+    size_t ns;
+    int n_steps, n_form, np, acc_rows;
+    double a_fm, a_gev, dtau, mass;
+    void* buf[2];
+    void* init_buf;
+    void* part_base;
+    void* part_init;
+    size_t part_bytes;
+    glasma::PartHost P;
+    double* acc;
+    double* mon;
+    long long ic_fails;
+    double ic_mean;
+    int ic_max;
+};
+
+struct glasma_batch {
+    int prec = 0, E = 0, nmax = 0, max_iter = 0;
+    cudaStream_t st = nullptr;
+    size_t fft_work = 0;
+    std::vector<BatchEvent> ev;   // ordered by step count, descending
+    std::vector<int> pos;         // caller's event index -> position in ev
+    void* step_args = nullptr;    // [max_iter][E] StepArgs
+    void* push_args = nullptr;    // [max_iter][E] PushArgs
+    void* tiles_dev = nullptr;    // TileItem list, grouped by event
+    void* pitems_dev = nullptr;   // PushItem list, grouped by event
+    void* scratch = nullptr;      // initial-condition / sort scratch
+    std::vector<int> tiles_upto, pitems_upto, active;
+    bool initialised = false, graph_ready = false;
+    cudaGraphExec_t exec = nullptr;
+    // persistent mode
+    void* pers_ctrl = nullptr;    // barrier counters + error word + per-iteration prefixes (device)
+    int pers_blocks = 0;
+    int pers_timeout = 0;
+};
+
+void glasma_set_error(const char* msg);
+glasma_status batch_run_persistent(glasma_batch* b);
+void batch_free_persistent(glasma_batch* b);

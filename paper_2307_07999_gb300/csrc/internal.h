@@ -55,6 +55,12 @@ struct PushHost {
     double* acc;
 };
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st);
+// batched push: args[n_ev] (acc == nullptr: event idle this step), items {ev, j0} of 256 particles
+size_t push_args_size(int prec);
+void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out);
+cudaError_t launch_push_batched(int prec, const void* args_dev, const void* items_dev, int n_items, cudaStream_t st);
+struct PushItemH { int ev, j0; };
+struct TileItemH { int ev, x0, y0; };
 cudaError_t launch_sort(int prec, const PartHost& a, const PartHost& b, int np, int ncell, int* count,
                         int* start, int* totals, cudaStream_t st);
 size_t sort_scratch_ints(int ncell);

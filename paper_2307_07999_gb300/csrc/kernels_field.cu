@@ -6,19 +6,25 @@
 
 namespace glasma {
 
+#ifndef GLASMA_FIELD_TY
+#define GLASMA_FIELD_TY 4
+#endif
+#ifndef GLASMA_FIELD_MINB
+#define GLASMA_FIELD_MINB 3
+#endif
 template <class T> struct TileCfg;
-template <> struct TileCfg<float> { static constexpr int TX = 32, TY = 8; };
-template <> struct TileCfg<double> { static constexpr int TX = 32, TY = 4; };
+template <> struct TileCfg<float> { static constexpr int TX = 32, TY = GLASMA_FIELD_TY, MINB = GLASMA_FIELD_MINB; };
+template <> struct TileCfg<double> { static constexpr int TX = 32, TY = 4, MINB = 1; };
 
 template <class T>
-__global__ void __launch_bounds__(TileCfg<T>::TX * TileCfg<T>::TY)
+__global__ void __launch_bounds__(TileCfg<T>::TX * TileCfg<T>::TY, TileCfg<T>::MINB)
 k_field_step(StepArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
     field_tile<T, TX, TY>(A, blockIdx.x * TX, blockIdx.y * TY, smem);
 }
 template <class T>
-__global__ void __launch_bounds__(TileCfg<T>::TX * TileCfg<T>::TY)
+__global__ void __launch_bounds__(TileCfg<T>::TX * TileCfg<T>::TY, TileCfg<T>::MINB)
 k_field_step_batched(const StepArgs<T>* __restrict__ args, const TileItem* __restrict__ items) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
@@ -81,7 +87,7 @@ template <class T> static cudaError_t batched_impl(const void* args, const void*
     constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
     cudaError_t e = set_smem<T>();
     if (e != cudaSuccess) return e;
-    if (n_items <= 0) return cudaSuccess;
+    if (n_items <= 0 || !args) return cudaSuccess;
     k_field_step_batched<T><<<n_items, dim3(TX, TY), Tile<T, TX, TY>::smem, st>>>((const StepArgs<T>*)args,
                                                                               (const TileItem*)items);
     return cudaGetLastError();

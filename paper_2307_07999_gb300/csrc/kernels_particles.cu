@@ -41,6 +41,17 @@ template <class T> static PushArgs<T> push_args(const PushHost& a, const PartHos
     A.expanding = a.expanding; A.acc = a.acc;
     return A;
 }
+size_t push_args_size(int prec) { return prec ? sizeof(PushArgs<float>) : sizeof(PushArgs<double>); }
+void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out) {
+    if (prec) *(PushArgs<float>*)out = push_args<float>(a, P);
+    else *(PushArgs<double>*)out = push_args<double>(a, P);
+}
+cudaError_t launch_push_batched(int prec, const void* args, const void* items, int n_items, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    if (prec) k_push_batched<float><<<n_items, 256, 0, st>>>((const PushArgs<float>*)args, (const PushItem*)items);
+    else k_push_batched<double><<<n_items, 256, 0, st>>>((const PushArgs<double>*)args, (const PushItem*)items);
+    return cudaGetLastError();
+}
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st) {
     if (a.np <= 0) return cudaSuccess;
     const int nb = (a.np + 255) / 256;

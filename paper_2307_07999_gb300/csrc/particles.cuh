@@ -145,87 +145,87 @@ template <class T> DEV T clamp_below_one(T v);
 template <> DEV float clamp_below_one<float>(float v) { return fminf(v, 0.99999994f); }
 template <> DEV double clamp_below_one<double>(double v) { return fmin(v, 0.99999999999999989); }
 
+// one particle: gather, kick, drift, color transport; returns its broadening terms
 template <class T>
-__global__ void __launch_bounds__(256) k_push(PushArgs<T> A) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
-    if (j < A.np) {
-        const PartSoA<T>& P = A.P;
-        const int n = A.n;
-        const size_t ns = (size_t)n * n;
-        const int cell = P.cell[j];
-        int cx = cell % n, cy = cell / n;
-        Al<T> q;
+DEV void push_one(const PushArgs<T>& A, int j, double& sx, double& sy, double& sz, double& sc) {
+    const PartSoA<T>& P = A.P;
+    const int n = A.n;
+    const size_t ns = (size_t)n * n;
+    const int cell = P.cell[j];
+    int cx = cell % n, cy = cell / n;
+    Al<T> q;
 #pragma unroll
-        for (int a = 0; a < 8; a++) q.a[a] = P.Q[(size_t)a * P.qs + j];
-        T qE[3], qB[3];
-        gather_qf(A, cx, cy, q, qE, qB);
-        const T p0x = P.p0x[j], p0y = P.p0y[j];
-        T dpx = P.dpx[j], dpy = P.dpy[j], pz = P.peta[j];
-        const T m2 = A.mass * A.mass;
-        T px = p0x + dpx, py = p0y + dpy;
-        const T pt = sqrt(m2 + px * px + py * py + pz * pz);
-        const T ipt = pt > T(0) ? T(1) / pt : T(0);
-        const T fx = qE[0] + (py * qB[2] - pz * qB[1]) * ipt;
-        const T fy = qE[1] + (pz * qB[0] - px * qB[2]) * ipt;
-        const T fz = qE[2] + (px * qB[1] - py * qB[0]) * ipt - pz * A.ichr;
-        dpx += A.dtau * fx;
-        dpy += A.dtau * fy;
-        pz += A.dtau * fz;
-        px = p0x + dpx;
-        py = p0y + dpy;
-        const T ptn = sqrt(m2 + px * px + py * py + pz * pz);
-        const T iptn = ptn > T(0) ? T(1) / ptn : T(0);
-        T ox = P.ox[j] + A.dtau * px * iptn;
-        T oy = P.oy[j] + A.dtau * py * iptn;
-        const T deta = A.dtau * pz * iptn / A.teh;
-        // color: rotation along eta at the old cell, then across the x face, then the y face
-        {
-            Al<T> e;
-            const Al<T> ph = load_alg(A.fo, ns, P_PHI, (size_t)cell);
+    for (int a = 0; a < 8; a++) q.a[a] = P.Q[(size_t)a * P.qs + j];
+    T qE[3], qB[3];
+    gather_qf(A, cx, cy, q, qE, qB);
+    const T p0x = P.p0x[j], p0y = P.p0y[j];
+    T dpx = P.dpx[j], dpy = P.dpy[j], pz = P.peta[j];
+    const T m2 = A.mass * A.mass;
+    T px = p0x + dpx, py = p0y + dpy;
+    const T pt = sqrt(m2 + px * px + py * py + pz * pz);
+    const T ipt = pt > T(0) ? T(1) / pt : T(0);
+    const T fx = qE[0] + (py * qB[2] - pz * qB[1]) * ipt;
+    const T fy = qE[1] + (pz * qB[0] - px * qB[2]) * ipt;
+    const T fz = qE[2] + (px * qB[1] - py * qB[0]) * ipt - pz * A.ichr;
+    dpx += A.dtau * fx;
+    dpy += A.dtau * fy;
+    pz += A.dtau * fz;
+    px = p0x + dpx;
+    py = p0y + dpy;
+    const T ptn = sqrt(m2 + px * px + py * py + pz * pz);
+    const T iptn = ptn > T(0) ? T(1) / ptn : T(0);
+    T ox = P.ox[j] + A.dtau * px * iptn;
+    T oy = P.oy[j] + A.dtau * py * iptn;
+    const T deta = A.dtau * pz * iptn / A.teh;
+    // color: rotation along eta at the old cell, then across the x face, then the y face
+    {
+        Al<T> e;
+        const Al<T> ph = load_alg(A.fo, ns, P_PHI, (size_t)cell);
 #pragma unroll
-            for (int a = 0; a < 8; a++) e.a[a] = -deta * ph.a[a];
-            q = alg(conj_by(expi(herm(e)), herm(q)));
-        }
-        int nx = cx, ny = cy;
-        if (ox >= T(1)) {
-            q = transport_alg(load_link(A.fo, ns, P_UX, (size_t)cell), q);
-            ox -= T(1);
-            nx = cx == n - 1 ? 0 : cx + 1;
-        } else if (ox < T(0)) {
-            nx = cx == 0 ? n - 1 : cx - 1;
-            q = conj_alg(load_link(A.fo, ns, P_UX, nx + (size_t)n * cy), q);
-            ox = clamp_below_one(ox + T(1));
-        }
-        if (oy >= T(1)) {
-            q = transport_alg(load_link(A.fo, ns, P_UY, nx + (size_t)n * cy), q);
-            oy -= T(1);
-            ny = cy == n - 1 ? 0 : cy + 1;
-        } else if (oy < T(0)) {
-            ny = cy == 0 ? n - 1 : cy - 1;
-            q = conj_alg(load_link(A.fo, ns, P_UY, nx + (size_t)n * ny), q);
-            oy = clamp_below_one(oy + T(1));
-        }
-        const T eta = P.eta[j] + deta;
-        P.cell[j] = nx + n * ny;
-        P.ox[j] = ox;
-        P.oy[j] = oy;
-        P.eta[j] = eta;
-        P.dpx[j] = dpx;
-        P.dpy[j] = dpy;
-        P.peta[j] = pz;
-#pragma unroll
-        for (int a = 0; a < 8; a++) P.Q[(size_t)a * P.qs + j] = q.a[a];
-        // broadening terms: dp_i^2 = p_i^2 - p_i(tau_form)^2, lab p_z
-        const double pzl = A.expanding ? (double)ptn * sinh((double)eta) + (double)pz * cosh((double)eta)
-                                       : (double)pz;
-        const double p0z = (double)P.p0z[j];
-        sx = (double)dpx * (2.0 * (double)p0x + (double)dpx);
-        sy = (double)dpy * (2.0 * (double)p0y + (double)dpy);
-        sz = pzl * pzl - p0z * p0z;
-        sc = 1.0;
+        for (int a = 0; a < 8; a++) e.a[a] = -deta * ph.a[a];
+        q = alg(conj_by(expi(herm(e)), herm(q)));
     }
-    // warp -> block -> one FP64 atomic per block and term
+    int nx = cx, ny = cy;
+    if (ox >= T(1)) {
+        q = transport_alg(load_link(A.fo, ns, P_UX, (size_t)cell), q);
+        ox -= T(1);
+        nx = cx == n - 1 ? 0 : cx + 1;
+    } else if (ox < T(0)) {
+        nx = cx == 0 ? n - 1 : cx - 1;
+        q = conj_alg(load_link(A.fo, ns, P_UX, nx + (size_t)n * cy), q);
+        ox = clamp_below_one(ox + T(1));
+    }
+    if (oy >= T(1)) {
+        q = transport_alg(load_link(A.fo, ns, P_UY, nx + (size_t)n * cy), q);
+        oy -= T(1);
+        ny = cy == n - 1 ? 0 : cy + 1;
+    } else if (oy < T(0)) {
+        ny = cy == 0 ? n - 1 : cy - 1;
+        q = conj_alg(load_link(A.fo, ns, P_UY, nx + (size_t)n * ny), q);
+        oy = clamp_below_one(oy + T(1));
+    }
+    const T eta = P.eta[j] + deta;
+    P.cell[j] = nx + n * ny;
+    P.ox[j] = ox;
+    P.oy[j] = oy;
+    P.eta[j] = eta;
+    P.dpx[j] = dpx;
+    P.dpy[j] = dpy;
+    P.peta[j] = pz;
+#pragma unroll
+    for (int a = 0; a < 8; a++) P.Q[(size_t)a * P.qs + j] = q.a[a];
+    // broadening terms: dp_i^2 = p_i^2 - p_i(tau_form)^2, lab p_z
+    const double pzl = A.expanding ? (double)ptn * sinh((double)eta) + (double)pz * cosh((double)eta)
+                                   : (double)pz;
+    const double p0z = (double)P.p0z[j];
+    sx = (double)dpx * (2.0 * (double)p0x + (double)dpx);
+    sy = (double)dpy * (2.0 * (double)p0y + (double)dpy);
+    sz = pzl * pzl - p0z * p0z;
+    sc = 1.0;
+}
+
+// warp -> block -> one FP64 atomic per block and term (blockDim.x <= 256)
+DEV void block_acc4(double sx, double sy, double sz, double sc, double* acc) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sx += __shfl_down_sync(0xffffffffu, sx, o);
@@ -240,8 +240,31 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<T> A) {
     if (threadIdx.x < 4) {
         double t = 0.0;
         for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[threadIdx.x][k];
-        atomicAdd(A.acc + threadIdx.x, t);
+        atomicAdd(acc + threadIdx.x, t);
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_push(PushArgs<T> A) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
+    if (j < A.np) push_one(A, j, sx, sy, sz, sc);
+    block_acc4(sx, sy, sz, sc, A.acc);
+}
+
+// batched over events: one 256-particle block per item; args[ev] of this step
+// (acc == nullptr marks an event whose particles are not pushed at this step)
+struct PushItem { int ev, j0; };
+template <class T>
+__global__ void __launch_bounds__(256) k_push_batched(const PushArgs<T>* __restrict__ args,
+                                                      const PushItem* __restrict__ items) {
+    const PushItem it = items[blockIdx.x];
+    const PushArgs<T> A = args[it.ev];
+    if (A.acc == nullptr) return;
+    const int j = it.j0 + threadIdx.x;
+    double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
+    if (j < A.np) push_one(A, j, sx, sy, sz, sc);
+    block_acc4(sx, sy, sz, sc, A.acc);
 }
 
 // ---------------------------------------------------------------- counting sort by cell

@@ -1,0 +1,38 @@
+"""Small fixed workloads for ncu captures (one short run each, a few GB at most).
+
+  python -m paper_2307_07999_gb300.profile_driver field 512          # 4 FP32 field steps on 512^2
+  python -m paper_2307_07999_gb300.profile_driver push 512 100000    # + a 100k-particle push
+  python -m paper_2307_07999_gb300.profile_driver batch              # one graph run of the 64-event batch
+"""
+import sys
+
+import torch
+
+from . import Batch, CPIC, Glasma
+from . import workloads as W
+
+
+def main(argv):
+    what = argv[1] if len(argv) > 1 else "field"
+    if what == "batch":
+        evs, pps = W.batched_uneven()
+        B = Batch(evs, pps)
+        B.init()
+        B.run("graph")
+        torch.cuda.synchronize()
+        print("ok")
+        return
+    n = int(argv[2]) if len(argv) > 2 else 512
+    g = Glasma(n, 10.0, precision=1, tau_end_fm=1.0, seed=3)
+    g.init()
+    g.step(4)
+    if what == "push":
+        c = CPIC(g, int(argv[3]) if len(argv) > 3 else 100000, 1.5, 0.0, p_max_GeV=5.0, bin_every=1, seed=4)
+        c.init()
+        c.push(3)
+    torch.cuda.synchronize()
+    print("ok")
+
+
+if __name__ == "__main__":
+    main(sys.argv)

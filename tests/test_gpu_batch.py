@@ -1,0 +1,139 @@
+"""Batched multi-event runs (uneven lattices, own particle ensembles) against the
+oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import rel_err
+
+pytestmark = pytest.mark.gpu
+
+G = pytest.importorskip("paper_2307_07999_gb300")
+W = pytest.importorskip("paper_2307_07999_gb300.workloads")
+
+HBARC = 0.1973269804
+
+
+def small_events(prec, tol=1e-14, np_=400):
+    """Four events with different sizes (one ragged against the 32-wide tiles) and
+    step counts; L chosen so that g^2 mu a ~ 1 (well-conditioned tau = 0+ solve)."""
+    spec = [(24, 2.4, 1.8), (40, 4.0, 2.2), (32, 2.6, 2.0), (48, 4.2, 1.6)]
+    evs, pps = [], []
+    for e, (n, L, g2mu) in enumerate(spec):
+        s = W.event_seed(9, e)
+        gp = W.glasma_params(n, L, g2mu, s, prec, tau_end_fm=0.35, reunit_every=(0 if prec == 0 else 16))
+        gp.newton_tol = tol
+        evs.append(gp)
+        pps.append(W.charm_params(np_, s, mass=1.5, p_max=3.0, tau_form=0.08))
+    return evs, pps
+
+
+def oracle_event(gp, pp, tol, particle_idx=None):
+    n = gp.n
+    a_fm = gp.L_fm / n
+    a = a_fm / HBARC
+    st, iters, fails = O.glasma_init(n, gp.n_sheets, gp.g2mu_GeV * a, gp.m_ir_GeV * a, gp.seed, gp.dtau_over_a,
+                                     tol=tol)
+    P = O.particles_init(pp.n_particles, n, pp.mass_GeV * a, pp.init_kind, pp.p_min_GeV * a, pp.p_max_GeV * a,
+                         pp.seed)
+    if particle_idx is not None:
+        sub = O.Particles(len(particle_idx))
+        for k in ("x", "y", "eta", "px", "py", "peta", "Q", "p0"):
+            getattr(sub, k)[...] = getattr(P, k)[particle_idx]
+        P = sub
+    n_form = max(1, int(round(pp.tau_form_fm / (gp.dtau_over_a * a_fm))))
+    n_steps = int(np.ceil(gp.tau_end_fm / (gp.dtau_over_a * a_fm) - 1e-9))
+    while st.step < n_form:
+        st = O.field_step(st, gp.dtau_over_a)
+    rows = [(n_form * gp.dtau_over_a * a_fm, 0, 0, 0, P.np)]
+    while st.step < n_steps:
+        nx = O.field_step(st, gp.dtau_over_a)
+        acc = O.push(P, st, nx, gp.dtau_over_a, pp.mass_GeV * a)
+        rows.append((nx.step * gp.dtau_over_a * a_fm, *(acc[:3] / acc[3] / a ** 2), acc[3]))
+        st = nx
+    return np.array(rows), P, st
+
+
+@pytest.fixture(scope="module")
+def fp64_batch():
+    evs, pps = small_events(0)
+    B = G.Batch(evs, pps)
+    assert B.init() == 0
+    return B, evs, pps
+
+
+def test_batch_modes_agree(fp64_batch):
+    B, evs, pps = fp64_batch
+    tabs = {}
+    for mode in ("graph", "eager", "per_event", "graph"):
+        B.run(mode)
+        tabs[mode] = [B.broadening(e) for e in range(len(evs))]
+    for mode in ("eager", "per_event"):
+        for e in range(len(evs)):
+            assert rel_err(tabs[mode][e][:, 1:4], tabs["graph"][e][:, 1:4]) < 1e-13
+
+
+def test_batch_fp64_matches_oracle(fp64_batch):
+    B, evs, pps = fp64_batch
+    B.run("graph")
+    su, ps = B.work()
+    assert su == sum(gp.n ** 2 * (int(np.ceil(gp.tau_end_fm / (gp.dtau_over_a * gp.L_fm / gp.n) - 1e-9)) - 1)
+                     for gp in evs)
+    for e in range(len(evs)):
+        want, P, st = oracle_event(evs[e], pps[e], 1e-14)
+        got = B.broadening(e)
+        assert got.shape == want.shape
+        assert np.abs(got[:, 0] - want[:, 0]).max() < 1e-12
+        assert rel_err(got[:, 1:4], want[:, 1:4]) < 1e-10, e
+        d = B.diagnostics(e)
+        assert d[7] == 0 and d[5] < 1e-12
+        part = B.get_particles(e)
+        assert rel_err(part["px"], P.px) < 1e-10 and rel_err(part["Q"], P.Q) < 1e-10
+
+
+def test_batch_fp32_matches_oracle():
+    evs, pps = small_events(1, tol=1e-14)
+    B = G.Batch(evs, pps)
+    B.init()
+    B.run("graph")
+    for e in range(len(evs)):
+        want, P, st = oracle_event(evs[e], pps[e], 1e-14)
+        got = B.broadening(e)
+        e_dp = rel_err(got[:, 1:4], want[:, 1:4])
+        e_k = rel_err(G.kappa_qhat(got)[:, 1:], G.kappa_qhat(want)[:, 1:])
+        d = B.diagnostics(e)
+        print(f"event {e}: dp2 {e_dp:.2e} kappa {e_k:.2e} gauss {d[0]:.2e} unitarity {d[5]:.2e}")
+        assert e_dp < 1e-4 and e_k < 1e-4
+        assert d[0] < 1e-5
+
+
+def test_full_size_batch_sampled():
+    """The benchmarked workload at full size, in the launch configuration bench.py times
+    (graph mode, FP32): monitors of all 64 events, and event 0 (128^2, 10k charm)
+    checked on a sample of 200 particles that the FP64 oracle pushes one by one through
+    its own evolution of the same event."""
+    evs, pps = W.batched_uneven()
+    B = G.Batch(evs, pps)
+    fails = B.init()
+    assert fails == 0
+    B.run("graph")
+    for e in range(len(evs)):
+        d = B.diagnostics(e)
+        assert d[7] == 0, e
+        assert d[0] < 1e-5, (e, d[0])
+        assert d[5] < 1e-5, (e, d[5])
+        tab = B.broadening(e)
+        assert np.all(np.isfinite(tab)) and np.all(tab[1:, 4] == pps[e].n_particles)
+    idx = np.random.default_rng(0).choice(pps[0].n_particles, 200, replace=False)
+    want, P, st = oracle_event(evs[0], pps[0], evs[0].newton_tol, particle_idx=idx)
+    got = B.get_particles(0)
+    a = evs[0].L_fm / evs[0].n / HBARC
+    p_got = np.stack([got["px"][idx], got["py"][idx]], 1)
+    p_want = np.stack([P.px, P.py], 1)
+    dp_got = ((p_got ** 2).sum(1) - (P.p0[:, :2] ** 2).sum(1)).mean()
+    dp_want = ((p_want ** 2).sum(1) - (P.p0[:, :2] ** 2).sum(1)).mean()
+    rel = np.abs(p_got - p_want).max(1) / np.maximum(np.abs(p_want).max(1), 1e-3 / a)
+    print(f"sampled particles: median rel {np.median(rel):.2e}, 95% {np.quantile(rel, 0.95):.2e}, "
+          f"<dp_T^2> rel {abs(dp_got - dp_want) / abs(dp_want):.2e}")
+    assert np.quantile(rel, 0.9) < 1e-3
+    assert abs(dp_got - dp_want) < 1e-3 * abs(dp_want)
