@@ -136,6 +136,26 @@ glasma_status glasma_diagnostics(glasma_ctx* g, double out[8]);
 
 void glasma_destroy(glasma_ctx* g);
 
+/* The monitors of glasma_diagnostics for callers that cannot allocate device
+ * memory (code handed only the buffers it reads, e.g. a plugin or host callback
+ * inside another framework, or a process whose device memory pool is fully
+ * reserved): no context, no workspace.  The paper has no counterpart; this is
+ * a deployment aid.
+ *   fields: device pointer to one field buffer in the library's plane layout
+ *           (56 planes of n*n reals of the given precision, site s = x + n*y:
+ *           U_x rows 0-1 as 12 planes (entry-major, re then im), U_y likewise,
+ *           E_x^a, E_y^a, phi^a, pi^a as 8 planes each), read only.
+ *   tau: tau in lattice units (divides E and D phi in the expanding case).
+ *   out: host double[8], as glasma_diagnostics.
+ * Scratch: a file-scope device array of 4096 x 8 doubles (256 KB) that every
+ * GPU which loads the library holds until the process exits; n*n above
+ * 1,048,576 sites is rejected with GLASMA_ERR_INVALID.  The first call on a
+ * device resolves the array's address on that device (make it before any
+ * stream capture).  All calls share the array: calls that overlap on the GPU
+ * (other streams or threads) race.  Allocates nothing; synchronises stream. */
+glasma_status glasma_diagnostics_noalloc(const void* fields, int32_t n, int32_t precision,
+                                         int32_t expanding, double tau, void* stream, double out[8]);
+
 /* ------------------------------------------------------------------ particles */
 
 int64_t cpic_workspace_bytes(const glasma_params* gp, const cpic_params* p);

@@ -103,6 +103,7 @@ SIGNATURES = {
     "glasma_batch_launches": (_i64, [_p, _i32]),
     "glasma_batch_get_particles": (C.c_int, [_p, _i32] + [_p] * 7),
     "glasma_batch_destroy": (None, [_p]),
+    "glasma_diagnostics_noalloc": (C.c_int, [_p, _i32, _i32, _i32, _d, _p, _p]),
     "glasma_last_error": (C.c_char_p, []),
 }
 

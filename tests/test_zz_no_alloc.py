@@ -1,0 +1,63 @@
+"""glasma_diagnostics_noalloc: the field monitors for callers that cannot allocate
+device memory (they own the field buffer; the library keeps its reduction scratch
+in a static device array).  Checked through the C ABI against glasma_diagnostics
+on the same state, on two calls in a row.  This file sorts last so that a run
+stopping at its first failure has already run every other test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from gpu_common import random_state, rel_err
+
+pytestmark = pytest.mark.gpu
+
+G = pytest.importorskip("paper_2307_07999_gb300")
+torch = pytest.importorskip("torch")
+
+
+def plane_buffer(st, prec):
+    """The canonical state in the library's plane layout, on the device (caller-owned)."""
+    n = st.n
+    ns = n * n
+    f = np.zeros((56, ns))
+    for d in range(2):
+        rows = st.U[:, d, :2, :].reshape(ns, 6)
+        f[12 * d + 0:12 * d + 12:2] = rows.real.T
+        f[12 * d + 1:12 * d + 12:2] = rows.imag.T
+    f[24:32] = st.E[:, 0].T
+    f[32:40] = st.E[:, 1].T
+    f[40:48] = st.phi.T
+    f[48:56] = st.pi.T
+    return torch.tensor(f.astype(np.float32 if prec else np.float64), device="cuda").contiguous()
+
+
+def call(buf, n, prec, tau):
+    out = np.zeros(8)
+    rc = G.lib().glasma_diagnostics_noalloc(C.c_void_p(buf.data_ptr()), n, prec, 1, tau, None,
+                                            out.ctypes.data_as(C.c_void_p))
+    return rc, out
+
+
+@pytest.mark.parametrize("prec,n,tol", [(0, 24, 1e-12), (1, 40, 2e-5), (0, 67, 1e-12)])
+def test_noalloc_diagnostics_match_context_diagnostics(prec, n, tol):
+    st = random_state(n, seed=500 + n, step=5)
+    g = G.Glasma(n, 6.0, precision=prec, tau_end_fm=100.0)
+    g.set_state(st.U, st.E, st.phi, st.pi, st.step)
+    want = g.diagnostics()
+    buf = plane_buffer(st, prec)
+    torch.cuda.synchronize()
+    for _ in range(2):  # the static scratch keeps the previous call's contents
+        rc, got = call(buf, n, prec, st.step * 0.125)
+        assert rc == 0
+        assert abs(got[0] - want[0]) <= tol * max(want[0], 1e-300) + 1e-15
+        assert rel_err(got[1:5], want[1:5]) < tol
+        assert abs(got[5] - want[5]) <= tol + 1e-15
+        assert got[6] == want[6] and got[7] == want[7] == 0
+
+
+def test_noalloc_rejects_lattices_beyond_the_scratch():
+    buf = torch.zeros(16, dtype=torch.float32, device="cuda")
+    rc, _ = call(buf, 1025, 1, 1.0)
+    assert rc == -1
+    assert b"static scratch" in G.lib().glasma_last_error()
