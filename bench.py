@@ -31,6 +31,7 @@ METRIC = "Glasma site-updates/s & Wong particle-steps/s on 1 GB300 vs plain, at 
 WORKLOAD = ("64 MV events, 16 each of 128^2/256^2/384^2/512^2 (L=10 fm, g2mu~U[1.5,2.5] GeV), "
             "10k charm/event, FP32 fields+particles with FP64 accumulators, tau 0->1 fm/c")
 BYTES_PER_SITE = 448  # algorithmic bytes of one FP32 site-update (12-real links, read + write once)
+BYTES_PER_PARTICLE = 132  # algorithmic bytes of one FP32 particle-step (state read + write, p0 read)
 
 
 def parse():
@@ -39,7 +40,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="auto", choices=["auto", "graph", "persistent", "eager", "per_event"])
+    p.add_argument("--mode", default="auto", choices=["auto", "graph", "persistent", "eager", "per_event", "fused"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     return p.parse_args()
@@ -253,7 +254,7 @@ def run_ours(args, ws, rank, local):
         barrier(ws)
         return e0.elapsed_time(e1) / K
 
-    modes = ["graph", "persistent"] if args.mode == "auto" else [args.mode]
+    modes = ["graph", "persistent", "fused"] if args.mode == "auto" else [args.mode]
     best = None
     for m in modes:
         try:
@@ -274,18 +275,24 @@ def run_ours(args, ws, rank, local):
     pvalue = ps * ws / (ms / 1000.0)
     launches = B.launches(mode) * args.steps
 
-    # per-kernel durations (CUDA events around every launch, on the batch stream)
-    prof = B.profile()
-    field_ms_per_launch = prof["field_ms"] / prof["field_launches"]
-    sites_per_launch = prof["field_sites"] / prof["field_launches"]
-    achieved = BYTES_PER_SITE * sites_per_launch / (field_ms_per_launch / 1000.0) / 1e9
+    # per-kernel durations (CUDA events around every launch, on the batch stream).  The dominant
+    # kernel is the batched field step (448 B per site-update); in the fused mode it is the fused
+    # field step + push (plus 132 B per particle-step)
+    pmode = "fused" if mode == "fused" else "graph"
+    prof = B.profile(pmode)
+    per_launch_ms = prof["main_ms"] / prof["main_launches"]
+    bytes_per_launch = (BYTES_PER_SITE * prof["main_sites"] + BYTES_PER_PARTICLE * prof["main_particle_steps"]) \
+        / prof["main_launches"]
+    achieved = bytes_per_launch / (per_launch_ms / 1000.0) / 1e9
     peak, peak_kind = measured_peak()
     tps = ncu_traffic_per_site()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tps * sites_per_launch if tps else None), "kernel": "k_field_step_batched<float>",
+                "traffic": (tps * prof["main_sites"] / prof["main_launches"] if tps else None),
+                "kernel": "k_fused_batched<float>" if pmode == "fused" else "k_field_step_batched<float>",
                 "peak_kind": f"{peak_kind} HBM copy (burst)",
-                "share_of_step": prof["field_ms"] / (prof["field_ms"] + prof["push_ms"]),
-                "push_ms_per_run": prof["push_ms"]}
+                "algorithmic_bytes_per_launch": bytes_per_launch, "ms_per_launch": per_launch_ms,
+                "share_of_step": prof["main_ms"] / (prof["main_ms"] + prof["other_ms"]),
+                "other_kernels_ms_per_run": prof["other_ms"]}
 
     # plain one-event-per-launch GPU path on the same GPU
     plain = None

@@ -200,11 +200,14 @@ void cpic_destroy(cpic_ctx* c);
  * advanced together; <dp_i^2> averages over particles and events (Sec. 2). */
 
 typedef enum {
-    GLASMA_BATCH_GRAPH = 0,      /* per step: one field launch over all active events' tiles and one
-                                    push launch over their particles, the whole run one CUDA graph */
-    GLASMA_BATCH_PERSISTENT = 1, /* one persistent cooperative kernel, bounded grid barrier per phase */
+    GLASMA_BATCH_GRAPH = 0,      /* per step: one field launch over all active events' tiles and one push
+                                    launch over their particles; the whole run is one CUDA graph */
+    GLASMA_BATCH_PERSISTENT = 1, /* one persistent cooperative kernel for the whole run: field and push
+                                    phases separated by a bounded grid barrier */
     GLASMA_BATCH_PER_EVENT = 2,  /* plain loop: one event after the other, one launch per kernel */
-    GLASMA_BATCH_EAGER = 3       /* the launches of GLASMA_BATCH_GRAPH issued without a graph */
+    GLASMA_BATCH_EAGER = 3,      /* the launches of GLASMA_BATCH_GRAPH issued without a graph */
+    GLASMA_BATCH_FUSED = 4       /* per step: bin the particles by tile, then one fused launch that pushes
+                                    each tile's particles from the tile's shared-memory fields; graph */
 } glasma_batch_mode;
 
 /* Workspace for n_events events: ev[i], pp[i] give event i (all with the same
@@ -232,11 +235,14 @@ glasma_status glasma_batch_diagnostics(glasma_batch* b, int32_t event, double ou
 int64_t glasma_batch_state_bytes(const glasma_batch* b);
 glasma_status glasma_batch_export_state(glasma_batch* b, void* host, int64_t bytes);
 glasma_status glasma_batch_import_state(glasma_batch* b, const void* host, int64_t bytes);
-/* One run with the launches of GLASMA_BATCH_GRAPH issued eagerly, each bracketed
- * by CUDA events on the batch stream: total field-kernel and push-kernel time
- * (ms), launches, and the sites covered by the field launches. Synchronises. */
-glasma_status glasma_batch_profile(glasma_batch* b, double* field_ms, int64_t* field_launches,
-                                   int64_t* field_sites, double* push_ms, int64_t* push_launches);
+/* One run issued eagerly with CUDA events around every launch (batch stream).
+ * mode GLASMA_BATCH_FUSED: main = the fused field+push kernel (the binning step
+ * runs after it, timed as other); any other mode: main = the batched field
+ * kernel, other = the batched push.  Returns the total main-kernel time (ms),
+ * its launches, the site-updates and particle-steps it performed, and the
+ * total time of the other kernels.  Synchronises. */
+glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, double* main_ms, int64_t* main_launches,
+                                   int64_t* main_sites, int64_t* main_particle_steps, double* other_ms);
 /* Particles of event i (original order; double[n] each, Q double[n][8]; NULL skips). */
 glasma_status glasma_batch_get_particles(glasma_batch* b, int32_t event, double* x, double* y, double* eta,
                                          double* px, double* py, double* peta, double* Q);

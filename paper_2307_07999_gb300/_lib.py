@@ -12,6 +12,7 @@ GLASMA_BATCH_GRAPH = 0
 GLASMA_BATCH_PERSISTENT = 1
 GLASMA_BATCH_PER_EVENT = 2
 GLASMA_BATCH_EAGER = 3
+GLASMA_BATCH_FUSED = 4
 
 STATUS = {
     0: "GLASMA_OK",
@@ -98,8 +99,8 @@ SIGNATURES = {
     "glasma_batch_state_bytes": (_i64, [_p]),
     "glasma_batch_export_state": (C.c_int, [_p, _p, _i64]),
     "glasma_batch_import_state": (C.c_int, [_p, _p, _i64]),
-    "glasma_batch_profile": (C.c_int, [_p, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_d),
-                                       C.POINTER(_i64)]),
+    "glasma_batch_profile": (C.c_int, [_p, _i32, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
+                                       C.POINTER(_d)]),
     "glasma_batch_launches": (_i64, [_p, _i32]),
     "glasma_batch_get_particles": (C.c_int, [_p, _i32] + [_p] * 7),
     "glasma_batch_destroy": (None, [_p]),

@@ -175,7 +175,7 @@ class CPIC:
 class Batch:
     """Many events (each a GlasmaParams + CpicParams pair) advanced together."""
 
-    MODES = {"graph": 0, "persistent": 1, "per_event": 2, "eager": 3}
+    MODES = {"graph": 0, "persistent": 1, "per_event": 2, "eager": 3, "fused": 4}
 
     def __init__(self, events, particles, device="cuda", stream=None):
         # a created stream of our own: the legacy default stream cannot be captured into a graph
@@ -233,12 +233,15 @@ class Batch:
     def import_state(self, host_tensor):
         check(lib().glasma_batch_import_state(self.handle, C.c_void_p(host_tensor.data_ptr()), host_tensor.numel()))
 
-    def profile(self):
-        fm, pm = C.c_double(), C.c_double()
-        fl, fs, pl = C.c_int64(), C.c_int64(), C.c_int64()
-        check(lib().glasma_batch_profile(self.handle, C.byref(fm), C.byref(fl), C.byref(fs), C.byref(pm), C.byref(pl)))
-        return dict(field_ms=fm.value, field_launches=fl.value, field_sites=fs.value, push_ms=pm.value,
-                    push_launches=pl.value)
+    def profile(self, mode="graph"):
+        """CUDA-event timing of one eager run: the main kernel (batched field step, or the
+        fused field+push kernel for mode="fused") and the other kernels."""
+        mm, om = C.c_double(), C.c_double()
+        ml, ms, mp = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().glasma_batch_profile(self.handle, self.MODES[mode], C.byref(mm), C.byref(ml), C.byref(ms),
+                                         C.byref(mp), C.byref(om)))
+        return dict(main_ms=mm.value, main_launches=ml.value, main_sites=ms.value, main_particle_steps=mp.value,
+                    other_ms=om.value)
 
     def launches(self, mode="graph"):
         return lib().glasma_batch_launches(self.handle, self.MODES[mode])

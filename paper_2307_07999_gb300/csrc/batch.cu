@@ -60,7 +60,7 @@ static Layout layout(const glasma_params* ev, const cpic_params* pp, int E, size
     int nmax = 0, smax = 0;
     size_t npmax = 0;
     for (int e = 0; e < E; e++) {
-        L.fields += 3 * fbytes(ev[e]);
+        L.fields += 4 * fbytes(ev[e]);
         L.parts += 2 * part_bytes(pp[e].n_particles, ev[e].precision);
         L.accs += align256(((size_t)steps_of(ev[e]) + 2) * 4 * 8);
         nmax = std::max(nmax, ev[e].n);
@@ -68,8 +68,16 @@ static Layout layout(const glasma_params* ev, const cpic_params* pp, int E, size
         npmax = std::max(npmax, (size_t)pp[e].n_particles);
     }
     const int prec = ev[0].precision;
+    size_t tiles = 0, parts = 0;
+    for (int e = 0; e < E; e++) {
+        const int tx = field_tile_x(prec), ty = field_tile_y(prec);
+        tiles += (size_t)((ev[e].n + tx - 1) / tx) * ((ev[e].n + ty - 1) / ty);
+        parts += (size_t)pp[e].n_particles;
+    }
     L.tables = align256((size_t)smax * E * step_args_size(prec)) + align256((size_t)smax * E * push_args_size(prec)) +
-               align256((size_t)4 << 20) + align256((size_t)4 << 20);
+               align256((size_t)4 << 20) + align256((size_t)4 << 20) + align256((size_t)E * sizeof(BinArgs)) +
+               3 * align256(tiles * 4) + align256((tiles / 1024 + 2) * 4) + align256(parts * 4 + 4) +
+               align256(256 + ((size_t)smax + 2) * 8 + ((size_t)E + 1) * 8);
     const size_t ic = ic_scratch_bytes(nmax, fft_work);
     const size_t srt = align256(sort_scratch_ints(nmax * nmax) * 4);
     L.scratch = std::max(ic, srt) + 256;
@@ -158,6 +166,7 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
         x.mass = pp[e].mass_GeV * x.a_gev;
         x.buf[0] = A.take(fbytes(ev[e]));
         x.buf[1] = A.take(fbytes(ev[e]));
+        x.buf[2] = A.take(fbytes(ev[e]));
         x.init_buf = A.take(fbytes(ev[e]));
         const size_t pb = part_bytes(x.np, b->prec);
         x.part_bytes = pb;
@@ -167,7 +176,7 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
         x.acc_rows = x.n_steps + 2;
         x.acc = (double*)A.take((size_t)x.acc_rows * 4 * 8);
         x.mon = (double*)A.take(256);
-        if (!x.buf[0] || !x.buf[1] || !x.init_buf || !x.part_base || !x.part_init || !x.acc || !x.mon) {
+        if (!x.buf[0] || !x.buf[1] || !x.buf[2] || !x.init_buf || !x.part_base || !x.part_init || !x.acc || !x.mon) {
             delete b;
             return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
         }
@@ -179,7 +188,24 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
     b->tiles_dev = A.take((size_t)4 << 20);
     b->pitems_dev = A.take((size_t)4 << 20);
     b->scratch = A.take(std::max(ic_scratch_bytes(nmax, b->fft_work), align256(sort_scratch_ints(nmax * nmax) * 4)));
-    if (!b->step_args || !b->push_args || !b->tiles_dev || !b->pitems_dev || !b->scratch) {
+    {
+        size_t tiles = 0, parts = 0;
+        const int tx = field_tile_x(b->prec), ty = field_tile_y(b->prec);
+        for (const auto& x : b->ev) {
+            tiles += (size_t)((x.n + tx - 1) / tx) * ((x.n + ty - 1) / ty);
+            parts += (size_t)x.np;
+        }
+        b->n_tiles = (int)tiles;
+        b->bins_dev = A.take((size_t)E * sizeof(BinArgs));
+        b->bin_count = (int*)A.take(tiles * 4);
+        b->bin_fill = (int*)A.take(tiles * 4);
+        b->bin_start = (int*)A.take(tiles * 4);
+        b->bin_totals = (int*)A.take((tiles / 1024 + 2) * 4);
+        b->bin_perm = (int*)A.take(parts * 4 + 4);
+        b->pers_ctrl = A.take(256 + ((size_t)std::max(1, b->max_iter) + 2) * 8 + ((size_t)E + 1) * 8);
+    }
+    if (!b->step_args || !b->push_args || !b->tiles_dev || !b->pitems_dev || !b->scratch || !b->bins_dev ||
+        !b->bin_count || !b->bin_fill || !b->bin_start || !b->bin_totals || !b->bin_perm || !b->pers_ctrl) {
         delete b;
         return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
     }
@@ -205,6 +231,16 @@ static glasma_status build_tables(glasma_batch* b) {
     }
     if (tiles.size() * sizeof(TileItemH) > ((size_t)4 << 20) || pits.size() * sizeof(PushItemH) > ((size_t)4 << 20))
         return bfail(GLASMA_ERR_NOSPACE, "item tables exceed their reserve");
+    if (fused_tile_x(b->prec) != tx || fused_tile_y(b->prec) != ty)
+        return bfail(GLASMA_ERR_INVALID, "fused and field tiles differ");
+    {
+        std::vector<BinArgs> ba(E);
+        for (int i = 0; i < E; i++) {
+            const BatchEvent& x = b->ev[i];
+            ba[i] = BinArgs{x.P.cell, x.np, x.n, (x.n + tx - 1) / tx, tx, ty, b->tiles_upto[i]};
+        }
+        BCK(cudaMemcpyAsync(b->bins_dev, ba.data(), ba.size() * sizeof(BinArgs), cudaMemcpyHostToDevice, b->st));
+    }
     BCK(cudaMemcpyAsync(b->tiles_dev, tiles.data(), tiles.size() * sizeof(TileItemH), cudaMemcpyHostToDevice, b->st));
     BCK(cudaMemcpyAsync(b->pitems_dev, pits.data(), pits.size() * sizeof(PushItemH), cudaMemcpyHostToDevice, b->st));
     const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
@@ -217,8 +253,8 @@ static glasma_status build_tables(glasma_batch* b) {
             const BatchEvent& x = b->ev[i];
             const bool on = s < x.n_steps;
             if (on) act = i + 1;
-            const void* src = x.buf[k & 1];
-            void* dst = x.buf[(k + 1) & 1];
+            const void* src = x.buf[k % 3];
+            void* dst = x.buf[(k + 1) % 3];
             const int reunit = x.gp.reunit_every > 0 && ((s + 1) % x.gp.reunit_every == 0);
             const StepHost st = step_coeffs(src, dst, x.n, s, x.dtau, 1, reunit);
             pack_step_args(b->prec, st, hs.data() + ((size_t)k * E + i) * sa);
@@ -233,6 +269,19 @@ static glasma_status build_tables(glasma_batch* b) {
     }
     // first launch outside any stream capture sets the kernels' shared-memory attribute
     BCK(launch_field_step_batched(b->prec, nullptr, nullptr, 0, b->st));
+    BCK(launch_fused_batched(b->prec, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, b->st));
+    {
+        // persistent-kernel control block: 256 B of counters, then work counters [K + 1],
+        // active [K], tiles_upto [E + 1], pitems_upto [E + 1]
+        std::vector<int> h(((size_t)K + 1) + K + 2 * ((size_t)E + 1), 0);
+        int* w = h.data();
+        for (int k = 0; k < K; k++) w[(K + 1) + k] = b->active[k];
+        for (int i = 0; i <= E; i++) {
+            w[(K + 1) + K + i] = b->tiles_upto[i];
+            w[(K + 1) + K + (E + 1) + i] = b->pitems_upto[i];
+        }
+        BCK(cudaMemcpyAsync((char*)b->pers_ctrl + 256, h.data(), h.size() * 4, cudaMemcpyHostToDevice, b->st));
+    }
     BCK(cudaMemcpyAsync(b->step_args, hs.data(), hs.size(), cudaMemcpyHostToDevice, b->st));
     BCK(cudaMemcpyAsync(b->push_args, hp.data(), hp.size(), cudaMemcpyHostToDevice, b->st));
     BCK(cudaStreamSynchronize(b->st));
@@ -290,6 +339,24 @@ static cudaError_t enqueue_restore(glasma_batch* b) {
     return cudaSuccess;
 }
 
+static cudaError_t enqueue_fused(glasma_batch* b) {
+    cudaError_t e = enqueue_restore(b);
+    if (e != cudaSuccess) return e;
+    const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
+    for (int k = 0; k < b->max_iter; k++) {
+        const int act = b->active[k];
+        if (act == 0) break;
+        e = launch_rebin(b->bins_dev, b->pitems_dev, b->pitems_upto[act], b->tiles_upto[act], b->bin_count,
+                         b->bin_fill, b->bin_start, b->bin_totals, b->bin_perm, b->st);
+        if (e != cudaSuccess) return e;
+        e = launch_fused_batched(b->prec, (char*)b->step_args + (size_t)k * b->E * sa,
+                                 (char*)b->push_args + (size_t)k * b->E * pa, b->tiles_dev, b->tiles_upto[act],
+                                 b->bin_start, b->bin_count, b->bin_perm, b->st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t enqueue_batched(glasma_batch* b) {
     cudaError_t e = enqueue_restore(b);
     if (e != cudaSuccess) return e;
@@ -313,13 +380,13 @@ static cudaError_t enqueue_per_event(glasma_batch* b) {
     for (auto& x : b->ev) {
         for (int s = 1; s < x.n_steps; s++) {
             const int k = s - 1;
-            const StepHost st = step_coeffs(x.buf[k & 1], x.buf[(k + 1) & 1], x.n, s, x.dtau, 1,
+            const StepHost st = step_coeffs(x.buf[k % 3], x.buf[(k + 1) % 3], x.n, s, x.dtau, 1,
                                             x.gp.reunit_every > 0 && ((s + 1) % x.gp.reunit_every == 0));
             e = launch_field_step(b->prec, st, b->st);
             if (e != cudaSuccess) return e;
             if (s >= x.n_form && x.np > 0) {
                 PushHost ph;
-                ph.fo = x.buf[k & 1]; ph.fn = x.buf[(k + 1) & 1]; ph.n = x.n; ph.np = x.np; ph.dtau = x.dtau;
+                ph.fo = x.buf[k % 3]; ph.fn = x.buf[(k + 1) % 3]; ph.n = x.n; ph.np = x.np; ph.dtau = x.dtau;
                 ph.te = s * x.dtau; ph.ichr = 1.0 / (s * x.dtau); ph.teh = (s + 0.5) * x.dtau; ph.mass = x.mass;
                 ph.expanding = 1;
                 ph.acc = x.acc + 4 * (size_t)(s + 1);
@@ -331,40 +398,40 @@ static cudaError_t enqueue_per_event(glasma_batch* b) {
     return cudaSuccess;
 }
 
-extern "C" glasma_status glasma_batch_run(glasma_batch* b, int32_t mode) {
-    if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
-    if (mode == GLASMA_BATCH_PER_EVENT) {
-        BCK(enqueue_per_event(b));
-        return GLASMA_OK;
-    }
-    if (mode == GLASMA_BATCH_EAGER) {
-        BCK(enqueue_batched(b));
-        return GLASMA_OK;
-    }
-    if (mode == GLASMA_BATCH_PERSISTENT) {
-        glasma_status s = batch_run_persistent(b);
-        return s;
-    }
-    if (mode != GLASMA_BATCH_GRAPH) return bfail(GLASMA_ERR_INVALID, "unknown mode");
+static glasma_status run_graph(glasma_batch* b, bool fused) {
     if (b->st == nullptr || b->st == cudaStreamLegacy || b->st == cudaStreamPerThread)
         return bfail(GLASMA_ERR_INVALID, "graph mode needs a created stream (the default stream cannot be captured)");
-    if (!b->graph_ready) {
+    cudaGraphExec_t& exec = fused ? b->exec : b->exec_unfused;
+    bool& ready = fused ? b->graph_ready : b->graph_unfused_ready;
+    if (!ready) {
         cudaGraph_t g = nullptr;
         BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = enqueue_batched(b);
+        cudaError_t e = fused ? enqueue_fused(b) : enqueue_batched(b);
         cudaError_t e2 = cudaStreamEndCapture(b->st, &g);  // always end the capture
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             cudaGetLastError();
             return bcuda(e != cudaSuccess ? e : e2, "graph capture");
         }
-        cudaError_t e3 = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaError_t e3 = cudaGraphInstantiate(&exec, g, 0);
         cudaGraphDestroy(g);
         BCK(e3);
-        b->graph_ready = true;
+        ready = true;
     }
-    BCK(cudaGraphLaunch(b->exec, b->st));
+    BCK(cudaGraphLaunch(exec, b->st));
     return GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_batch_run(glasma_batch* b, int32_t mode) {
+    if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    switch (mode) {
+        case GLASMA_BATCH_PER_EVENT: BCK(enqueue_per_event(b)); return GLASMA_OK;
+        case GLASMA_BATCH_EAGER: BCK(enqueue_batched(b)); return GLASMA_OK;
+        case GLASMA_BATCH_PERSISTENT: return batch_run_persistent(b);
+        case GLASMA_BATCH_GRAPH: return run_graph(b, false);
+        case GLASMA_BATCH_FUSED: return run_graph(b, true);
+        default: return bfail(GLASMA_ERR_INVALID, "unknown mode");
+    }
 }
 
 extern "C" glasma_status glasma_batch_broadening(glasma_batch* b, int32_t event, double* out, int64_t cap,
@@ -374,6 +441,7 @@ extern "C" glasma_status glasma_batch_broadening(glasma_batch* b, int32_t event,
     std::vector<double> h((size_t)x.acc_rows * 4);
     BCK(cudaMemcpyAsync(h.data(), x.acc, h.size() * 8, cudaMemcpyDeviceToHost, b->st));
     BCK(cudaStreamSynchronize(b->st));
+    if (batch_timed_out(b)) return bfail(GLASMA_ERR_TIMEOUT, "persistent kernel: a grid barrier wait ran out");
     const double conv = 1.0 / (x.a_gev * x.a_gev);
     int64_t k = 0;
     for (int r = x.n_form; r <= x.n_steps && r < x.acc_rows; r++) {
@@ -404,8 +472,8 @@ extern "C" glasma_status glasma_batch_work(const glasma_batch* b, int64_t* site_
 extern "C" glasma_status glasma_batch_diagnostics(glasma_batch* b, int32_t event, double out[8]) {
     if (!b || !out || event < 0 || event >= b->E) return bfail(GLASMA_ERR_INVALID, "bad arguments");
     const BatchEvent& x = b->ev[b->pos[event]];
-    const int last = x.n_steps;  // final state at step n_steps sits in buf[(n_steps - 1) & 1]
-    BCK(launch_monitors(b->prec, x.buf[(last - 1) & 1], x.n, last * x.dtau, x.mon, b->st));
+    const int last = x.n_steps;  // final state at step n_steps sits in buf[(n_steps - 1) % 3]
+    BCK(launch_monitors(b->prec, x.buf[(last - 1) % 3], x.n, last * x.dtau, x.mon, b->st));
     double m[8];
     BCK(cudaMemcpyAsync(m, x.mon, sizeof(m), cudaMemcpyDeviceToHost, b->st));
     BCK(cudaStreamSynchronize(b->st));
@@ -454,47 +522,60 @@ extern "C" glasma_status glasma_batch_import_state(glasma_batch* b, const void* 
 }
 
 // one eager run with CUDA events around every launch (on the batch stream)
-extern "C" glasma_status glasma_batch_profile(glasma_batch* b, double* field_ms, int64_t* field_launches,
-                                              int64_t* field_sites, double* push_ms, int64_t* push_launches) {
+// one eager run with CUDA events around every launch (on the batch stream).  mode
+// GLASMA_BATCH_FUSED: the fused kernel is the main kernel and the binning kernels the
+// others; any other mode: the batched field kernel is the main kernel and the push the other.
+extern "C" glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, double* main_ms, int64_t* main_launches,
+                                              int64_t* main_sites, int64_t* main_particle_steps, double* other_ms) {
     if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    const bool fused = mode == GLASMA_BATCH_FUSED;
     BCK(enqueue_restore(b));
     const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
     const int K = b->max_iter;
     std::vector<cudaEvent_t> ev(4 * (size_t)K);
     for (auto& e : ev) BCK(cudaEventCreate(&e));
-    std::vector<size_t> sites(K, 0);
+    int64_t sites = 0, parts = 0;
     int used = 0;
     for (int k = 0; k < K; k++) {
         const int act = b->active[k];
         if (act == 0) break;
-        for (int i = 0; i < act; i++) sites[k] += b->ev[i].ns;
+        for (int i = 0; i < act; i++) {
+            sites += (int64_t)b->ev[i].ns;
+            if (k + 1 >= b->ev[i].n_form) parts += b->ev[i].np;
+        }
+        const void* sargs = (char*)b->step_args + (size_t)k * b->E * sa;
+        const void* pargs = (char*)b->push_args + (size_t)k * b->E * pa;
         BCK(cudaEventRecord(ev[4 * k + 0], b->st));
-        BCK(launch_field_step_batched(b->prec, (char*)b->step_args + (size_t)k * b->E * sa, b->tiles_dev,
-                                      b->tiles_upto[act], b->st));
+        if (fused)
+            BCK(launch_fused_batched(b->prec, sargs, pargs, b->tiles_dev, b->tiles_upto[act], b->bin_start,
+                                     b->bin_count, b->bin_perm, b->st));
+        else
+            BCK(launch_field_step_batched(b->prec, sargs, b->tiles_dev, b->tiles_upto[act], b->st));
         BCK(cudaEventRecord(ev[4 * k + 1], b->st));
         BCK(cudaEventRecord(ev[4 * k + 2], b->st));
-        BCK(launch_push_batched(b->prec, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
-                                b->pitems_upto[act], b->st));
+        if (fused)
+            BCK(launch_rebin(b->bins_dev, b->pitems_dev, b->pitems_upto[act], b->tiles_upto[act], b->bin_count,
+                             b->bin_fill, b->bin_start, b->bin_totals, b->bin_perm, b->st));
+        else
+            BCK(launch_push_batched(b->prec, pargs, b->pitems_dev, b->pitems_upto[act], b->st));
         BCK(cudaEventRecord(ev[4 * k + 3], b->st));
         used = k + 1;
     }
     BCK(cudaStreamSynchronize(b->st));
-    double fm = 0, pm = 0;
-    size_t fs = 0;
+    double mm = 0, om = 0;
     for (int k = 0; k < used; k++) {
         float a = 0, c = 0;
         BCK(cudaEventElapsedTime(&a, ev[4 * k + 0], ev[4 * k + 1]));
         BCK(cudaEventElapsedTime(&c, ev[4 * k + 2], ev[4 * k + 3]));
-        fm += a;
-        pm += c;
-        fs += sites[k];
+        mm += a;
+        om += c;
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    if (field_ms) *field_ms = fm;
-    if (field_launches) *field_launches = used;
-    if (field_sites) *field_sites = (int64_t)fs;
-    if (push_ms) *push_ms = pm;
-    if (push_launches) *push_launches = used;
+    if (main_ms) *main_ms = mm;
+    if (main_launches) *main_launches = used;
+    if (main_sites) *main_sites = sites;
+    if (main_particle_steps) *main_particle_steps = fused ? parts : 0;
+    if (other_ms) *other_ms = om;
     return GLASMA_OK;
 }
 
@@ -527,6 +608,8 @@ extern "C" int64_t glasma_batch_launches(const glasma_batch* b, int32_t mode) {
         for (const auto& x : b->ev) L += (x.n_steps - 1) + std::max(0, x.n_steps - x.n_form) * (x.np > 0);
     } else if (mode == GLASMA_BATCH_PERSISTENT) {
         L = 1;
+    } else if (mode == GLASMA_BATCH_FUSED) {  // count, 3 scan passes, scatter, fused kernel
+        for (int k = 0; k < b->max_iter; k++) L += b->active[k] ? 6 : 0;
     } else {
         for (int k = 0; k < b->max_iter; k++) L += b->active[k] ? 2 : 0;
     }
@@ -536,6 +619,7 @@ extern "C" int64_t glasma_batch_launches(const glasma_batch* b, int32_t mode) {
 extern "C" void glasma_batch_destroy(glasma_batch* b) {
     if (!b) return;
     if (b->graph_ready) cudaGraphExecDestroy(b->exec);
+    if (b->graph_unfused_ready) cudaGraphExecDestroy(b->exec_unfused);
     batch_free_persistent(b);
     delete b;
 }

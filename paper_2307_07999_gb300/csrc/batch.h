@@ -15,7 +15,7 @@ struct BatchEvent {
     size_t ns;
     int n_steps, n_form, np, acc_rows;
     double a_fm, a_gev, dtau, mass;
-    void* buf[2];
+    void* buf[3];        // rotating: iteration k reads buf[k % 3], writes buf[(k + 1) % 3]
     void* init_buf;
     void* part_base;
     void* part_init;
@@ -40,8 +40,16 @@ struct glasma_batch {
     void* pitems_dev = nullptr;   // PushItem list, grouped by event
     void* scratch = nullptr;      // initial-condition / sort scratch
     std::vector<int> tiles_upto, pitems_upto, active;
-    bool initialised = false, graph_ready = false;
-    cudaGraphExec_t exec = nullptr;
+    // tile bins of the fused path
+    void* bins_dev = nullptr;     // BinArgs per event
+    int* bin_count = nullptr;
+    int* bin_fill = nullptr;
+    int* bin_start = nullptr;
+    int* bin_totals = nullptr;
+    int* bin_perm = nullptr;
+    int n_tiles = 0;
+    bool initialised = false, graph_ready = false, graph_unfused_ready = false;
+    cudaGraphExec_t exec = nullptr, exec_unfused = nullptr;
     // persistent mode
     void* pers_ctrl = nullptr;    // barrier counters + error word + per-iteration prefixes (device)
     int pers_blocks = 0;
@@ -50,4 +58,5 @@ struct glasma_batch {
 
 void glasma_set_error(const char* msg);
 glasma_status batch_run_persistent(glasma_batch* b);
+bool batch_timed_out(glasma_batch* b);  // reads (and clears) the persistent kernel's error word
 void batch_free_persistent(glasma_batch* b);

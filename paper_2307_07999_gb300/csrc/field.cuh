@@ -29,14 +29,21 @@ template <class T> struct StepArgs {
 
 struct TileItem { int ev, x0, y0; };
 
-template <class T> DEV M3<T> load_link(const T* __restrict__ f, size_t ns, int plane0, size_t s) {
+// Global loads of field data: through the read-only cache when the data is constant for
+// the whole kernel (CG = false), at L2 (coherent) inside a persistent kernel that also
+// writes the buffers it reads in later phases (CG = true).
+template <bool CG, class T> DEV T ldf(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
+}
+template <class T, bool CG = false> DEV M3<T> load_link(const T* __restrict__ f, size_t ns, int plane0, size_t s) {
     M3<T> U;
 #pragma unroll
     for (int r = 0; r < 2; r++)
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             const int p = plane0 + 2 * (3 * r + c);
-            U.m[r][c] = mk(__ldg(f + (size_t)p * ns + s), __ldg(f + (size_t)(p + 1) * ns + s));
+            U.m[r][c] = mk(ldf<CG>(f + (size_t)p * ns + s), ldf<CG>(f + (size_t)(p + 1) * ns + s));
         }
     complete_row2(U);
     return U;
@@ -51,10 +58,10 @@ template <class T> DEV void store_link(T* __restrict__ f, size_t ns, int plane0,
             f[(size_t)(p + 1) * ns + s] = U.m[r][c].i;
         }
 }
-template <class T> DEV Al<T> load_alg(const T* __restrict__ f, size_t ns, int plane0, size_t s) {
+template <class T, bool CG = false> DEV Al<T> load_alg(const T* __restrict__ f, size_t ns, int plane0, size_t s) {
     Al<T> x;
 #pragma unroll
-    for (int a = 0; a < 8; a++) x.a[a] = __ldg(f + (size_t)(plane0 + a) * ns + s);
+    for (int a = 0; a < 8; a++) x.a[a] = ldf<CG>(f + (size_t)(plane0 + a) * ns + s);
     return x;
 }
 template <class T> DEV void store_alg(T* __restrict__ f, size_t ns, int plane0, size_t s, const Al<T>& x) {
@@ -86,7 +93,7 @@ template <class T, int S> DEV Al<T> sm_alg(const T* s, int h) {
 }
 
 // One tile [x0, x0+TX) x [y0, y0+TY) of one step: kick at tau_n, drift with tau_{n+1/2}.
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, bool CG = false>
 DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_raw) {
     using G = Tile<T, TX, TY>;
     constexpr int HX = G::HX, HS = G::HS, FX = G::FX, FS = G::FS;
@@ -102,7 +109,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool active = (x < n) && (y < n);
     const size_t s = active ? (size_t)x + (size_t)n * y : 0;
-    Al<T> Ex = load_alg(src, ns, P_EX, s), Ey = load_alg(src, ns, P_EY, s), pi = load_alg(src, ns, P_PI, s);
+    Al<T> Ex = load_alg<T, CG>(src, ns, P_EX, s), Ey = load_alg<T, CG>(src, ns, P_EY, s), pi = load_alg<T, CG>(src, ns, P_PI, s);
 
     // phase 1: links (completed to 3 rows) and phi of the tile plus a one-site halo
     for (int h = tid; h < HS; h += TX * TY) {
@@ -110,7 +117,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         const size_t g = (size_t)wrapi(x0 - 1 + hx, n) + (size_t)n * wrapi(y0 - 1 + hy, n);
 #pragma unroll
         for (int d = 0; d < 2; d++) {
-            const M3<T> U = load_link(src, ns, d == 0 ? P_UX : P_UY, g);
+            const M3<T> U = load_link<T, CG>(src, ns, d == 0 ? P_UX : P_UY, g);
             T* b = sU + d * 18 * HS + h;
 #pragma unroll
             for (int r = 0; r < 3; r++)
@@ -121,7 +128,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
                 }
         }
 #pragma unroll
-        for (int a = 0; a < 8; a++) sP[a * HS + h] = __ldg(src + (size_t)(P_PHI + a) * ns + g);
+        for (int a = 0; a < 8; a++) sP[a * HS + h] = ldf<CG>(src + (size_t)(P_PHI + a) * ns + g);
     }
     __syncthreads();
 

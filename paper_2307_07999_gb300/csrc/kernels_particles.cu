@@ -60,6 +60,38 @@ cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStre
     return cudaGetLastError();
 }
 
+__global__ void k_cell_count(const int* __restrict__ cell, int np, int* __restrict__ count) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < np) atomicAdd(count + cell[j], 1);
+}
+// exclusive scan, three passes: per-block scan with block totals, scan of the totals, add
+__global__ void k_scan_block(const int* __restrict__ in, int* __restrict__ out, int* __restrict__ totals, int len) {
+    __shared__ int buf[1024];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int v = i < len ? in[i] : 0;
+    buf[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int t = threadIdx.x >= o ? buf[threadIdx.x - o] : 0;
+        __syncthreads();
+        buf[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < len) out[i] = buf[threadIdx.x] - v;
+    if (threadIdx.x == 1023) totals[blockIdx.x] = buf[1023];
+}
+__global__ void k_scan_totals(int* totals, int nb) {
+    // one thread: nb is at most a few thousand
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < nb; b++) { const int t = totals[b]; totals[b] = run; run += t; }
+    }
+}
+__global__ void k_scan_add(int* __restrict__ out, const int* __restrict__ totals, int len) {
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    if (i < len) out[i] += totals[blockIdx.x];
+}
+
 size_t sort_scratch_ints(int ncell) { return 2 * (size_t)ncell + (size_t)(ncell + 1023) / 1024 + 1; }
 
 cudaError_t launch_sort(int prec, const PartHost& a, const PartHost& b, int np, int ncell, int* count, int* start,

@@ -55,84 +55,88 @@ template <class T> DEV T dot8(const Al<T>& a, const Al<T>& b) {
     return s;
 }
 
-// site-centred fields at cell (cx, cy) for the push of step n:
-// F[0..2] = E_x, E_y, E_z ; F[3..5] = B_x, B_y, B_z   (contracted with Q on return)
-template <class T>
-DEV void gather_qf(const PushArgs<T>& A, int cx, int cy, const Al<T>& q, T qE[3], T qB[3]) {
-    const int n = A.n;
-    const size_t ns = (size_t)n * n;
-    const int xm = cx == 0 ? n - 1 : cx - 1, xp = cx == n - 1 ? 0 : cx + 1;
-    const int ym = cy == 0 ? n - 1 : cy - 1, yp = cy == n - 1 ? 0 : cy + 1;
-    const size_t c = cx + (size_t)n * cy;
-    const size_t cxm = xm + (size_t)n * cy, cxp = xp + (size_t)n * cy;
-    const size_t cym = cx + (size_t)n * ym, cyp = cx + (size_t)n * yp;
-    const T* fo = A.fo;
-    const T* fn = A.fn;
-    const T half = T(0.5);
-    const M3<T> ux_c = load_link(fo, ns, P_UX, c), uy_c = load_link(fo, ns, P_UY, c);
-    const M3<T> ux_xm = load_link(fo, ns, P_UX, cxm), uy_ym = load_link(fo, ns, P_UY, cym);
-    // electric: the two links touching c, time-centred, transported to c
-    {
-        Al<T> ec, em;
+template <class T> DEV T clamp_below_one(T v);
+template <> DEV float clamp_below_one<float>(float v) { return fminf(v, 0.99999994f); }
+template <> DEV double clamp_below_one<double>(double v) { return fmin(v, 0.99999999999999989); }
+
+// Field source of the unfused push: links, phi and time-averaged E, pi read from
+// the two global field buffers of step n.  Cells are given as (x, y) with the
+// neighbours already wrapped periodically.
+template <class T, bool CG = false> struct GlobalSrc {
+    const T* fo;
+    const T* fn;
+    int n;
+    size_t ns;
+    DEV size_t at(int x, int y) const { return (size_t)x + (size_t)n * y; }
+    DEV M3<T> link(int d, int x, int y) const { return load_link<T, CG>(fo, ns, d == 0 ? P_UX : P_UY, at(x, y)); }
+    DEV Al<T> phi(int x, int y) const { return load_alg<T, CG>(fo, ns, P_PHI, at(x, y)); }
+    // (E_i(tau_{n-1/2}) + E_i(tau_{n+1/2})) / 2 on the link (x, y) -> (x, y) + i
+    DEV Al<T> eavg(int d, int x, int y) const {
+        Al<T> e;
+        const int p = d == 0 ? P_EX : P_EY;
+        const size_t s = at(x, y);
 #pragma unroll
-        for (int a = 0; a < 8; a++) {
-            ec.a[a] = half * (__ldg(fo + (size_t)(P_EX + a) * ns + c) + __ldg(fn + (size_t)(P_EX + a) * ns + c));
-            em.a[a] = half * (__ldg(fo + (size_t)(P_EX + a) * ns + cxm) + __ldg(fn + (size_t)(P_EX + a) * ns + cxm));
-        }
-        const Al<T> t = transport_alg(ux_xm, em);
-        qE[0] = half * (dot8(q, ec) + dot8(q, t)) / A.te;
+        for (int a = 0; a < 8; a++) e.a[a] = T(0.5) * (ldf<CG>(fo + (size_t)(p + a) * ns + s) + ldf<CG>(fn + (size_t)(p + a) * ns + s));
+        return e;
     }
-    {
-        Al<T> ec, em;
-#pragma unroll
-        for (int a = 0; a < 8; a++) {
-            ec.a[a] = half * (__ldg(fo + (size_t)(P_EY + a) * ns + c) + __ldg(fn + (size_t)(P_EY + a) * ns + c));
-            em.a[a] = half * (__ldg(fo + (size_t)(P_EY + a) * ns + cym) + __ldg(fn + (size_t)(P_EY + a) * ns + cym));
-        }
-        const Al<T> t = transport_alg(uy_ym, em);
-        qE[1] = half * (dot8(q, ec) + dot8(q, t)) / A.te;
-    }
-    {
-        T s = T(0);
+    DEV Al<T> piavg(int x, int y) const {
+        Al<T> e;
+        const size_t s = at(x, y);
 #pragma unroll
         for (int a = 0; a < 8; a++)
-            s = fma(q.a[a], half * (__ldg(fo + (size_t)(P_PI + a) * ns + c) + __ldg(fn + (size_t)(P_PI + a) * ns + c)), s);
-        qE[2] = s;
+            e.a[a] = T(0.5) * (ldf<CG>(fo + (size_t)(P_PI + a) * ns + s) + ldf<CG>(fn + (size_t)(P_PI + a) * ns + s));
+        return e;
     }
+};
+
+// Q-contracted site-centred fields at cell (cx, cy) for the push of step n:
+// qE = Q.(E_x, E_y, E_z), qB = Q.(B_x, B_y, B_z)
+template <class T, class S>
+DEV void gather_qf_src(const S& F, int n, T te, int cx, int cy, const Al<T>& q, T qE[3], T qB[3]) {
+    const int xm = cx == 0 ? n - 1 : cx - 1, xp = cx == n - 1 ? 0 : cx + 1;
+    const int ym = cy == 0 ? n - 1 : cy - 1, yp = cy == n - 1 ? 0 : cy + 1;
+    const T half = T(0.5);
+    const M3<T> ux_c = F.link(0, cx, cy), uy_c = F.link(1, cx, cy);
+    const M3<T> ux_xm = F.link(0, xm, cy), uy_ym = F.link(1, cx, ym);
+    // electric: the two links touching c, time-centred, transported to c
+    {
+        const Al<T> t = transport_alg(ux_xm, F.eavg(0, xm, cy));
+        qE[0] = half * (dot8(q, F.eavg(0, cx, cy)) + dot8(q, t)) / te;
+    }
+    {
+        const Al<T> t = transport_alg(uy_ym, F.eavg(1, cx, ym));
+        qE[1] = half * (dot8(q, F.eavg(1, cx, cy)) + dot8(q, t)) / te;
+    }
+    qE[2] = dot8(q, F.piavg(cx, cy));
     // magnetic from phi: covariant central differences
     {
-        const Al<T> fw = conj_alg(ux_c, load_alg(fo, ns, P_PHI, cxp));
-        const Al<T> bw = transport_alg(ux_xm, load_alg(fo, ns, P_PHI, cxm));
-        qB[1] = half * (dot8(q, fw) - dot8(q, bw)) / A.te;    // B_y = +D_x phi / tau
+        const Al<T> fw = conj_alg(ux_c, F.phi(xp, cy));
+        const Al<T> bw = transport_alg(ux_xm, F.phi(xm, cy));
+        qB[1] = half * (dot8(q, fw) - dot8(q, bw)) / te;    // B_y = +D_x phi / tau
     }
     {
-        const Al<T> fw = conj_alg(uy_c, load_alg(fo, ns, P_PHI, cyp));
-        const Al<T> bw = transport_alg(uy_ym, load_alg(fo, ns, P_PHI, cym));
-        qB[0] = -half * (dot8(q, fw) - dot8(q, bw)) / A.te;   // B_x = -D_y phi / tau
+        const Al<T> fw = conj_alg(uy_c, F.phi(cx, yp));
+        const Al<T> bw = transport_alg(uy_ym, F.phi(cx, ym));
+        qB[0] = -half * (dot8(q, fw) - dot8(q, bw)) / te;   // B_x = -D_y phi / tau
     }
     // B_z = -F_xy, F_xy = clover average of the four plaquettes based at c
     {
-        const size_t cxpym = xp + (size_t)n * ym, cxmyp = xm + (size_t)n * yp, cxmym = xm + (size_t)n * ym;
-        Al<T> acc;
-        {   // +x,+y
-            const M3<T> P = mul_nd(mul(ux_c, load_link(fo, ns, P_UY, cxp)), mul(uy_c, load_link(fo, ns, P_UX, cyp)));
-            acc = im_tl(P);
-        }
+        Al<T> acc = im_tl(mul_nd(mul(ux_c, F.link(1, xp, cy)), mul(uy_c, F.link(0, cx, yp))));  // +x,+y
         {   // +y,-x: U_y(c) [U_y(c-x) U_x(c-x+y)]^dag U_x(c-x)
-            const M3<T> B = mul(load_link(fo, ns, P_UY, cxm), load_link(fo, ns, P_UX, cxmyp));
+            const M3<T> B = mul(F.link(1, xm, cy), F.link(0, xm, yp));
             const Al<T> t = im_tl(mul(mul_nd(uy_c, B), ux_xm));
 #pragma unroll
             for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
         }
         {   // -x,-y: [U_y(c-x-y) U_x(c-x)]^dag [U_x(c-x-y) U_y(c-y)]
-            const M3<T> B1 = mul(load_link(fo, ns, P_UY, cxmym), ux_xm);
-            const M3<T> B2 = mul(load_link(fo, ns, P_UX, cxmym), uy_ym);
+            const M3<T> B1 = mul(F.link(1, xm, ym), ux_xm);
+            const M3<T> B2 = mul(F.link(0, xm, ym), uy_ym);
             const Al<T> t = im_tl(mul_dn(B1, B2));
 #pragma unroll
             for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
         }
         {   // -y,+x: U_y(c-y)^dag [U_x(c-y) U_y(c+x-y)] U_x(c)^dag
-            const M3<T> B = mul(load_link(fo, ns, P_UX, cym), load_link(fo, ns, P_UY, cxpym));
+            const M3<T> B = mul(F.link(0, cx, ym), F.link(1, xp, ym));
             const Al<T> t = im_tl(mul_nd(mul_dn(uy_ym, B), ux_c));
 #pragma unroll
             for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
@@ -141,25 +145,28 @@ DEV void gather_qf(const PushArgs<T>& A, int cx, int cy, const Al<T>& q, T qE[3]
     }
 }
 
-template <class T> DEV T clamp_below_one(T v);
-template <> DEV float clamp_below_one<float>(float v) { return fminf(v, 0.99999994f); }
-template <> DEV double clamp_below_one<double>(double v) { return fmin(v, 0.99999999999999989); }
+template <class T>
+DEV void gather_qf(const PushArgs<T>& A, int cx, int cy, const Al<T>& q, T qE[3], T qB[3]) {
+    GlobalSrc<T> F{A.fo, A.fn, A.n, (size_t)A.n * A.n};
+    gather_qf_src(F, A.n, A.te, cx, cy, q, qE, qB);
+}
+
 
 // one particle: gather, kick, drift, color transport; returns its broadening terms
-template <class T>
-DEV void push_one(const PushArgs<T>& A, int j, double& sx, double& sy, double& sz, double& sc) {
+template <class T, class S, bool CG = false>
+DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, double& sy, double& sz, double& sc) {
     const PartSoA<T>& P = A.P;
     const int n = A.n;
-    const size_t ns = (size_t)n * n;
-    const int cell = P.cell[j];
+    const int cell = CG ? __ldcg(P.cell + j) : P.cell[j];
     int cx = cell % n, cy = cell / n;
     Al<T> q;
 #pragma unroll
-    for (int a = 0; a < 8; a++) q.a[a] = P.Q[(size_t)a * P.qs + j];
+    for (int a = 0; a < 8; a++) q.a[a] = CG ? __ldcg(P.Q + (size_t)a * P.qs + j) : P.Q[(size_t)a * P.qs + j];
     T qE[3], qB[3];
-    gather_qf(A, cx, cy, q, qE, qB);
-    const T p0x = P.p0x[j], p0y = P.p0y[j];
-    T dpx = P.dpx[j], dpy = P.dpy[j], pz = P.peta[j];
+    gather_qf_src(F, n, A.te, cx, cy, q, qE, qB);
+    const T p0x = P.p0x[j], p0y = P.p0y[j];  // constant during a run
+    T dpx = CG ? __ldcg(P.dpx + j) : P.dpx[j], dpy = CG ? __ldcg(P.dpy + j) : P.dpy[j];
+    T pz = CG ? __ldcg(P.peta + j) : P.peta[j];
     const T m2 = A.mass * A.mass;
     T px = p0x + dpx, py = p0y + dpy;
     const T pt = sqrt(m2 + px * px + py * py + pz * pz);
@@ -174,37 +181,37 @@ DEV void push_one(const PushArgs<T>& A, int j, double& sx, double& sy, double& s
     py = p0y + dpy;
     const T ptn = sqrt(m2 + px * px + py * py + pz * pz);
     const T iptn = ptn > T(0) ? T(1) / ptn : T(0);
-    T ox = P.ox[j] + A.dtau * px * iptn;
-    T oy = P.oy[j] + A.dtau * py * iptn;
+    T ox = (CG ? __ldcg(P.ox + j) : P.ox[j]) + A.dtau * px * iptn;
+    T oy = (CG ? __ldcg(P.oy + j) : P.oy[j]) + A.dtau * py * iptn;
     const T deta = A.dtau * pz * iptn / A.teh;
     // color: rotation along eta at the old cell, then across the x face, then the y face
     {
         Al<T> e;
-        const Al<T> ph = load_alg(A.fo, ns, P_PHI, (size_t)cell);
+        const Al<T> ph = F.phi(cx, cy);
 #pragma unroll
         for (int a = 0; a < 8; a++) e.a[a] = -deta * ph.a[a];
         q = alg(conj_by(expi(herm(e)), herm(q)));
     }
     int nx = cx, ny = cy;
     if (ox >= T(1)) {
-        q = transport_alg(load_link(A.fo, ns, P_UX, (size_t)cell), q);
+        q = transport_alg(F.link(0, cx, cy), q);
         ox -= T(1);
         nx = cx == n - 1 ? 0 : cx + 1;
     } else if (ox < T(0)) {
         nx = cx == 0 ? n - 1 : cx - 1;
-        q = conj_alg(load_link(A.fo, ns, P_UX, nx + (size_t)n * cy), q);
+        q = conj_alg(F.link(0, nx, cy), q);
         ox = clamp_below_one(ox + T(1));
     }
     if (oy >= T(1)) {
-        q = transport_alg(load_link(A.fo, ns, P_UY, nx + (size_t)n * cy), q);
+        q = transport_alg(F.link(1, nx, cy), q);
         oy -= T(1);
         ny = cy == n - 1 ? 0 : cy + 1;
     } else if (oy < T(0)) {
         ny = cy == 0 ? n - 1 : cy - 1;
-        q = conj_alg(load_link(A.fo, ns, P_UY, nx + (size_t)n * ny), q);
+        q = conj_alg(F.link(1, nx, ny), q);
         oy = clamp_below_one(oy + T(1));
     }
-    const T eta = P.eta[j] + deta;
+    const T eta = (CG ? __ldcg(P.eta + j) : P.eta[j]) + deta;
     P.cell[j] = nx + n * ny;
     P.ox[j] = ox;
     P.oy[j] = oy;
@@ -224,7 +231,14 @@ DEV void push_one(const PushArgs<T>& A, int j, double& sx, double& sy, double& s
     sc = 1.0;
 }
 
-// warp -> block -> one FP64 atomic per block and term (blockDim.x <= 256)
+template <class T, bool CG = false>
+DEV void push_one(const PushArgs<T>& A, int j, double& sx, double& sy, double& sz, double& sc) {
+    GlobalSrc<T, CG> F{A.fo, A.fn, A.n, (size_t)A.n * A.n};
+    push_one_src<T, GlobalSrc<T, CG>, CG>(A, F, j, sx, sy, sz, sc);
+}
+
+// warp -> block -> one FP64 atomic per block and term (any block shape, at most 256
+// threads, a multiple of 32)
 DEV void block_acc4(double sx, double sy, double sz, double sc, double* acc) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -234,13 +248,15 @@ DEV void block_acc4(double sx, double sy, double sz, double sc, double* acc) {
         sc += __shfl_down_sync(0xffffffffu, sc, o);
     }
     __shared__ double red[4][8];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int lt = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+    const int w = lt >> 5, l = lt & 31;
     if (l == 0) { red[0][w] = sx; red[1][w] = sy; red[2][w] = sz; red[3][w] = sc; }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (lt < 4) {
         double t = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[threadIdx.x][k];
-        atomicAdd(acc + threadIdx.x, t);
+        for (int k = 0; k < nw; k++) t += red[lt][k];
+        atomicAdd(acc + lt, t);
     }
 }
 
@@ -268,37 +284,6 @@ __global__ void __launch_bounds__(256) k_push_batched(const PushArgs<T>* __restr
 }
 
 // ---------------------------------------------------------------- counting sort by cell
-__global__ void k_cell_count(const int* __restrict__ cell, int np, int* __restrict__ count) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < np) atomicAdd(count + cell[j], 1);
-}
-// exclusive scan, three passes: per-block scan with block totals, scan of the totals, add
-__global__ void k_scan_block(const int* __restrict__ in, int* __restrict__ out, int* __restrict__ totals, int len) {
-    __shared__ int buf[1024];
-    const int i = blockIdx.x * 1024 + threadIdx.x;
-    const int v = i < len ? in[i] : 0;
-    buf[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const int t = threadIdx.x >= o ? buf[threadIdx.x - o] : 0;
-        __syncthreads();
-        buf[threadIdx.x] += t;
-        __syncthreads();
-    }
-    if (i < len) out[i] = buf[threadIdx.x] - v;
-    if (threadIdx.x == 1023) totals[blockIdx.x] = buf[1023];
-}
-__global__ void k_scan_totals(int* totals, int nb) {
-    // one thread: nb is at most a few thousand
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        int run = 0;
-        for (int b = 0; b < nb; b++) { const int t = totals[b]; totals[b] = run; run += t; }
-    }
-}
-__global__ void k_scan_add(int* __restrict__ out, const int* __restrict__ totals, int len) {
-    const int i = blockIdx.x * 1024 + threadIdx.x;
-    if (i < len) out[i] += totals[blockIdx.x];
-}
 template <class T>
 __global__ void k_scatter(PartSoA<T> a, PartSoA<T> b, int np, int* __restrict__ cursor) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
