@@ -70,6 +70,12 @@ def _declare(L):
         "o_push": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p]),
         "o_casimirs": (None, [_p, _p, _p]),
         "o_pz_lab": (_d, [_d, _d, _d, _d, _d]),
+        "o_mlp_forward": (None, [_i] + [_p] * 10),
+        "o_mlp_loss_backward": (_d, [_i] + [_p] * 14),
+        "o_ic_features": (None, [_p, _p, _p]),
+        "o_ic_target": (None, [_p, _p, _p, _p]),
+        "o_ic_delta": (None, [_p, _p, _p, _p]),
+        "o_ic_series": (None, [_p, _p, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -404,3 +410,55 @@ def casimirs(Q):
 
 def pz_lab(mass, px, py, peta, eta):
     return lib().o_pz_lab(mass, px, py, peta, eta)
+
+
+# ---------------------------------------------------------------- warm-start network
+MLP_SHAPES = {"W1": (128, 36), "b1": (128,), "W2": (128, 128), "b2": (128,), "W3": (16, 128), "b3": (16,)}
+
+
+def mlp_forward(x, w):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    B = x.shape[0]
+    h1, h2, y = rz(B, 128), rz(B, 128), rz(B, 16)
+    ws = [np.ascontiguousarray(w[k], dtype=np.float64) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+    lib().o_mlp_forward(B, _ptr(x), *[_ptr(a) for a in ws], _ptr(h1), _ptr(h2), _ptr(y))
+    return y, h1, h2
+
+
+def mlp_loss_grad(x, t, w):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    ws = [np.ascontiguousarray(w[k], dtype=np.float64) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+    g = {k: rz(*s) for k, s in MLP_SHAPES.items()}
+    loss = lib().o_mlp_loss_backward(x.shape[0], _ptr(x), _ptr(t), *[_ptr(a) for a in ws],
+                                     *[_ptr(g[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+    return loss, g
+
+
+def ic_features(U1, U2):
+    f = rz(36)
+    a = np.ascontiguousarray(U1, dtype=np.complex128)
+    b = np.ascontiguousarray(U2, dtype=np.complex128)
+    lib().o_ic_features(_ptr(a), _ptr(b), _ptr(f))
+    return f
+
+
+def ic_series(U1, U2):
+    d = rz(8)
+    args = [np.ascontiguousarray(m, dtype=np.complex128) for m in (U1, U2)]
+    lib().o_ic_series(*[_ptr(m) for m in args], _ptr(d))
+    return d
+
+
+def ic_delta(U1, U2, U):
+    d = rz(8)
+    args = [np.ascontiguousarray(m, dtype=np.complex128) for m in (U1, U2, U)]
+    lib().o_ic_delta(*[_ptr(m) for m in args], _ptr(d))
+    return d
+
+
+def ic_target(U1, U2, U):
+    d = rz(8)
+    args = [np.ascontiguousarray(m, dtype=np.complex128) for m in (U1, U2, U)]
+    lib().o_ic_target(*[_ptr(m) for m in args], _ptr(d))
+    return d

@@ -77,17 +77,6 @@ double o_potential(int n, double tau, int expanding, const cplx *U, const double
     return tb * vb + tp * vp;
 }
 
-/* components of i[A, B] for Hermitian A, B given by components */
-static void icomm(const double a[8], const double b[8], double out[8]) {
-    cplx A[9], B[9], AB[9], BA[9], C[9];
-    o_alg_to_mat(a, A);
-    o_alg_to_mat(b, B);
-    o_mul(A, B, AB);
-    o_mul(B, A, BA);
-    for (int k = 0; k < 9; k++) C[k] = I * (AB[k] - BA[k]);
-    o_mat_to_alg(C, out);
-}
-
 void o_force(int n, double tau, int expanding, const cplx *U, const double *phi, double *fE,
              double *fpi) {
     double tb = expanding ? tau : 1.0, tp = expanding ? 1.0 / tau : 1.0;
@@ -108,7 +97,7 @@ void o_force(int n, double tau, int expanding, const cplx *U, const double *phi,
         /* E_x */
         o_transport(U + 18 * sym + 9, F + 8 * sym, tr);
         o_conj_by(U + 18 * s + 0, phi + 8 * sxp, psi);
-        icomm(phi + 8 * s, psi, cm);
+        o_icomm(phi + 8 * s, psi, cm);
         for (int a = 0; a < 8; a++) fE[16 * s + a] = tb * (-F[8 * s + a] + tr[a]) - tp * cm[a];
         double lap[8];
         for (int a = 0; a < 8; a++) lap[a] = psi[a] - 2.0 * phi[8 * s + a];
@@ -117,7 +106,7 @@ void o_force(int n, double tau, int expanding, const cplx *U, const double *phi,
         /* E_y */
         o_transport(U + 18 * sxm + 0, F + 8 * sxm, tr);
         o_conj_by(U + 18 * s + 9, phi + 8 * syp, psi);
-        icomm(phi + 8 * s, psi, cm);
+        o_icomm(phi + 8 * s, psi, cm);
         for (int a = 0; a < 8; a++) fE[16 * s + 8 + a] = tb * (F[8 * s + a] - tr[a]) - tp * cm[a];
         for (int a = 0; a < 8; a++) lap[a] += psi[a] - 2.0 * phi[8 * s + a];
         o_transport(U + 18 * sym + 9, phi + 8 * sym, chi);
@@ -170,7 +159,7 @@ void o_gauss(int n, const cplx *U, const double *E, const double *phi, const dou
             for (int a = 0; a < 8; a++) g[a] -= tr[a];
             o_transport(U + 18 * sym + 9, E + 16 * sym + 8, tr);
             for (int a = 0; a < 8; a++) g[a] -= tr[a];
-            icomm(phi + 8 * s, pi + 8 * s, cm);
+            o_icomm(phi + 8 * s, pi + 8 * s, cm);
             for (int a = 0; a < 8; a++) G[8 * s + a] = g[a] + cm[a];
         }
 }

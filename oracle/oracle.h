@@ -40,6 +40,7 @@ void o_exp_i(const double x[8], cplx U[9]);              /* U = exp(i x^a t^a) *
 void o_expm(const cplx A[9], cplx R[9]);                 /* R = exp(A), any 3x3 */
 void o_transport(const cplx U[9], const double x[8], double y[8]); /* y = U^dag X U */
 void o_conj_by(const cplx U[9], const double x[8], double y[8]);   /* y = U X U^dag */
+void o_icomm(const double a[8], const double b[8], double c[8]);   /* c = i[A, B] */
 void o_structure_constants(double f[512], double d[512]);
 void o_haar(const double g[18], cplx U[9]);  /* U(3) Haar from 9 complex Gaussians */
 void o_reunitarize(cplx U[9]);
@@ -115,6 +116,8 @@ double o_mlp_loss_backward(int batch, const double *x, const double *target,
                            double *gW1, double *gb1, double *gW2, double *gb2,
                            double *gW3, double *gb3);
 void o_ic_features(const cplx U1[9], const cplx U2[9], double feat[36]);
-int o_su3_log(const cplx U[9], double x[8]);
+void o_ic_series(const cplx U1[9], const cplx U2[9], double ds[8]);
+void o_ic_delta(const cplx U1[9], const cplx U2[9], const cplx U[9], double delta[8]);
+void o_ic_target(const cplx U1[9], const cplx U2[9], const cplx U[9], double target[8]);
 
 #endif

@@ -218,3 +218,14 @@ double o_unitarity_dev(const cplx U[9]) {
     double dd = cabs(o_det(U) - 1.0);
     return dd > m ? dd : m;
 }
+
+/* components of i[A, B] for Hermitian A = a^a t^a, B = b^a t^a */
+void o_icomm(const double a[8], const double b[8], double out[8]) {
+    cplx A[9], B[9], AB[9], BA[9], C[9];
+    o_alg_to_mat(a, A);
+    o_alg_to_mat(b, B);
+    o_mul(A, B, AB);
+    o_mul(B, A, BA);
+    for (int k = 0; k < 9; k++) C[k] = I * (AB[k] - BA[k]);
+    o_mat_to_alg(C, out);
+}

@@ -21,6 +21,9 @@ from .api import (  # noqa: F401
     Batch,
     Glasma,
     HBARC,
+    WarmStartNet,
+    ic_dataset,
+    init_warm,
     broadening_accumulate,
     cpic_create,
     cpic_init,

@@ -105,6 +105,18 @@ SIGNATURES = {
     "glasma_batch_get_particles": (C.c_int, [_p, _i32] + [_p] * 7),
     "glasma_batch_destroy": (None, [_p]),
     "glasma_diagnostics_noalloc": (C.c_int, [_p, _i32, _i32, _i32, _d, _p, _p]),
+    "glasma_mlp_workspace_bytes": (_i64, []),
+    "glasma_mlp_create": (C.c_int, [_p, _i64, C.c_uint64, _p, _pp]),
+    "glasma_mlp_destroy": (None, [_p]),
+    "glasma_mlp_set_scales": (C.c_int, [_p, C.c_float, C.c_float]),
+    "glasma_mlp_fit_scales": (C.c_int, [_p, _p, _p, _i64]),
+    "glasma_mlp_train": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, C.c_float, C.POINTER(_d)]),
+    "glasma_mlp_loss_grad": (C.c_int, [_p, _p, _p, _i64, C.POINTER(_d), _p]),
+    "glasma_mlp_predict": (C.c_int, [_p, _p, _i64, _p]),
+    "glasma_mlp_get_params": (C.c_int, [_p, _p, _p]),
+    "glasma_mlp_set_params": (C.c_int, [_p, _p]),
+    "glasma_ic_dataset": (C.c_int, [_p, _p, _p]),
+    "glasma_init_warm": (C.c_int, [_p, _p]),
     "glasma_last_error": (C.c_char_p, []),
 }
 

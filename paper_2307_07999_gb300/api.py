@@ -127,6 +127,92 @@ class Glasma:
             self.handle = None
 
 
+class WarmStartNet:
+    """The warm-start network of the tau = 0+ link solve (see include/glasma.h)."""
+
+    N_PARAMS = 23312
+    SHAPES = (("W1", (128, 36)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (16, 128)),
+              ("b3", (16,)))
+
+    def __init__(self, seed=7, device="cuda", stream=None):
+        nb = lib().glasma_mlp_workspace_bytes()
+        self._ws, ptr = _workspace(nb, device)
+        h = C.c_void_p()
+        check(lib().glasma_mlp_create(C.c_void_p(ptr), nb, seed, _stream_ptr(stream), C.byref(h)))
+        self.handle = h
+
+    @staticmethod
+    def _t(x):
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+        return C.c_void_p(x.data_ptr())
+
+    def fit_scales(self, X, T):
+        check(lib().glasma_mlp_fit_scales(self.handle, self._t(X), self._t(T), X.shape[0]))
+
+    def set_scales(self, xs, ys):
+        check(lib().glasma_mlp_set_scales(self.handle, xs, ys))
+
+    def train(self, X, T, epochs=1, batch=4096, lr=1e-3):
+        loss = C.c_double()
+        check(lib().glasma_mlp_train(self.handle, self._t(X), self._t(T), X.shape[0], epochs, batch, lr,
+                                     C.byref(loss)))
+        return loss.value
+
+    def loss_grad(self, X, T):
+        loss = C.c_double()
+        g = np.zeros(self.N_PARAMS, dtype=np.float32)
+        check(lib().glasma_mlp_loss_grad(self.handle, self._t(X), self._t(T), X.shape[0], C.byref(loss), _dp(g)))
+        return loss.value, self.unflatten(g)
+
+    def predict(self, X):
+        Y = torch.empty((X.shape[0], 8), dtype=torch.float32, device=X.device)
+        check(lib().glasma_mlp_predict(self.handle, self._t(X), X.shape[0], self._t(Y)))
+        return Y
+
+    def params(self):
+        p = np.zeros(self.N_PARAMS, dtype=np.float32)
+        sc = np.zeros(2, dtype=np.float32)
+        check(lib().glasma_mlp_get_params(self.handle, _dp(p), _dp(sc)))
+        return self.unflatten(p), sc
+
+    def set_params(self, d):
+        flat = np.concatenate([np.asarray(d[k], dtype=np.float32).reshape(-1) for k, _ in self.SHAPES])
+        check(lib().glasma_mlp_set_params(self.handle, _dp(flat)))
+
+    @classmethod
+    def unflatten(cls, flat):
+        out, o = {}, 0
+        for k, s in cls.SHAPES:
+            n = int(np.prod(s))
+            out[k] = flat[o:o + n].reshape(s)
+            o += n
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib().glasma_mlp_destroy(h)
+            self.handle = None
+
+
+def ic_dataset(glasma):
+    """Features [2 n^2, 36] and targets [2 n^2, 8] (device FP32) of the context's last
+    initial condition."""
+    nl = 2 * glasma.n * glasma.n
+    X = torch.empty((nl, 36), dtype=torch.float32, device="cuda")
+    T = torch.empty((nl, 8), dtype=torch.float32, device="cuda")
+    check(lib().glasma_ic_dataset(glasma.handle, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr())))
+    return X, T
+
+
+def init_warm(glasma, net):
+    """glasma_init_warm: MV initial conditions with the network's Newton starts."""
+    st = lib().glasma_init_warm(glasma.handle, net.handle)
+    if st not in (0, -5):
+        check(st)
+    return glasma.ic_stats()
+
+
 class CPIC:
     """A particle ensemble bound to a Glasma context."""
 

@@ -125,7 +125,7 @@ extern "C" glasma_status glasma_create(const glasma_params* p, void* ws, int64_t
 
 extern "C" void glasma_destroy(glasma_ctx* g) { delete g; }
 
-extern "C" glasma_status glasma_init(glasma_ctx* g) {
+static glasma_status init_impl(glasma_ctx* g, glasma_mlp* mlp) {
     if (!g) return fail(GLASMA_ERR_INVALID, "null context");
     if (!g->p.expanding) return fail(GLASMA_ERR_INVALID, "MV initial conditions need the expanding evolution");
     const ICScratch sc = ic_layout(g->ic_base, g->n, g->fft_work);
@@ -133,12 +133,28 @@ extern "C" glasma_status glasma_init(glasma_ctx* g) {
     const int tol_it = g->p.newton_max_iter > 0 ? g->p.newton_max_iter : 100;
     const double tol = g->p.newton_tol > 0 ? g->p.newton_tol : 1e-12;
     int rc = ic_run(g->prec, g->n, g->p.n_sheets, g->p.g2mu_GeV * g->a_gev, g->p.m_ir_GeV * g->a_gev, g->p.seed,
-                    g->dtau, tol, tol_it, sc, g->buf[0], g->st, &g->ic_fails, &g->ic_mean, &g->ic_max, &err);
+                    g->dtau, tol, tol_it, sc, g->buf[0], g->st, &g->ic_fails, &g->ic_mean, &g->ic_max, &err, mlp);
     if (rc == -6) return fail(GLASMA_ERR_NOSPACE, "%s", err);
     if (rc != 0) return fail(GLASMA_ERR_CUDA, "%s", err);
     g->cur = 0;
     g->step = 1;
     return g->ic_fails ? fail(GLASMA_ERR_NOCONV, "some tau=0+ links did not converge") : GLASMA_OK;
+}
+
+extern "C" glasma_status glasma_init(glasma_ctx* g) { return init_impl(g, nullptr); }
+
+extern "C" glasma_status glasma_init_warm(glasma_ctx* g, glasma_mlp* mlp) {
+    if (!mlp) return fail(GLASMA_ERR_INVALID, "null network");
+    return init_impl(g, mlp);
+}
+
+extern "C" glasma_status glasma_ic_dataset(glasma_ctx* g, float* X, float* T) {
+    if (!g || !X || !T) return fail(GLASMA_ERR_INVALID, "null argument");
+    if (g->step < 0) return fail(GLASMA_ERR_INVALID, "no initial condition to read");
+    const ICScratch sc = ic_layout(g->ic_base, g->n, g->fft_work);
+    CK(launch_ic_features(sc, g->n, X, T, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return GLASMA_OK;
 }
 
 extern "C" glasma_status glasma_ic_stats(const glasma_ctx* g, int64_t* failures, double* mean_iter, int32_t* max_iter) {

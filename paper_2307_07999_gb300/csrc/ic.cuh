@@ -6,7 +6,9 @@
 //   Wilson    V_A <- exp(-i Lambda_{A,n}) V_A, sheet 1 first
 //   links     U^(A)_i(x) = V_A(x) V_A(x+i)^dag
 //   matching  Im Tr[t^a (U1 + U2)(1 + U^dag)] = 0, Newton in U <- exp(i d.t) U, step
-//             halving, start U1 U2 (restart from 1 if it stalls)
+//             halving, start U1 U2 (restart from 1 if it stalls); the warm start
+//             exp(i (d_series + d_net).t) U1 U2 adds a third-order series and a
+//             learned correction (mlp.cu)
 //   pi(0)     -(i/4) sum_i {[(U-1)(U2^dag - U1^dag) - h.c.](x) + [(U^dag-1)(U2 - U1) - h.c.](x-i)}
 // All initial-condition arithmetic is FP64, whatever the evolution precision.
 #pragma once
@@ -144,6 +146,28 @@ DEV bool solve8(double J[8][8], double b[8], double d[8]) {
         d[i] = s / J[i][i];
     }
     return true;
+}
+// Small-field series of the solution's offset from U1 U2: U = exp(i d.t) U1 U2 with
+//   d = -c/2 - (3/8) i[a1, c] - (1/8) i[a2, c] + O(a^4),  a_k = im_tl(U_k), c = i[a1, a2]
+// (obtained by expanding the matching condition order by order in the link fields).
+struct IcSeries {
+    Al<double> a1, a2, c, cubic;  // cubic = d + c/2
+};
+DEV IcSeries ic_series(const M3<double>& U1, const M3<double>& U2) {
+    IcSeries q;
+    q.a1 = im_tl(U1);
+    q.a2 = im_tl(U2);
+    q.c = icomm(q.a1, q.a2);
+    const Al<double> c1 = icomm(q.a1, q.c), c2 = icomm(q.a2, q.c);
+#pragma unroll
+    for (int a = 0; a < 8; a++) q.cubic.a[a] = -0.375 * c1.a[a] - 0.125 * c2.a[a];
+    return q;
+}
+DEV Al<double> series_offset(const IcSeries& q) {
+    Al<double> d;
+#pragma unroll
+    for (int a = 0; a < 8; a++) d.a[a] = -0.5 * q.c.a[a] + q.cubic.a[a];
+    return d;
 }
 // Newton with step halving from the given U; returns iterations or -1
 DEV int newton_link(const M3<double>& U1, const M3<double>& U2, M3<double>& U, double tol, int max_iter,

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+struct glasma_mlp;  // the warm-start network (mlp.cu)
+
 namespace glasma {
 
 constexpr int N_FIELD_PLANES = 56;
@@ -90,13 +92,18 @@ struct ICScratch {
     int* iters;               // [2 ns]
     double* res;              // [2 ns]
     void* fft_work; size_t fft_work_bytes;
+    float* X;                 // [2 ns][36] warm-start features
+    float* D;                 // [2 ns][8]  predicted starting corrections
 };
 size_t ic_scratch_bytes(int n, size_t fft_work_bytes);
 ICScratch ic_layout(void* base, int n, size_t fft_work_bytes);
 // full MV pipeline; writes the state at step 1 into buf; fails/iters summary into host ints
+// mlp (nullable): the warm-start network proposes each link's Newton start
 int ic_run(int prec, int n, int n_sheets, double g2mua, double m_ir_a, uint64_t seed, double dtau, double tol,
            int max_iter, const ICScratch& s, void* buf, cudaStream_t st, long long* fails, double* mean_it,
-           int* max_it, const char** err);
+           int* max_it, const char** err, ::glasma_mlp* mlp = nullptr);
 size_t ic_fft_work_bytes(int n, const char** err);
+cudaError_t launch_ic_features(const ICScratch& s, int n, float* X, float* T, cudaStream_t st);
+cudaError_t mlp_predict_dev(::glasma_mlp* M, const float* X, int64_t N, float* Y, cudaStream_t st);
 
 }  // namespace glasma

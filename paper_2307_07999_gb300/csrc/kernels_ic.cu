@@ -12,7 +12,8 @@ namespace glasma {
 size_t ic_scratch_bytes(int n, size_t fft_work_bytes) {
     const size_t ns = (size_t)n * n;
     return 2 * align256(ns * 18 * 8) + align256(ns * 8 * 16) + align256(ns * 36 * 8) + align256(ns * 8 * 8) +
-           align256(2 * ns * 4) + align256(2 * ns * 8) + align256(fft_work_bytes) + 256;
+           align256(2 * ns * 4) + align256(2 * ns * 8) + align256(fft_work_bytes) + align256(2 * ns * 36 * 4) +
+           align256(2 * ns * 8 * 4) + 256;
 }
 ICScratch ic_layout(void* base, int n, size_t fft_work_bytes) {
     const size_t ns = (size_t)n * n;
@@ -27,6 +28,9 @@ ICScratch ic_layout(void* base, int n, size_t fft_work_bytes) {
     s.res = (double*)p; p += align256(2 * ns * 8);
     s.fft_work = p;
     s.fft_work_bytes = fft_work_bytes;
+    p += align256(fft_work_bytes);
+    s.X = (float*)p; p += align256(2 * ns * 36 * 4);
+    s.D = (float*)p;
     return s;
 }
 
@@ -99,9 +103,13 @@ DEV M3<double> nucleus_link(const double* V, int n, int x, int y, int d) {
     const int yn = d == 1 ? (y == n - 1 ? 0 : y + 1) : y;
     return mul_nd(ld18(V + 18 * (x + (size_t)n * y)), ld18(V + 18 * (xn + (size_t)n * yn)));
 }
+// Newton solve per link.  Start: exp(i (d_s + delta).t) U1 U2 when a predicted
+// correction delta is given (d_s the third-order series of ic.cuh), else U1 U2; on
+// a stall, restart from U1 U2 (after a warm start) and then from 1.  The iteration
+// count includes every attempt.
 __global__ void k_links_solve(const double* __restrict__ V1, const double* __restrict__ V2, int n, double tol,
                               int max_iter, double* __restrict__ U, int* __restrict__ iters,
-                              double* __restrict__ res) {
+                              double* __restrict__ res, const float* __restrict__ delta) {
     const size_t ns = (size_t)n * n;
     const size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (l >= 2 * ns) return;
@@ -109,14 +117,31 @@ __global__ void k_links_solve(const double* __restrict__ V1, const double* __res
     const int d = (int)(l & 1);
     const int x = (int)(s % n), y = (int)(s / n);
     const M3<double> U1 = nucleus_link(V1, n, x, y, d), U2 = nucleus_link(V2, n, x, y, d);
-    M3<double> u = mul(U1, U2);
+    const M3<double> P = mul(U1, U2);
+    M3<double> u = P;
+    int spent = 0;
     double r;
-    int it = newton_link(U1, U2, u, tol, max_iter, r);
+    int it;
+    if (delta) {
+        Al<double> dl = series_offset(ic_series(U1, U2));
+#pragma unroll
+        for (int a = 0; a < 8; a++) dl.a[a] += (double)delta[8 * l + a];
+        u = mul(expi(herm(dl)), P);
+        it = newton_link(U1, U2, u, tol, max_iter, r);
+        if (it < 0) {
+            spent = max_iter;
+            u = P;
+            it = newton_link(U1, U2, u, tol, max_iter, r);
+        }
+    } else {
+        it = newton_link(U1, U2, u, tol, max_iter, r);
+    }
     if (it < 0) {
+        spent += max_iter;
         u = ident();
         it = newton_link(U1, U2, u, tol, max_iter, r);
-        if (it >= 0) it += max_iter;
     }
+    if (it >= 0) it += spent;
     st18(U + 36 * s + 18 * d, u);
     iters[l] = it;
     res[l] = r;
@@ -188,7 +213,7 @@ __global__ void k_ic_finalize(const double* __restrict__ U, const double* __rest
 
 int ic_run(int prec, int n, int n_sheets, double g2mua, double m_ir_a, uint64_t seed, double dtau, double tol,
            int max_iter, const ICScratch& s, void* buf, cudaStream_t st, long long* fails, double* mean_it,
-           int* max_it, const char** err) {
+           int* max_it, const char** err, ::glasma_mlp* mlp) {
     const size_t ns = (size_t)n * n;
     const uint2 key = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
     const double sigma = g2mua / sqrt((double)n_sheets);
@@ -221,7 +246,12 @@ int ic_run(int prec, int n, int n_sheets, double g2mua, double m_ir_a, uint64_t 
             k_wilson_accum<<<nb, 256, 0, st>>>(fb, V, n);
         }
     }
-    k_links_solve<<<(int)((2 * ns + 63) / 64), 64, 0, st>>>(s.V1, s.V2, n, tol, max_iter, s.U, s.iters, s.res);
+    if (mlp) {
+        IC_CHECK(launch_ic_features(s, n, s.X, nullptr, st));
+        IC_CHECK(mlp_predict_dev(mlp, s.X, (int64_t)(2 * ns), s.D, st));
+    }
+    k_links_solve<<<(int)((2 * ns + 63) / 64), 64, 0, st>>>(s.V1, s.V2, n, tol, max_iter, s.U, s.iters, s.res,
+                                                            mlp ? s.D : nullptr);
     k_pi0<<<nb, 256, 0, st>>>(s.V1, s.V2, s.U, n, s.pi0);
     if (prec) k_ic_finalize<float><<<nb, 256, 0, st>>>(s.U, s.pi0, n, dtau, (float*)buf);
     else k_ic_finalize<double><<<nb, 256, 0, st>>>(s.U, s.pi0, n, dtau, (double*)buf);
