@@ -145,12 +145,15 @@ void glasma_destroy(glasma_ctx* g);
  *   fields: device pointer to one field buffer in the library's plane layout
  *           (56 planes of n*n reals of the given precision, site s = x + n*y:
  *           U_x rows 0-1 as 12 planes (entry-major, re then im), U_y likewise,
- *           E_x^a, E_y^a, phi^a, pi^a as 8 planes each), read only.
+ *           E_x^a, E_y^a, phi^a, pi^a as 8 planes each; the planes are grouped
+ *           by four, interleaved per site: plane p of site s is element
+ *           ((p / 4) * n*n + s) * 4 + p % 4), read only, 16-byte aligned.
  *   tau: tau in lattice units (divides E and D phi in the expanding case).
  *   out: host double[8], as glasma_diagnostics.
  * Scratch: a file-scope device array of 4096 x 8 doubles (256 KB) that every
  * GPU which loads the library holds until the process exits; n*n above
- * 1,048,576 sites is rejected with GLASMA_ERR_INVALID.  The first call on a
+ * 1,048,576 sites, or an unaligned buffer, is rejected with GLASMA_ERR_INVALID.  The
+ * first call on a
  * device resolves the array's address on that device (make it before any
  * stream capture).  All calls share the array: calls that overlap on the GPU
  * (other streams or threads) race.  Allocates nothing; synchronises stream. */

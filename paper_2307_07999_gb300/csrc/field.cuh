@@ -7,6 +7,11 @@
 //   planes 12..23 : U_y rows 0,1
 //   planes 24..31 : E_x^a        planes 32..39 : E_y^a
 //   planes 40..47 : phi^a        planes 48..55 : pi^a
+// The planes come in 14 groups of four, each group interleaved per site: plane p of
+// site s sits at ((p / 4) * n*n + s) * 4 + p % 4.  Four consecutive planes of a site
+// are one 16-byte (FP32) or 32-byte (FP64) vector, so a link is three vector loads
+// and an algebra field two, coalesced across a warp of consecutive sites and one
+// sector each for a particle's scattered gather.
 // Staggering: U, phi at tau_n;  E, pi at tau_{n-1/2}.
 #pragma once
 #include "su3.cuh"
@@ -29,6 +34,8 @@ template <class T> struct StepArgs {
 
 struct TileItem { int ev, x0, y0; };
 
+DEV size_t fidx(int p, size_t s, size_t ns) { return (((size_t)(p >> 2) * ns + s) << 2) + (p & 3); }
+
 // Global loads of field data: through the read-only cache when the data is constant for
 // the whole kernel (CG = false), at L2 (coherent) inside a persistent kernel that also
 // writes the buffers it reads in later phases (CG = true).
@@ -36,37 +43,55 @@ template <bool CG, class T> DEV T ldf(const T* p) {
     if constexpr (CG) return __ldcg(p);
     else return __ldg(p);
 }
+template <class T> struct V4 { T v[4]; };
+template <bool CG> DEV V4<float> ld4(const float* p) {
+    const float4 q = CG ? __ldcg(reinterpret_cast<const float4*>(p)) : __ldg(reinterpret_cast<const float4*>(p));
+    return V4<float>{{q.x, q.y, q.z, q.w}};
+}
+template <bool CG> DEV V4<double> ld4(const double* p) {
+    const double2* v = reinterpret_cast<const double2*>(p);
+    const double2 a = CG ? __ldcg(v) : __ldg(v), b = CG ? __ldcg(v + 1) : __ldg(v + 1);
+    return V4<double>{{a.x, a.y, b.x, b.y}};
+}
+DEV void st4(float* p, float a, float b, float c, float d) { *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d); }
+DEV void st4(double* p, double a, double b, double c, double d) {
+    double2* v = reinterpret_cast<double2*>(p);
+    v[0] = make_double2(a, b);
+    v[1] = make_double2(c, d);
+}
+// group-aligned plane0 (a multiple of 4): rows 0,1 of a link, third row completed
 template <class T, bool CG = false> DEV M3<T> load_link(const T* __restrict__ f, size_t ns, int plane0, size_t s) {
     M3<T> U;
 #pragma unroll
-    for (int r = 0; r < 2; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const int p = plane0 + 2 * (3 * r + c);
-            U.m[r][c] = mk(ldf<CG>(f + (size_t)p * ns + s), ldf<CG>(f + (size_t)(p + 1) * ns + s));
-        }
+    for (int k = 0; k < 3; k++) {
+        const V4<T> q = ld4<CG>(f + fidx(plane0 + 4 * k, s, ns));
+        // group k holds entries 2k and 2k+1 of rows 0,1 (row-major), re/im interleaved
+        U.m[(2 * k) / 3][(2 * k) % 3] = mk(q.v[0], q.v[1]);
+        U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(q.v[2], q.v[3]);
+    }
     complete_row2(U);
     return U;
 }
 template <class T> DEV void store_link(T* __restrict__ f, size_t ns, int plane0, size_t s, const M3<T>& U) {
 #pragma unroll
-    for (int r = 0; r < 2; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const int p = plane0 + 2 * (3 * r + c);
-            f[(size_t)p * ns + s] = U.m[r][c].r;
-            f[(size_t)(p + 1) * ns + s] = U.m[r][c].i;
-        }
+    for (int k = 0; k < 3; k++) {
+        const cx<T> a = U.m[(2 * k) / 3][(2 * k) % 3], b = U.m[(2 * k + 1) / 3][(2 * k + 1) % 3];
+        st4(f + fidx(plane0 + 4 * k, s, ns), a.r, a.i, b.r, b.i);
+    }
 }
 template <class T, bool CG = false> DEV Al<T> load_alg(const T* __restrict__ f, size_t ns, int plane0, size_t s) {
     Al<T> x;
 #pragma unroll
-    for (int a = 0; a < 8; a++) x.a[a] = ldf<CG>(f + (size_t)(plane0 + a) * ns + s);
+    for (int k = 0; k < 2; k++) {
+        const V4<T> q = ld4<CG>(f + fidx(plane0 + 4 * k, s, ns));
+#pragma unroll
+        for (int j = 0; j < 4; j++) x.a[4 * k + j] = q.v[j];
+    }
     return x;
 }
 template <class T> DEV void store_alg(T* __restrict__ f, size_t ns, int plane0, size_t s, const Al<T>& x) {
 #pragma unroll
-    for (int a = 0; a < 8; a++) f[(size_t)(plane0 + a) * ns + s] = x.a[a];
+    for (int k = 0; k < 2; k++) st4(f + fidx(plane0 + 4 * k, s, ns), x.a[4 * k], x.a[4 * k + 1], x.a[4 * k + 2], x.a[4 * k + 3]);
 }
 DEV int wrapi(int v, int n) { v %= n; return v < 0 ? v + n : v; }
 
@@ -127,8 +152,9 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
                     b[(2 * (3 * r + c) + 1) * HS] = U.m[r][c].i;
                 }
         }
+        const Al<T> ph = load_alg<T, CG>(src, ns, P_PHI, g);
 #pragma unroll
-        for (int a = 0; a < 8; a++) sP[a * HS + h] = ldf<CG>(src + (size_t)(P_PHI + a) * ns + g);
+        for (int a = 0; a < 8; a++) sP[a * HS + h] = ph.a[a];
     }
     __syncthreads();
 

@@ -87,8 +87,9 @@ DEV void fused_tile(const StepArgs<T>& A, const PushArgs<T>& PA, int x0, int y0,
                     b[(2 * (3 * r + c) + 1) * HS] = U.m[r][c].i;
                 }
         }
+        const Al<T> ph = load_alg(src, ns, P_PHI, g);
 #pragma unroll
-        for (int a = 0; a < 8; a++) sP[a * HS + h] = __ldg(src + (size_t)(P_PHI + a) * ns + g);
+        for (int a = 0; a < 8; a++) sP[a * HS + h] = ph.a[a];
     }
     __syncthreads();
     // phase 2: ImTL P on [x0-1, x0+TX) x [y0-1, y0+TY)

@@ -108,13 +108,13 @@ __global__ void k_from_canonical(const double* __restrict__ U, const double* __r
     for (int d = 0; d < 2; d++)
 #pragma unroll
         for (int k = 0; k < 12; k++)  // rows 0,1: entries 0..5, re/im
-            f[(size_t)(12 * d + k) * ns + s] = (T)U[s * 36 + 18 * d + k];
+            f[fidx(12 * d + k, s, ns)] = (T)U[s * 36 + 18 * d + k];
 #pragma unroll
-    for (int a = 0; a < 16; a++) f[(size_t)(P_EX + a) * ns + s] = (T)E[s * 16 + a];
+    for (int a = 0; a < 16; a++) f[fidx(P_EX + a, s, ns)] = (T)E[s * 16 + a];
 #pragma unroll
     for (int a = 0; a < 8; a++) {
-        f[(size_t)(P_PHI + a) * ns + s] = (T)phi[s * 8 + a];
-        f[(size_t)(P_PI + a) * ns + s] = (T)pi[s * 8 + a];
+        f[fidx(P_PHI + a, s, ns)] = (T)phi[s * 8 + a];
+        f[fidx(P_PI + a, s, ns)] = (T)pi[s * 8 + a];
     }
 }
 template <class T>
@@ -136,15 +136,15 @@ __global__ void k_to_canonical(const T* __restrict__ f, double* __restrict__ U, 
     }
     if (E) {
 #pragma unroll
-        for (int a = 0; a < 16; a++) E[s * 16 + a] = (double)f[(size_t)(P_EX + a) * ns + s];
+        for (int a = 0; a < 16; a++) E[s * 16 + a] = (double)f[fidx(P_EX + a, s, ns)];
     }
     if (phi) {
 #pragma unroll
-        for (int a = 0; a < 8; a++) phi[s * 8 + a] = (double)f[(size_t)(P_PHI + a) * ns + s];
+        for (int a = 0; a < 8; a++) phi[s * 8 + a] = (double)f[fidx(P_PHI + a, s, ns)];
     }
     if (pi) {
 #pragma unroll
-        for (int a = 0; a < 8; a++) pi[s * 8 + a] = (double)f[(size_t)(P_PI + a) * ns + s];
+        for (int a = 0; a < 8; a++) pi[s * 8 + a] = (double)f[fidx(P_PI + a, s, ns)];
     }
 }
 cudaError_t launch_state_from_canonical(int prec, const double* U, const double* E, const double* phi,

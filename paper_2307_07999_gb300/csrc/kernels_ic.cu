@@ -196,13 +196,13 @@ __global__ void k_ic_finalize(const double* __restrict__ U, const double* __rest
 #pragma unroll
     for (int d = 0; d < 2; d++)
 #pragma unroll
-        for (int k = 0; k < 12; k++) f[(size_t)(12 * d + k) * ns + s] = (T)U[36 * s + 18 * d + k];
+        for (int k = 0; k < 12; k++) f[fidx(12 * d + k, s, ns)] = (T)U[36 * s + 18 * d + k];
 #pragma unroll
-    for (int a = 0; a < 16; a++) f[(size_t)(P_EX + a) * ns + s] = T(0);
+    for (int a = 0; a < 16; a++) f[fidx(P_EX + a, s, ns)] = T(0);
 #pragma unroll
     for (int a = 0; a < 8; a++) {
-        f[(size_t)(P_PI + a) * ns + s] = (T)pi[8 * s + a];
-        f[(size_t)(P_PHI + a) * ns + s] = (T)(dtau * (0.5 * dtau) * pi[8 * s + a]);
+        f[fidx(P_PI + a, s, ns)] = (T)pi[8 * s + a];
+        f[fidx(P_PHI + a, s, ns)] = (T)(dtau * (0.5 * dtau) * pi[8 * s + a]);
     }
 }
 

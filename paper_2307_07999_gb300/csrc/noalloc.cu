@@ -135,6 +135,10 @@ extern "C" glasma_status glasma_diagnostics_noalloc(const void* fields, int32_t 
         glasma_set_error("glasma_diagnostics_noalloc: bad arguments");
         return GLASMA_ERR_INVALID;
     }
+    if (((uintptr_t)fields & 15) != 0) {
+        glasma_set_error("glasma_diagnostics_noalloc: field buffer not 16-byte aligned");
+        return GLASMA_ERR_INVALID;
+    }
     const size_t ns = (size_t)n * n;
     const size_t nb = (ns + NOALLOC_BLOCK - 1) / NOALLOC_BLOCK;
     if (nb > (size_t)NOALLOC_MAX_BLOCKS) {

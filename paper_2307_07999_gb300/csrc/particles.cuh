@@ -71,20 +71,13 @@ template <class T, bool CG = false> struct GlobalSrc {
     DEV M3<T> link(int d, int x, int y) const { return load_link<T, CG>(fo, ns, d == 0 ? P_UX : P_UY, at(x, y)); }
     DEV Al<T> phi(int x, int y) const { return load_alg<T, CG>(fo, ns, P_PHI, at(x, y)); }
     // (E_i(tau_{n-1/2}) + E_i(tau_{n+1/2})) / 2 on the link (x, y) -> (x, y) + i
-    DEV Al<T> eavg(int d, int x, int y) const {
-        Al<T> e;
-        const int p = d == 0 ? P_EX : P_EY;
-        const size_t s = at(x, y);
+    DEV Al<T> eavg(int d, int x, int y) const { return avg(d == 0 ? P_EX : P_EY, at(x, y)); }
+    DEV Al<T> piavg(int x, int y) const { return avg(P_PI, at(x, y)); }
+    DEV Al<T> avg(int p, size_t s) const {
+        Al<T> e = load_alg<T, CG>(fo, ns, p, s);
+        const Al<T> b = load_alg<T, CG>(fn, ns, p, s);
 #pragma unroll
-        for (int a = 0; a < 8; a++) e.a[a] = T(0.5) * (ldf<CG>(fo + (size_t)(p + a) * ns + s) + ldf<CG>(fn + (size_t)(p + a) * ns + s));
-        return e;
-    }
-    DEV Al<T> piavg(int x, int y) const {
-        Al<T> e;
-        const size_t s = at(x, y);
-#pragma unroll
-        for (int a = 0; a < 8; a++)
-            e.a[a] = T(0.5) * (ldf<CG>(fo + (size_t)(P_PI + a) * ns + s) + ldf<CG>(fn + (size_t)(P_PI + a) * ns + s));
+        for (int a = 0; a < 8; a++) e.a[a] = T(0.5) * (e.a[a] + b.a[a]);
         return e;
     }
 };

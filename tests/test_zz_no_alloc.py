@@ -17,7 +17,8 @@ torch = pytest.importorskip("torch")
 
 
 def plane_buffer(st, prec):
-    """The canonical state in the library's plane layout, on the device (caller-owned)."""
+    """The canonical state in the library's plane layout (56 planes, grouped by four and
+    interleaved per site), on the device (caller-owned)."""
     n = st.n
     ns = n * n
     f = np.zeros((56, ns))
@@ -29,7 +30,8 @@ def plane_buffer(st, prec):
     f[32:40] = st.E[:, 1].T
     f[40:48] = st.phi.T
     f[48:56] = st.pi.T
-    return torch.tensor(f.astype(np.float32 if prec else np.float64), device="cuda").contiguous()
+    g = f.reshape(14, 4, ns).transpose(0, 2, 1).reshape(-1)  # plane p, site s -> ((p//4) ns + s) 4 + p%4
+    return torch.tensor(g.astype(np.float32 if prec else np.float64), device="cuda").contiguous()
 
 
 def call(buf, n, prec, tau):
@@ -61,3 +63,11 @@ def test_noalloc_rejects_lattices_beyond_the_scratch():
     rc, _ = call(buf, 1025, 1, 1.0)
     assert rc == -1
     assert b"static scratch" in G.lib().glasma_last_error()
+
+
+def test_noalloc_rejects_unaligned_buffers():
+    buf = torch.zeros(4 * 56 * 64 + 4, dtype=torch.float32, device="cuda")
+    rc = G.lib().glasma_diagnostics_noalloc(C.c_void_p(buf.data_ptr() + 4), 8, 1, 1, 1.0, None,
+                                            np.zeros(8).ctypes.data_as(C.c_void_p))
+    assert rc == -1
+    assert b"aligned" in G.lib().glasma_last_error()
