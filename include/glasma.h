@@ -146,8 +146,8 @@ void glasma_destroy(glasma_ctx* g);
  *           (56 planes of n*n reals of the given precision, site s = x + n*y:
  *           U_x rows 0-1 as 12 planes (entry-major, re then im), U_y likewise,
  *           E_x^a, E_y^a, phi^a, pi^a as 8 planes each; the planes are grouped
- *           by four, interleaved per site: plane p of site s is element
- *           ((p / 4) * n*n + s) * 4 + p % 4), read only, 16-byte aligned.
+ *           by eight, interleaved per site: plane p of site s is element
+ *           ((p / 8) * n*n + s) * 8 + p % 8), read only, 16-byte aligned.
  *   tau: tau in lattice units (divides E and D phi in the expanding case).
  *   out: host double[8], as glasma_diagnostics.
  * Scratch: a file-scope device array of 4096 x 8 doubles (256 KB) that every

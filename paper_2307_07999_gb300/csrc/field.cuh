@@ -7,11 +7,11 @@
 //   planes 12..23 : U_y rows 0,1
 //   planes 24..31 : E_x^a        planes 32..39 : E_y^a
 //   planes 40..47 : phi^a        planes 48..55 : pi^a
-// The planes come in 14 groups of four, each group interleaved per site: plane p of
-// site s sits at ((p / 4) * n*n + s) * 4 + p % 4.  Four consecutive planes of a site
-// are one 16-byte (FP32) or 32-byte (FP64) vector, so a link is three vector loads
-// and an algebra field two, coalesced across a warp of consecutive sites and one
-// sector each for a particle's scattered gather.
+// The planes come in 7 groups of eight, each group interleaved per site: plane p of
+// site s sits at ((p / 8) * n*n + s) * 8 + p % 8.  A group of one site is one 32-byte
+// sector in FP32, loaded as two 16-byte vectors: a warp of consecutive sites reads
+// contiguous memory, and a particle's scattered gather touches few sectors (both
+// links of a cell: three; E_x and E_y: two; phi, pi: one each).
 // Staggering: U, phi at tau_n;  E, pi at tau_{n-1/2}.
 #pragma once
 #include "su3.cuh"
@@ -34,7 +34,7 @@ template <class T> struct StepArgs {
 
 struct TileItem { int ev, x0, y0; };
 
-DEV size_t fidx(int p, size_t s, size_t ns) { return (((size_t)(p >> 2) * ns + s) << 2) + (p & 3); }
+DEV size_t fidx(int p, size_t s, size_t ns) { return (((size_t)(p >> 3) * ns + s) << 3) + (p & 7); }
 
 // Global loads of field data: through the read-only cache when the data is constant for
 // the whole kernel (CG = false), at L2 (coherent) inside a persistent kernel that also
@@ -44,6 +44,7 @@ template <bool CG, class T> DEV T ldf(const T* p) {
     else return __ldg(p);
 }
 template <class T> struct V4 { T v[4]; };
+template <class T> struct V8 { T v[8]; };
 template <bool CG> DEV V4<float> ld4(const float* p) {
     const float4 q = CG ? __ldcg(reinterpret_cast<const float4*>(p)) : __ldg(reinterpret_cast<const float4*>(p));
     return V4<float>{{q.x, q.y, q.z, q.w}};
@@ -53,24 +54,98 @@ template <bool CG> DEV V4<double> ld4(const double* p) {
     const double2 a = CG ? __ldcg(v) : __ldg(v), b = CG ? __ldcg(v + 1) : __ldg(v + 1);
     return V4<double>{{a.x, a.y, b.x, b.y}};
 }
+// one plane group of a site: a 32-byte load in FP32 (sm_100 family 256-bit access;
+// the address is 32-byte aligned), two in FP64.  The non-coherent form is a plain
+// asm (it may be scheduled freely: the data is constant for the kernel); the
+// coherent form is volatile so that it stays on its side of the persistent
+// kernel's grid barriers.
+template <bool CG> DEV V8<float> ld8(const float* p) {
+    V8<float> r;
+    if constexpr (CG)
+        asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]),
+                       "=f"(r.v[6]), "=f"(r.v[7])
+                     : "l"(p)
+                     : "memory");
+    else
+        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+              "=f"(r.v[7])
+            : "l"(p));
+    return r;
+}
+template <bool CG> DEV V8<double> ld8(const double* p) {
+    const V4<double> a = ld4<CG>(p), b = ld4<CG>(p + 4);
+    return V8<double>{{a.v[0], a.v[1], a.v[2], a.v[3], b.v[0], b.v[1], b.v[2], b.v[3]}};
+}
 DEV void st4(float* p, float a, float b, float c, float d) { *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d); }
 DEV void st4(double* p, double a, double b, double c, double d) {
     double2* v = reinterpret_cast<double2*>(p);
     v[0] = make_double2(a, b);
     v[1] = make_double2(c, d);
 }
-// group-aligned plane0 (a multiple of 4): rows 0,1 of a link, third row completed
+DEV void st8(float* p, const V8<float>& x) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(x.v[0]), "f"(x.v[1]), "f"(x.v[2]),
+                 "f"(x.v[3]), "f"(x.v[4]), "f"(x.v[5]), "f"(x.v[6]), "f"(x.v[7])
+                 : "memory");
+}
+DEV void st8(double* p, const V8<double>& x) {
+    st4(p, x.v[0], x.v[1], x.v[2], x.v[3]);
+    st4(p + 4, x.v[4], x.v[5], x.v[6], x.v[7]);
+}
+// entry e = 0..5 of rows 0,1 of a link (row-major) from the 12 reals of its planes
+template <class T> DEV void put_entry(M3<T>& U, int e, T re, T im) { U.m[e / 3][e % 3] = mk(re, im); }
+
+// plane0 a multiple of 4 (planes plane0..plane0+3 are one aligned 4-vector): rows 0,1 of a
+// link, third row completed
 template <class T, bool CG = false> DEV M3<T> load_link(const T* __restrict__ f, size_t ns, int plane0, size_t s) {
     M3<T> U;
+    if (plane0 == P_UX) {  // planes 0..7 (group 0), 8..11 (first half of group 1)
+        const V8<T> a = ld8<CG>(f + fidx(0, s, ns));
+        const V4<T> b = ld4<CG>(f + fidx(8, s, ns));
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const V4<T> q = ld4<CG>(f + fidx(plane0 + 4 * k, s, ns));
-        // group k holds entries 2k and 2k+1 of rows 0,1 (row-major), re/im interleaved
-        U.m[(2 * k) / 3][(2 * k) % 3] = mk(q.v[0], q.v[1]);
-        U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(q.v[2], q.v[3]);
+        for (int e = 0; e < 4; e++) put_entry(U, e, a.v[2 * e], a.v[2 * e + 1]);
+        put_entry(U, 4, b.v[0], b.v[1]);
+        put_entry(U, 5, b.v[2], b.v[3]);
+    } else {  // planes 12..15 (second half of group 1), 16..23 (group 2)
+        const V4<T> a = ld4<CG>(f + fidx(12, s, ns));
+        const V8<T> b = ld8<CG>(f + fidx(16, s, ns));
+        put_entry(U, 0, a.v[0], a.v[1]);
+        put_entry(U, 1, a.v[2], a.v[3]);
+#pragma unroll
+        for (int e = 0; e < 4; e++) put_entry(U, 2 + e, b.v[2 * e], b.v[2 * e + 1]);
     }
     complete_row2(U);
     return U;
+}
+// both links of a site from its three link groups
+template <class T, bool CG = false> DEV void load_links(const T* __restrict__ f, size_t ns, size_t s, M3<T>& ux, M3<T>& uy) {
+    const V8<T> a = ld8<CG>(f + fidx(0, s, ns)), b = ld8<CG>(f + fidx(8, s, ns)), c = ld8<CG>(f + fidx(16, s, ns));
+#pragma unroll
+    for (int e = 0; e < 4; e++) put_entry(ux, e, a.v[2 * e], a.v[2 * e + 1]);
+    put_entry(ux, 4, b.v[0], b.v[1]);
+    put_entry(ux, 5, b.v[2], b.v[3]);
+    put_entry(uy, 0, b.v[4], b.v[5]);
+    put_entry(uy, 1, b.v[6], b.v[7]);
+#pragma unroll
+    for (int e = 0; e < 4; e++) put_entry(uy, 2 + e, c.v[2 * e], c.v[2 * e + 1]);
+    complete_row2(ux);
+    complete_row2(uy);
+}
+template <class T> DEV void store_links(T* __restrict__ f, size_t ns, size_t s, const M3<T>& ux, const M3<T>& uy) {
+    V8<T> a, b, c;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        a.v[2 * e] = ux.m[e / 3][e % 3].r;
+        a.v[2 * e + 1] = ux.m[e / 3][e % 3].i;
+        c.v[2 * e] = uy.m[(e + 2) / 3][(e + 2) % 3].r;
+        c.v[2 * e + 1] = uy.m[(e + 2) / 3][(e + 2) % 3].i;
+    }
+    b.v[0] = ux.m[1][1].r; b.v[1] = ux.m[1][1].i; b.v[2] = ux.m[1][2].r; b.v[3] = ux.m[1][2].i;
+    b.v[4] = uy.m[0][0].r; b.v[5] = uy.m[0][0].i; b.v[6] = uy.m[0][1].r; b.v[7] = uy.m[0][1].i;
+    st8(f + fidx(0, s, ns), a);
+    st8(f + fidx(8, s, ns), b);
+    st8(f + fidx(16, s, ns), c);
 }
 template <class T> DEV void store_link(T* __restrict__ f, size_t ns, int plane0, size_t s, const M3<T>& U) {
 #pragma unroll
@@ -79,28 +154,23 @@ template <class T> DEV void store_link(T* __restrict__ f, size_t ns, int plane0,
         st4(f + fidx(plane0 + 4 * k, s, ns), a.r, a.i, b.r, b.i);
     }
 }
+// plane0 a multiple of 8 (one group)
 template <class T, bool CG = false> DEV Al<T> load_alg(const T* __restrict__ f, size_t ns, int plane0, size_t s) {
+    const V8<T> q = ld8<CG>(f + fidx(plane0, s, ns));
     Al<T> x;
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const V4<T> q = ld4<CG>(f + fidx(plane0 + 4 * k, s, ns));
-#pragma unroll
-        for (int j = 0; j < 4; j++) x.a[4 * k + j] = q.v[j];
-    }
+    for (int a = 0; a < 8; a++) x.a[a] = q.v[a];
     return x;
 }
 template <class T> DEV void store_alg(T* __restrict__ f, size_t ns, int plane0, size_t s, const Al<T>& x) {
+    V8<T> q;
 #pragma unroll
-    for (int k = 0; k < 2; k++) st4(f + fidx(plane0 + 4 * k, s, ns), x.a[4 * k], x.a[4 * k + 1], x.a[4 * k + 2], x.a[4 * k + 3]);
+    for (int a = 0; a < 8; a++) q.v[a] = x.a[a];
+    st8(f + fidx(plane0, s, ns), q);
 }
 DEV int wrapi(int v, int n) { v %= n; return v < 0 ? v + n : v; }
 
-template <class T, int TX, int TY> struct Tile {
-    static constexpr int HX = TX + 2, HY = TY + 2, HS = HX * HY;
-    static constexpr int FX = TX + 1, FY = TY + 1, FS = FX * FY;
-    static constexpr size_t smem = sizeof(T) * (size_t)(2 * 18 * HS + 8 * HS + 8 * FS);
-};
-
+// SoA tile staging (one plane per entry): used by the fused field + push kernel
 template <class T, int HS> DEV M3<T> sm_link(const T* sU, int d, int h) {
     M3<T> U;
     const T* b = sU + d * 18 * HS + h;
@@ -117,14 +187,68 @@ template <class T, int S> DEV Al<T> sm_alg(const T* s, int h) {
     return x;
 }
 
+// Record tile staging of the field step: per site, a link as 20 reals (its 9 complex
+// entries and two of padding) and an algebra field as 12 reals (8 and four of padding),
+// moved as 16-byte vectors.  Record strides of 20 and 12 words put the eight threads
+// of a quarter warp on distinct banks.
+constexpr int REC_L = 20, REC_A = 12;
+template <class T, int TX, int TY> struct RecTile {
+    static constexpr int HX = TX + 2, HY = TY + 2, HS = HX * HY;
+    static constexpr int FX = TX + 1, FY = TY + 1, FS = FX * FY;
+    static constexpr size_t smem = sizeof(T) * (size_t)(2 * REC_L * HS + REC_A * HS + REC_A * FS);
+};
+DEV void lds_v(const float* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+DEV void lds_v(const double* p, double* o) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+}
+DEV void sts_v(float* p, const float* o) { *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]); }
+DEV void sts_v(double* p, const double* o) { *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]); }
+template <class T> DEV M3<T> rec_link(const T* sU, int h) {
+    constexpr int NV = 16 / sizeof(T);
+    T b[REC_L];
+#pragma unroll
+    for (int k = 0; k < REC_L; k += NV) lds_v(sU + h * REC_L + k, b + k);
+    M3<T> U;
+#pragma unroll
+    for (int e = 0; e < 9; e++) U.m[e / 3][e % 3] = mk(b[2 * e], b[2 * e + 1]);
+    return U;
+}
+template <class T> DEV void rec_put_link(T* sU, int h, const M3<T>& U) {
+    constexpr int NV = 16 / sizeof(T);
+    T b[REC_L];
+#pragma unroll
+    for (int e = 0; e < 9; e++) { b[2 * e] = U.m[e / 3][e % 3].r; b[2 * e + 1] = U.m[e / 3][e % 3].i; }
+    b[18] = T(0);
+    b[19] = T(0);
+#pragma unroll
+    for (int k = 0; k < REC_L; k += NV) sts_v(sU + h * REC_L + k, b + k);
+}
+template <class T> DEV Al<T> rec_alg(const T* s, int h) {
+    constexpr int NV = 16 / sizeof(T);
+    Al<T> x;
+#pragma unroll
+    for (int k = 0; k < 8; k += NV) lds_v(s + h * REC_A + k, x.a + k);
+    return x;
+}
+template <class T> DEV void rec_put_alg(T* s, int h, const Al<T>& x) {
+    constexpr int NV = 16 / sizeof(T);
+#pragma unroll
+    for (int k = 0; k < 8; k += NV) sts_v(s + h * REC_A + k, x.a + k);
+}
+
 // One tile [x0, x0+TX) x [y0, y0+TY) of one step: kick at tau_n, drift with tau_{n+1/2}.
 template <class T, int TX, int TY, bool CG = false>
 DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_raw) {
-    using G = Tile<T, TX, TY>;
+    using G = RecTile<T, TX, TY>;
     constexpr int HX = G::HX, HS = G::HS, FX = G::FX, FS = G::FS;
-    T* sU = reinterpret_cast<T*>(smem_raw);  // [2][18][HS]
-    T* sP = sU + 2 * 18 * HS;                // [8][HS]  phi
-    T* sF = sP + 8 * HS;                     // [8][FS]  ImTL of the plaquette
+    T* sUx = reinterpret_cast<T*>(smem_raw);  // [HS][REC_L]  U_x
+    T* sUy = sUx + REC_L * HS;                // [HS][REC_L]  U_y
+    T* sP = sUy + REC_L * HS;                 // [HS][REC_A]  phi
+    T* sF = sP + REC_A * HS;                  // [FS][REC_A]  ImTL of the plaquette
     const int n = A.n;
     const size_t ns = (size_t)n * n;
     const int tid = threadIdx.y * TX + threadIdx.x;
@@ -140,21 +264,11 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     for (int h = tid; h < HS; h += TX * TY) {
         const int hx = h % HX, hy = h / HX;
         const size_t g = (size_t)wrapi(x0 - 1 + hx, n) + (size_t)n * wrapi(y0 - 1 + hy, n);
-#pragma unroll
-        for (int d = 0; d < 2; d++) {
-            const M3<T> U = load_link<T, CG>(src, ns, d == 0 ? P_UX : P_UY, g);
-            T* b = sU + d * 18 * HS + h;
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    b[(2 * (3 * r + c)) * HS] = U.m[r][c].r;
-                    b[(2 * (3 * r + c) + 1) * HS] = U.m[r][c].i;
-                }
-        }
-        const Al<T> ph = load_alg<T, CG>(src, ns, P_PHI, g);
-#pragma unroll
-        for (int a = 0; a < 8; a++) sP[a * HS + h] = ph.a[a];
+        M3<T> ux, uy;
+        load_links<T, CG>(src, ns, g, ux, uy);
+        rec_put_link(sUx, h, ux);
+        rec_put_link(sUy, h, uy);
+        rec_put_alg(sP, h, load_alg<T, CG>(src, ns, P_PHI, g));
     }
     __syncthreads();
 
@@ -162,11 +276,9 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     for (int i = tid; i < FS; i += TX * TY) {
         const int fx = i % FX, fy = i / FX;
         const int h = fy * HX + fx;
-        const M3<T> a1 = mul(sm_link<T, HS>(sU, 0, h), sm_link<T, HS>(sU, 1, h + 1));
-        const M3<T> b1 = mul(sm_link<T, HS>(sU, 1, h), sm_link<T, HS>(sU, 0, h + HX));
-        const Al<T> F = im_tl(mul_nd(a1, b1));
-#pragma unroll
-        for (int a = 0; a < 8; a++) sF[a * FS + i] = F.a[a];
+        const M3<T> a1 = mul(rec_link(sUx, h), rec_link(sUy, h + 1));
+        const M3<T> b1 = mul(rec_link(sUy, h), rec_link(sUx, h + HX));
+        rec_put_alg(sF, i, im_tl(mul_nd(a1, b1)));
     }
     __syncthreads();
     if (!active) return;
@@ -174,30 +286,30 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     // phase 3: kick and drift of the own site
     const int h = (threadIdx.y + 1) * HX + threadIdx.x + 1;
     const int f = (threadIdx.y + 1) * FX + threadIdx.x + 1;
-    const Al<T> phi = sm_alg<T, HS>(sP, h);
-    const M3<T> ux = sm_link<T, HS>(sU, 0, h), uy = sm_link<T, HS>(sU, 1, h);
-    const M3<T> uxm = sm_link<T, HS>(sU, 0, h - 1), uym = sm_link<T, HS>(sU, 1, h - HX);
+    const Al<T> phi = rec_alg(sP, h);
+    const M3<T> ux = rec_link(sUx, h), uy = rec_link(sUy, h);
+    const M3<T> uxm = rec_link(sUx, h - 1), uym = rec_link(sUy, h - HX);
     const T dt = A.dtau, tb = A.tb, tp = A.tp;
 
-    const Al<T> psx = conj_alg(ux, sm_alg<T, HS>(sP, h + 1));
-    const Al<T> psy = conj_alg(uy, sm_alg<T, HS>(sP, h + HX));
+    const Al<T> psx = conj_alg(ux, rec_alg(sP, h + 1));
+    const Al<T> psy = conj_alg(uy, rec_alg(sP, h + HX));
     {
-        const Al<T> chx = transport_alg(uxm, sm_alg<T, HS>(sP, h - 1));
-        const Al<T> chy = transport_alg(uym, sm_alg<T, HS>(sP, h - HX));
+        const Al<T> chx = transport_alg(uxm, rec_alg(sP, h - 1));
+        const Al<T> chy = transport_alg(uym, rec_alg(sP, h - HX));
 #pragma unroll
         for (int a = 0; a < 8; a++)
             pi.a[a] += dt * tp * (psx.a[a] + chx.a[a] + psy.a[a] + chy.a[a] - T(4) * phi.a[a]);
     }
-    const Al<T> F0 = sm_alg<T, FS>(sF, f);
+    const Al<T> F0 = rec_alg(sF, f);
     {
         const Al<T> cm = icomm(phi, psx);
-        const Al<T> t1 = transport_alg(uym, sm_alg<T, FS>(sF, f - FX));
+        const Al<T> t1 = transport_alg(uym, rec_alg(sF, f - FX));
 #pragma unroll
         for (int a = 0; a < 8; a++) Ex.a[a] += dt * (tb * (t1.a[a] - F0.a[a]) - tp * cm.a[a]);
     }
     {
         const Al<T> cm = icomm(phi, psy);
-        const Al<T> t2 = transport_alg(uxm, sm_alg<T, FS>(sF, f - 1));
+        const Al<T> t2 = transport_alg(uxm, rec_alg(sF, f - 1));
 #pragma unroll
         for (int a = 0; a < 8; a++) Ey.a[a] += dt * (tb * (F0.a[a] - t2.a[a]) - tp * cm.a[a]);
     }
@@ -210,6 +322,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     for (int a = 0; a < 8; a++) phin.a[a] = phi.a[a] + A.pe * pi.a[a];
     store_alg(dst, ns, P_PHI, s, phin);
     // drift of the links: U <- exp(i ue E) U
+    M3<T> Vn[2];
 #pragma unroll
     for (int d = 0; d < 2; d++) {
         Al<T> e = d == 0 ? Ex : Ey;
@@ -221,15 +334,12 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
 #pragma unroll
         for (int r = 0; r < 2; r++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                cx<T> v = W.m[r][0] * U.m[0][c];
-                fma_(v, W.m[r][1], U.m[1][c]);
-                fma_(v, W.m[r][2], U.m[2][c]);
-                V.m[r][c] = v;
-            }
+            for (int c = 0; c < 3; c++)
+                V.m[r][c] = val(cmac(cmac(cmul(W.m[r][0], U.m[0][c]), W.m[r][1], U.m[1][c]), W.m[r][2], U.m[2][c]));
         if (A.reunit) reunit_rows(V);
-        store_link(dst, ns, d == 0 ? P_UX : P_UY, s, V);
+        Vn[d] = V;
     }
+    store_links(dst, ns, s, Vn[0], Vn[1]);
 }
 
 }  // namespace glasma

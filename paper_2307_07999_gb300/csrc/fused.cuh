@@ -13,8 +13,7 @@
 namespace glasma {
 
 template <class T, int TX, int TY> struct FusedTile {
-    using G = Tile<T, TX, TY>;
-    static constexpr int HX = G::HX, HS = G::HS, FX = G::FX, FS = G::FS;
+    static constexpr int HX = TX + 2, HS = HX * (TY + 2), FX = TX + 1, FS = FX * (TY + 1);
     static constexpr int SEX = (TX + 1) * TY;  // E_x average on x in [x0-1, x0+TX), y in tile
     static constexpr int SEY = TX * (TY + 1);  // E_y average on x in tile, y in [y0-1, y0+TY)
     static constexpr int SPI = TX * TY;        // pi average on the tile
@@ -41,6 +40,10 @@ template <class T, int TX, int TY> struct SmemSrc {
         return d + 1;
     }
     DEV M3<T> link(int d, int x, int y) const { return sm_link<T, FT::HS>(sU, d, hy(y) * FT::HX + hx(x)); }
+    DEV void links(int x, int y, M3<T>& ux, M3<T>& uy) const {
+        ux = link(0, x, y);
+        uy = link(1, x, y);
+    }
     DEV Al<T> phi(int x, int y) const { return sm_alg<T, FT::HS>(sP, hy(y) * FT::HX + hx(x)); }
     DEV Al<T> eavg(int d, int x, int y) const {
         if (d == 0) return sm_alg<T, FT::SEX>(sEx, (hy(y) - 1) * (TX + 1) + hx(x));
@@ -75,9 +78,11 @@ DEV void fused_tile(const StepArgs<T>& A, const PushArgs<T>& PA, int x0, int y0,
     for (int h = tid; h < HS; h += TX * TY) {
         const int hx = h % HX, hy = h / HX;
         const size_t g = (size_t)wrapi(x0 - 1 + hx, n) + (size_t)n * wrapi(y0 - 1 + hy, n);
+        M3<T> UU[2];
+        load_links(src, ns, g, UU[0], UU[1]);
 #pragma unroll
         for (int d = 0; d < 2; d++) {
-            const M3<T> U = load_link(src, ns, d == 0 ? P_UX : P_UY, g);
+            const M3<T>& U = UU[d];
             T* b = sU + d * 18 * HS + h;
 #pragma unroll
             for (int r = 0; r < 3; r++)
@@ -151,6 +156,7 @@ DEV void fused_tile(const StepArgs<T>& A, const PushArgs<T>& PA, int x0, int y0,
 #pragma unroll
         for (int a = 0; a < 8; a++) phin.a[a] = phi.a[a] + A.pe * pin.a[a];
         store_alg(dst, ns, P_PHI, s, phin);
+        M3<T> Vn[2];
 #pragma unroll
         for (int d = 0; d < 2; d++) {
             Al<T> e = d == 0 ? Exn : Eyn;
@@ -162,15 +168,12 @@ DEV void fused_tile(const StepArgs<T>& A, const PushArgs<T>& PA, int x0, int y0,
 #pragma unroll
             for (int r = 0; r < 2; r++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    cx<T> v = W.m[r][0] * U.m[0][c];
-                    fma_(v, W.m[r][1], U.m[1][c]);
-                    fma_(v, W.m[r][2], U.m[2][c]);
-                    V.m[r][c] = v;
-                }
+                for (int c = 0; c < 3; c++)
+                    V.m[r][c] = val(cmac(cmac(cmul(W.m[r][0], U.m[0][c]), W.m[r][1], U.m[1][c]), W.m[r][2], U.m[2][c]));
             if (A.reunit) reunit_rows(V);
-            store_link(dst, ns, d == 0 ? P_UX : P_UY, s, V);
+            Vn[d] = V;
         }
+        store_links(dst, ns, s, Vn[0], Vn[1]);
     }
     const bool push = PA.acc != nullptr && tcount > 0;
     // phase 3b: E_x on the halo column and E_y on the halo row (kick only)

@@ -60,7 +60,7 @@ int field_tile_y(int prec) { return prec ? TileCfg<float>::TY : TileCfg<double>:
 
 template <class T> static cudaError_t set_smem() {
     constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
-    const size_t sm = Tile<T, TX, TY>::smem;
+    const size_t sm = RecTile<T, TX, TY>::smem;
     static bool done = false;
     if (!done) {
         cudaError_t e = cudaFuncSetAttribute(k_field_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -77,7 +77,7 @@ template <class T> static cudaError_t step_impl(const StepHost& a, cudaStream_t 
     cudaError_t e = set_smem<T>();
     if (e != cudaSuccess) return e;
     dim3 grid((a.n + TX - 1) / TX, (a.n + TY - 1) / TY), block(TX, TY);
-    k_field_step<T><<<grid, block, Tile<T, TX, TY>::smem, st>>>(to_args<T>(a));
+    k_field_step<T><<<grid, block, RecTile<T, TX, TY>::smem, st>>>(to_args<T>(a));
     return cudaGetLastError();
 }
 cudaError_t launch_field_step(int prec, const StepHost& a, cudaStream_t st) {
@@ -88,7 +88,7 @@ template <class T> static cudaError_t batched_impl(const void* args, const void*
     cudaError_t e = set_smem<T>();
     if (e != cudaSuccess) return e;
     if (n_items <= 0 || !args) return cudaSuccess;
-    k_field_step_batched<T><<<n_items, dim3(TX, TY), Tile<T, TX, TY>::smem, st>>>((const StepArgs<T>*)args,
+    k_field_step_batched<T><<<n_items, dim3(TX, TY), RecTile<T, TX, TY>::smem, st>>>((const StepArgs<T>*)args,
                                                                               (const TileItem*)items);
     return cudaGetLastError();
 }
@@ -183,7 +183,8 @@ __global__ void k_monitors(const T* __restrict__ f, int n, double te, double* mo
         const int x = (int)(s % n), y = (int)(s / n);
         const size_t sxm = (x == 0 ? n - 1 : x - 1) + (size_t)n * y, sym = x + (size_t)n * (y == 0 ? n - 1 : y - 1);
         const size_t sxp = (x == n - 1 ? 0 : x + 1) + (size_t)n * y, syp = x + (size_t)n * (y == n - 1 ? 0 : y + 1);
-        const M3<T> ux = load_link(f, ns, P_UX, s), uy = load_link(f, ns, P_UY, s);
+        M3<T> ux, uy;
+        load_links(f, ns, s, ux, uy);
         const Al<T> ex = load_alg(f, ns, P_EX, s), ey = load_alg(f, ns, P_EY, s);
         const Al<T> phi = load_alg(f, ns, P_PHI, s), pi = load_alg(f, ns, P_PI, s);
         // Gauss law G = sum_i [E_i(x) - U_i(x-i)^dag E_i(x-i) U_i(x-i)] + i[phi, pi]

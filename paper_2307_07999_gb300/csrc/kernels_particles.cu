@@ -48,8 +48,9 @@ void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out) {
 }
 cudaError_t launch_push_batched(int prec, const void* args, const void* items, int n_items, cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
-    if (prec) k_push_batched<float><<<n_items, 256, 0, st>>>((const PushArgs<float>*)args, (const PushItem*)items);
-    else k_push_batched<double><<<n_items, 256, 0, st>>>((const PushArgs<double>*)args, (const PushItem*)items);
+    const unsigned nb = (unsigned)n_items * PUSH_SUB;
+    if (prec) k_push_batched<float><<<nb, PUSH_THREADS, 0, st>>>((const PushArgs<float>*)args, (const PushItem*)items);
+    else k_push_batched<double><<<nb, PUSH_THREADS, 0, st>>>((const PushArgs<double>*)args, (const PushItem*)items);
     return cudaGetLastError();
 }
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st) {

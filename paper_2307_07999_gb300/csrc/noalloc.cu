@@ -27,7 +27,8 @@ DEV void site_terms(const T* __restrict__ f, int n, size_t s, double te, double 
     const int x = (int)(s % n), y = (int)(s / n);
     const size_t sxm = (x == 0 ? n - 1 : x - 1) + (size_t)n * y, sym = x + (size_t)n * (y == 0 ? n - 1 : y - 1);
     const size_t sxp = (x == n - 1 ? 0 : x + 1) + (size_t)n * y, syp = x + (size_t)n * (y == n - 1 ? 0 : y + 1);
-    const M3<T> ux = load_link(f, ns, P_UX, s), uy = load_link(f, ns, P_UY, s);
+    M3<T> ux, uy;
+    load_links(f, ns, s, ux, uy);
     const Al<T> ex = load_alg(f, ns, P_EX, s), ey = load_alg(f, ns, P_EY, s);
     const Al<T> phi = load_alg(f, ns, P_PHI, s), pi = load_alg(f, ns, P_PI, s);
     const Al<T> tx = transport_alg(load_link(f, ns, P_UX, sxm), load_alg(f, ns, P_EX, sxm));

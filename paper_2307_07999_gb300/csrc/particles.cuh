@@ -39,13 +39,8 @@ template <class T> DEV M3<T> mul_dn(const M3<T>& A, const M3<T>& B) {  // A^dag 
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            cx<T> s = mk(T(0), T(0));
-            fmca_(s, A.m[0][i], B.m[0][j]);
-            fmca_(s, A.m[1][i], B.m[1][j]);
-            fmca_(s, A.m[2][i], B.m[2][j]);
-            C.m[i][j] = s;
-        }
+        for (int j = 0; j < 3; j++)
+            C.m[i][j] = val(ccmac(ccmac(ccmul(A.m[0][i], B.m[0][j]), A.m[1][i], B.m[1][j]), A.m[2][i], B.m[2][j]));
     return C;
 }
 template <class T> DEV T dot8(const Al<T>& a, const Al<T>& b) {
@@ -69,6 +64,7 @@ template <class T, bool CG = false> struct GlobalSrc {
     size_t ns;
     DEV size_t at(int x, int y) const { return (size_t)x + (size_t)n * y; }
     DEV M3<T> link(int d, int x, int y) const { return load_link<T, CG>(fo, ns, d == 0 ? P_UX : P_UY, at(x, y)); }
+    DEV void links(int x, int y, M3<T>& ux, M3<T>& uy) const { load_links<T, CG>(fo, ns, at(x, y), ux, uy); }
     DEV Al<T> phi(int x, int y) const { return load_alg<T, CG>(fo, ns, P_PHI, at(x, y)); }
     // (E_i(tau_{n-1/2}) + E_i(tau_{n+1/2})) / 2 on the link (x, y) -> (x, y) + i
     DEV Al<T> eavg(int d, int x, int y) const { return avg(d == 0 ? P_EX : P_EY, at(x, y)); }
@@ -89,8 +85,11 @@ DEV void gather_qf_src(const S& F, int n, T te, int cx, int cy, const Al<T>& q, 
     const int xm = cx == 0 ? n - 1 : cx - 1, xp = cx == n - 1 ? 0 : cx + 1;
     const int ym = cy == 0 ? n - 1 : cy - 1, yp = cy == n - 1 ? 0 : cy + 1;
     const T half = T(0.5);
-    const M3<T> ux_c = F.link(0, cx, cy), uy_c = F.link(1, cx, cy);
-    const M3<T> ux_xm = F.link(0, xm, cy), uy_ym = F.link(1, cx, ym);
+    // cells whose two links are both used load them together (three sectors in FP32)
+    M3<T> ux_c, uy_c, ux_xm, uy_xm, ux_ym, uy_ym;
+    F.links(cx, cy, ux_c, uy_c);
+    F.links(xm, cy, ux_xm, uy_xm);
+    F.links(cx, ym, ux_ym, uy_ym);
     // electric: the two links touching c, time-centred, transported to c
     {
         const Al<T> t = transport_alg(ux_xm, F.eavg(0, xm, cy));
@@ -116,20 +115,22 @@ DEV void gather_qf_src(const S& F, int n, T te, int cx, int cy, const Al<T>& q, 
     {
         Al<T> acc = im_tl(mul_nd(mul(ux_c, F.link(1, xp, cy)), mul(uy_c, F.link(0, cx, yp))));  // +x,+y
         {   // +y,-x: U_y(c) [U_y(c-x) U_x(c-x+y)]^dag U_x(c-x)
-            const M3<T> B = mul(F.link(1, xm, cy), F.link(0, xm, yp));
+            const M3<T> B = mul(uy_xm, F.link(0, xm, yp));
             const Al<T> t = im_tl(mul(mul_nd(uy_c, B), ux_xm));
 #pragma unroll
             for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
         }
         {   // -x,-y: [U_y(c-x-y) U_x(c-x)]^dag [U_x(c-x-y) U_y(c-y)]
-            const M3<T> B1 = mul(F.link(1, xm, ym), ux_xm);
-            const M3<T> B2 = mul(F.link(0, xm, ym), uy_ym);
+            M3<T> ux_xmym, uy_xmym;
+            F.links(xm, ym, ux_xmym, uy_xmym);
+            const M3<T> B1 = mul(uy_xmym, ux_xm);
+            const M3<T> B2 = mul(ux_xmym, uy_ym);
             const Al<T> t = im_tl(mul_dn(B1, B2));
 #pragma unroll
             for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
         }
         {   // -y,+x: U_y(c-y)^dag [U_x(c-y) U_y(c+x-y)] U_x(c)^dag
-            const M3<T> B = mul(F.link(0, cx, ym), F.link(1, xp, ym));
+            const M3<T> B = mul(ux_ym, F.link(1, xp, ym));
             const Al<T> t = im_tl(mul_nd(mul_dn(uy_ym, B), ux_c));
 #pragma unroll
             for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
@@ -261,16 +262,25 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<T> A) {
     block_acc4(sx, sy, sz, sc, A.acc);
 }
 
-// batched over events: one 256-particle block per item; args[ev] of this step
-// (acc == nullptr marks an event whose particles are not pushed at this step)
+// batched over events: one item per 256 particles of an event, pushed by
+// 256 / PUSH_THREADS blocks; args[ev] of this step (acc == nullptr marks an event
+// whose particles are not pushed at this step)
+#ifndef GLASMA_PUSH_THREADS
+#define GLASMA_PUSH_THREADS 256
+#endif
+#ifndef GLASMA_PUSH_MINB
+#define GLASMA_PUSH_MINB 1
+#endif
+constexpr int PUSH_THREADS = GLASMA_PUSH_THREADS, PUSH_SUB = 256 / GLASMA_PUSH_THREADS;
+static_assert(256 % GLASMA_PUSH_THREADS == 0 && GLASMA_PUSH_THREADS % 32 == 0, "push block");
 struct PushItem { int ev, j0; };
 template <class T>
-__global__ void __launch_bounds__(256) k_push_batched(const PushArgs<T>* __restrict__ args,
-                                                      const PushItem* __restrict__ items) {
-    const PushItem it = items[blockIdx.x];
+__global__ void __launch_bounds__(GLASMA_PUSH_THREADS, GLASMA_PUSH_MINB)
+k_push_batched(const PushArgs<T>* __restrict__ args, const PushItem* __restrict__ items) {
+    const PushItem it = items[blockIdx.x / PUSH_SUB];
     const PushArgs<T> A = args[it.ev];
     if (A.acc == nullptr) return;
-    const int j = it.j0 + threadIdx.x;
+    const int j = it.j0 + (int)(blockIdx.x % PUSH_SUB) * PUSH_THREADS + threadIdx.x;
     double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
     if (j < A.np) push_one(A, j, sx, sy, sz, sc);
     block_acc4(sx, sy, sz, sc, A.acc);

@@ -124,7 +124,7 @@ k_persistent(PersArgs<T> a) {
 
 template <class T> static glasma_status run_impl(glasma_batch* b) {
     constexpr int TX = PersCfg<T>::TX, TY = PersCfg<T>::TY;
-    const size_t sm = Tile<T, TX, TY>::smem;
+    const size_t sm = RecTile<T, TX, TY>::smem;
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(k_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)

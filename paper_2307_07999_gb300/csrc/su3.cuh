@@ -46,6 +46,101 @@ template <class T> DEV void fmca_(cx<T>& acc, cx<T> a, cx<T> b) {
     acc.i = fma(a.r, b.i, fma(-a.i, b.r, acc.i));
 }
 
+// ---------------------------------------------------------------- complex products
+// Accumulated complex products.  In FP32 they run on the sm_100-family paired FMA
+// (fma.rn.f32x2) with the complex number as the register pair (re, im):
+//   a b       = a.r (b.r, b.i) + a.i (-b.i, b.r)
+//   a conj(b) = a.r (b.r, -b.i) + a.i (b.i, b.r)
+//   conj(a) b = a.r (b.r, b.i) + a.i (b.i, -b.r)
+// two paired FMAs where the scalar form takes four (the broadcast pairs (a.r, a.r)
+// cost nothing; a negated lane costs one instruction, shared by every product that
+// reuses b).  FP64 keeps scalar FMAs.
+template <class T> struct CA;
+template <> struct CA<double> { cx<double> z; };
+template <> struct CA<float> { unsigned long long v; };
+
+DEV unsigned long long pk2(float a, float b) {
+    unsigned long long d;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(d) : "f"(a), "f"(b));
+    return d;
+}
+DEV cx<float> upk2(unsigned long long d) {
+    cx<float> z;
+    asm("mov.b64 {%0,%1}, %2;" : "=f"(z.r), "=f"(z.i) : "l"(d));
+    return z;
+}
+DEV unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+DEV unsigned long long fmul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+DEV unsigned long long fadd2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+DEV unsigned long long fsub2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+DEV cx<float> val(CA<float> a) { return upk2(a.v); }
+DEV cx<double> val(CA<double> a) { return a.z; }
+// a b
+DEV CA<float> cmul(cx<float> a, cx<float> b) {
+    return {ffma2(pk2(a.i, a.i), pk2(-b.i, b.r), fmul2(pk2(a.r, a.r), pk2(b.r, b.i)))};
+}
+DEV CA<double> cmul(cx<double> a, cx<double> b) { return {a * b}; }
+// acc + a b
+DEV CA<float> cmac(CA<float> c, cx<float> a, cx<float> b) {
+    return {ffma2(pk2(a.i, a.i), pk2(-b.i, b.r), ffma2(pk2(a.r, a.r), pk2(b.r, b.i), c.v))};
+}
+DEV CA<double> cmac(CA<double> c, cx<double> a, cx<double> b) { fma_(c.z, a, b); return c; }
+// a conj(b)
+DEV CA<float> cmulc(cx<float> a, cx<float> b) {
+    return {ffma2(pk2(a.i, a.i), pk2(b.i, b.r), fmul2(pk2(a.r, a.r), pk2(b.r, -b.i)))};
+}
+DEV CA<double> cmulc(cx<double> a, cx<double> b) { return {mulc(a, b)}; }
+// acc + a conj(b)
+DEV CA<float> cmacc(CA<float> c, cx<float> a, cx<float> b) {
+    return {ffma2(pk2(a.i, a.i), pk2(b.i, b.r), ffma2(pk2(a.r, a.r), pk2(b.r, -b.i), c.v))};
+}
+DEV CA<double> cmacc(CA<double> c, cx<double> a, cx<double> b) { fmac_(c.z, a, b); return c; }
+// conj(a) b
+DEV CA<float> ccmul(cx<float> a, cx<float> b) {
+    return {ffma2(pk2(a.i, a.i), pk2(b.i, -b.r), fmul2(pk2(a.r, a.r), pk2(b.r, b.i)))};
+}
+DEV CA<double> ccmul(cx<double> a, cx<double> b) { return {mk(a.r * b.r + a.i * b.i, a.r * b.i - a.i * b.r)}; }
+// acc + conj(a) b
+DEV CA<float> ccmac(CA<float> c, cx<float> a, cx<float> b) {
+    return {ffma2(pk2(a.i, a.i), pk2(b.i, -b.r), ffma2(pk2(a.r, a.r), pk2(b.r, b.i), c.v))};
+}
+DEV CA<double> ccmac(CA<double> c, cx<double> a, cx<double> b) { fmca_(c.z, a, b); return c; }
+// s b and acc + s b for real s
+DEV CA<float> rmul(float s, cx<float> b) { return {fmul2(pk2(s, s), pk2(b.r, b.i))}; }
+DEV CA<double> rmul(double s, cx<double> b) { return {s * b}; }
+DEV CA<float> rmac(CA<float> c, float s, cx<float> b) { return {ffma2(pk2(s, s), pk2(b.r, b.i), c.v)}; }
+DEV CA<double> rmac(CA<double> c, double s, cx<double> b) {
+    c.z.r = fma(s, b.r, c.z.r);
+    c.z.i = fma(s, b.i, c.z.i);
+    return c;
+}
+// Re(conj(a) b) summed over three pairs: the real part of a Hermitian product's diagonal
+DEV float redot3(cx<float> a0, cx<float> b0, cx<float> a1, cx<float> b1, cx<float> a2, cx<float> b2) {
+    const cx<float> p = upk2(ffma2(pk2(a2.r, a2.i), pk2(b2.r, b2.i),
+                                   ffma2(pk2(a1.r, a1.i), pk2(b1.r, b1.i), fmul2(pk2(a0.r, a0.i), pk2(b0.r, b0.i)))));
+    return p.r + p.i;
+}
+DEV double redot3(cx<double> a0, cx<double> b0, cx<double> a1, cx<double> b1, cx<double> a2, cx<double> b2) {
+    return fma(a2.r, b2.r, fma(a2.i, b2.i, fma(a1.r, b1.r, fma(a1.i, b1.i, fma(a0.r, b0.r, a0.i * b0.i)))));
+}
+
 template <class T> struct M3 { cx<T> m[3][3]; };   // general 3x3 complex
 template <class T> struct Al { T a[8]; };          // su(3) components
 // Hermitian 3x3: real diagonal d0,d1,d2 and upper entries u01,u02,u12
@@ -102,9 +197,9 @@ template <class T> DEV Al<T> im_tl(const M3<T>& P) {
 template <class T> DEV void complete_row2(M3<T>& U) {
     const cx<T>* a = U.m[0];
     const cx<T>* b = U.m[1];
-    U.m[2][0] = cj(a[1] * b[2] - a[2] * b[1]);
-    U.m[2][1] = cj(a[2] * b[0] - a[0] * b[2]);
-    U.m[2][2] = cj(a[0] * b[1] - a[1] * b[0]);
+    U.m[2][0] = cj(val(cmul(a[1], b[2])) - val(cmul(a[2], b[1])));
+    U.m[2][1] = cj(val(cmul(a[2], b[0])) - val(cmul(a[0], b[2])));
+    U.m[2][2] = cj(val(cmul(a[0], b[1])) - val(cmul(a[1], b[0])));
 }
 // C = A B
 template <class T> DEV M3<T> mul(const M3<T>& A, const M3<T>& B) {
@@ -112,12 +207,8 @@ template <class T> DEV M3<T> mul(const M3<T>& A, const M3<T>& B) {
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            cx<T> s = A.m[i][0] * B.m[0][j];
-            fma_(s, A.m[i][1], B.m[1][j]);
-            fma_(s, A.m[i][2], B.m[2][j]);
-            C.m[i][j] = s;
-        }
+        for (int j = 0; j < 3; j++)
+            C.m[i][j] = val(cmac(cmac(cmul(A.m[i][0], B.m[0][j]), A.m[i][1], B.m[1][j]), A.m[i][2], B.m[2][j]));
     return C;
 }
 // C = A B^dag
@@ -126,12 +217,8 @@ template <class T> DEV M3<T> mul_nd(const M3<T>& A, const M3<T>& B) {
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            cx<T> s = mulc(A.m[i][0], B.m[j][0]);
-            fmac_(s, A.m[i][1], B.m[j][1]);
-            fmac_(s, A.m[i][2], B.m[j][2]);
-            C.m[i][j] = s;
-        }
+        for (int j = 0; j < 3; j++)
+            C.m[i][j] = val(cmacc(cmacc(cmulc(A.m[i][0], B.m[j][0]), A.m[i][1], B.m[j][1]), A.m[i][2], B.m[j][2]));
     return C;
 }
 // ImTL(A B^dag) without forming the real parts of the diagonal
@@ -139,64 +226,51 @@ template <class T> DEV Al<T> im_tl_nd(const M3<T>& A, const M3<T>& B) {
     return im_tl(mul_nd(A, B));
 }
 
+// (X B)_ij for Hermitian X: sum_k X_ik B_kj with X_ik real on the diagonal, the
+// stored upper entry above it and its conjugate below
+template <class T> DEV cx<T> hmul_entry(const H3<T>& X, const M3<T>& B, int i, int j) {
+    if (i == 0) return val(cmac(cmac(rmul(X.d0, B.m[0][j]), X.u01, B.m[1][j]), X.u02, B.m[2][j]));
+    if (i == 1) return val(cmac(rmac(ccmul(X.u01, B.m[0][j]), X.d1, B.m[1][j]), X.u12, B.m[2][j]));
+    return val(rmac(ccmac(ccmul(X.u02, B.m[0][j]), X.u12, B.m[1][j]), X.d2, B.m[2][j]));
+}
+// (A X)_ij for Hermitian X
+template <class T> DEV cx<T> mulh_entry(const M3<T>& A, const H3<T>& X, int i, int j) {
+    if (j == 0) return val(cmacc(cmacc(rmul(X.d0, A.m[i][0]), A.m[i][1], X.u01), A.m[i][2], X.u02));
+    if (j == 1) return val(cmacc(rmac(cmul(A.m[i][0], X.u01), X.d1, A.m[i][1]), A.m[i][2], X.u12));
+    return val(rmac(cmac(cmul(A.m[i][0], X.u02), A.m[i][1], X.u12), X.d2, A.m[i][2]));
+}
 // U^dag X U for Hermitian X (result Hermitian; only diagonal + upper computed)
 template <class T> DEV H3<T> transport(const M3<T>& U, const H3<T>& X) {
-    // W = X U
-    M3<T> W;
+    M3<T> W;  // X U
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            cx<T> s = mk(T(0), T(0));
-#pragma unroll
-            for (int k = 0; k < 3; k++) fma_(s, hget(X, i, k), U.m[k][j]);
-            W.m[i][j] = s;
-        }
-    // R = U^dag W, R_ij = sum_k conj(U_ki) W_kj
+        for (int j = 0; j < 3; j++) W.m[i][j] = hmul_entry(X, U, i, j);
+    // R_ij = sum_k conj(U_ki) W_kj
     H3<T> R;
-    cx<T> r;
-#define GL_RIJ(i, j)                                        \
-    r = mk(T(0), T(0));                                     \
-    fmca_(r, U.m[0][i], W.m[0][j]);                         \
-    fmca_(r, U.m[1][i], W.m[1][j]);                         \
-    fmca_(r, U.m[2][i], W.m[2][j]);
-    GL_RIJ(0, 0) R.d0 = r.r;
-    GL_RIJ(1, 1) R.d1 = r.r;
-    GL_RIJ(2, 2) R.d2 = r.r;
-    GL_RIJ(0, 1) R.u01 = r;
-    GL_RIJ(0, 2) R.u02 = r;
-    GL_RIJ(1, 2) R.u12 = r;
-#undef GL_RIJ
+    R.d0 = redot3(U.m[0][0], W.m[0][0], U.m[1][0], W.m[1][0], U.m[2][0], W.m[2][0]);
+    R.d1 = redot3(U.m[0][1], W.m[0][1], U.m[1][1], W.m[1][1], U.m[2][1], W.m[2][1]);
+    R.d2 = redot3(U.m[0][2], W.m[0][2], U.m[1][2], W.m[1][2], U.m[2][2], W.m[2][2]);
+    R.u01 = val(ccmac(ccmac(ccmul(U.m[0][0], W.m[0][1]), U.m[1][0], W.m[1][1]), U.m[2][0], W.m[2][1]));
+    R.u02 = val(ccmac(ccmac(ccmul(U.m[0][0], W.m[0][2]), U.m[1][0], W.m[1][2]), U.m[2][0], W.m[2][2]));
+    R.u12 = val(ccmac(ccmac(ccmul(U.m[0][1], W.m[0][2]), U.m[1][1], W.m[1][2]), U.m[2][1], W.m[2][2]));
     return R;
 }
 // U X U^dag for Hermitian X
 template <class T> DEV H3<T> conj_by(const M3<T>& U, const H3<T>& X) {
-    // W = U X
-    M3<T> W;
+    M3<T> W;  // U X
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            cx<T> s = mk(T(0), T(0));
-#pragma unroll
-            for (int k = 0; k < 3; k++) fma_(s, U.m[i][k], hget(X, k, j));
-            W.m[i][j] = s;
-        }
+        for (int j = 0; j < 3; j++) W.m[i][j] = mulh_entry(U, X, i, j);
     // R_ij = sum_k W_ik conj(U_jk)
     H3<T> R;
-    cx<T> r;
-#define GL_RIJ(i, j)                                        \
-    r = mk(T(0), T(0));                                     \
-    fmac_(r, W.m[i][0], U.m[j][0]);                         \
-    fmac_(r, W.m[i][1], U.m[j][1]);                         \
-    fmac_(r, W.m[i][2], U.m[j][2]);
-    GL_RIJ(0, 0) R.d0 = r.r;
-    GL_RIJ(1, 1) R.d1 = r.r;
-    GL_RIJ(2, 2) R.d2 = r.r;
-    GL_RIJ(0, 1) R.u01 = r;
-    GL_RIJ(0, 2) R.u02 = r;
-    GL_RIJ(1, 2) R.u12 = r;
-#undef GL_RIJ
+    R.d0 = redot3(U.m[0][0], W.m[0][0], U.m[0][1], W.m[0][1], U.m[0][2], W.m[0][2]);
+    R.d1 = redot3(U.m[1][0], W.m[1][0], U.m[1][1], W.m[1][1], U.m[1][2], W.m[1][2]);
+    R.d2 = redot3(U.m[2][0], W.m[2][0], U.m[2][1], W.m[2][1], U.m[2][2], W.m[2][2]);
+    R.u01 = val(cmacc(cmacc(cmulc(W.m[0][0], U.m[1][0]), W.m[0][1], U.m[1][1]), W.m[0][2], U.m[1][2]));
+    R.u02 = val(cmacc(cmacc(cmulc(W.m[0][0], U.m[2][0]), W.m[0][1], U.m[2][1]), W.m[0][2], U.m[2][2]));
+    R.u12 = val(cmacc(cmacc(cmulc(W.m[1][0], U.m[2][0]), W.m[1][1], U.m[2][1]), W.m[1][2], U.m[2][2]));
     return R;
 }
 template <class T> DEV Al<T> transport_alg(const M3<T>& U, const Al<T>& x) {
@@ -301,9 +375,10 @@ template <class T> DEV M3<T> expi(const H3<T>& X) {
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            cx<T> w = f1 * hget(X, i, j);
-            fma_(w, f2, hget(X2, i, j));
-            if (i == j) w = w + f0;
+            cx<T> w;
+            if (i == j) w = val(rmac(rmul(hget(X, i, i).r, f1), hget(X2, i, i).r, f2)) + f0;
+            else if (i < j) w = val(cmac(cmul(f1, hget(X, i, j)), f2, hget(X2, i, j)));
+            else w = val(cmacc(cmulc(f1, hget(X, j, i)), f2, hget(X2, j, i)));
             W.m[i][j] = w;
         }
     return W;

@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 
 
 def plane_buffer(st, prec):
-    """The canonical state in the library's plane layout (56 planes, grouped by four and
+    """The canonical state in the library's plane layout (56 planes, grouped by eight and
     interleaved per site), on the device (caller-owned)."""
     n = st.n
     ns = n * n
@@ -30,7 +30,7 @@ def plane_buffer(st, prec):
     f[32:40] = st.E[:, 1].T
     f[40:48] = st.phi.T
     f[48:56] = st.pi.T
-    g = f.reshape(14, 4, ns).transpose(0, 2, 1).reshape(-1)  # plane p, site s -> ((p//4) ns + s) 4 + p%4
+    g = f.reshape(7, 8, ns).transpose(0, 2, 1).reshape(-1)  # plane p, site s -> ((p//8) ns + s) 8 + p%8
     return torch.tensor(g.astype(np.float32 if prec else np.float64), device="cuda").contiguous()
 
 
