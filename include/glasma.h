@@ -294,6 +294,20 @@ glasma_status glasma_batch_get_particles(glasma_batch* b, int32_t event, double*
                                          double* px, double* py, double* peta, double* Q);
 /* Kernel launches of one run in the given mode. */
 int64_t glasma_batch_launches(const glasma_batch* b, int32_t mode);
+/* Tile shapes of the batched field step (graph and eager modes).  The FP32 kernel is
+ * compiled for several (TX, TY, minimum resident CTAs per SM); FP64 has one.  The
+ * per-site arithmetic is the same in every shape, so results do not depend on it.
+ * glasma_batch_tune times each variant's field kernel over the first `steps`
+ * iterations of the batch (restored to its initial state; one untimed warm-up
+ * iteration first), keeps the fastest and returns it in *chosen, the times (ms) in
+ * ms[variants] unless NULL.  Changing the variant drops the captured graph of the
+ * graph mode (it is captured again at the next run).  Synchronises. */
+int32_t glasma_field_tile_variants(int32_t precision);
+glasma_status glasma_field_tile_shape(int32_t precision, int32_t variant, int32_t* tx, int32_t* ty,
+                                      int32_t* min_ctas);
+int32_t glasma_batch_variant(const glasma_batch* b);
+glasma_status glasma_batch_set_variant(glasma_batch* b, int32_t variant);
+glasma_status glasma_batch_tune(glasma_batch* b, int32_t steps, int32_t* chosen, double* ms);
 void glasma_batch_destroy(glasma_batch* b);
 
 const char* glasma_last_error(void);

@@ -28,6 +28,8 @@ from .api import (  # noqa: F401
     cpic_create,
     cpic_init,
     cpic_push,
+    field_tile_shape,
+    field_tile_variants,
     glasma_create,
     glasma_init,
     glasma_step,

@@ -102,6 +102,11 @@ SIGNATURES = {
     "glasma_batch_profile": (C.c_int, [_p, _i32, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
                                        C.POINTER(_d)]),
     "glasma_batch_launches": (_i64, [_p, _i32]),
+    "glasma_field_tile_variants": (_i32, [_i32]),
+    "glasma_field_tile_shape": (C.c_int, [_i32, _i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)]),
+    "glasma_batch_variant": (_i32, [_p]),
+    "glasma_batch_set_variant": (C.c_int, [_p, _i32]),
+    "glasma_batch_tune": (C.c_int, [_p, _i32, C.POINTER(_i32), C.POINTER(_d)]),
     "glasma_batch_get_particles": (C.c_int, [_p, _i32] + [_p] * 7),
     "glasma_batch_destroy": (None, [_p]),
     "glasma_diagnostics_noalloc": (C.c_int, [_p, _i32, _i32, _i32, _d, _p, _p]),

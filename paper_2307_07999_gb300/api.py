@@ -332,6 +332,22 @@ class Batch:
     def launches(self, mode="graph"):
         return lib().glasma_batch_launches(self.handle, self.MODES[mode])
 
+    @property
+    def variant(self):
+        return lib().glasma_batch_variant(self.handle)
+
+    def set_variant(self, v):
+        check(lib().glasma_batch_set_variant(self.handle, v))
+
+    def tune(self, steps=8):
+        """glasma_batch_tune: time every field tile variant, keep the fastest.
+        Returns (chosen variant, [ms per variant])."""
+        nv = lib().glasma_field_tile_variants(self.ev[0].precision)
+        ms = (C.c_double * nv)()
+        ch = C.c_int32()
+        check(lib().glasma_batch_tune(self.handle, steps, C.byref(ch), ms))
+        return ch.value, list(ms)
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h:
@@ -349,3 +365,14 @@ def kappa_qhat(table):
     if len(t) >= 2:
         out[:, 1:] = np.gradient(table[:, 1:4], t, axis=0, edge_order=1)
     return out
+
+
+def field_tile_shape(precision, v):
+    """(TX, TY, minimum CTAs per SM) of field tile variant v."""
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    check(lib().glasma_field_tile_shape(precision, v, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def field_tile_variants(precision):
+    return lib().glasma_field_tile_variants(precision)

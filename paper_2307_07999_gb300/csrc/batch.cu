@@ -75,7 +75,7 @@ static Layout layout(const glasma_params* ev, const cpic_params* pp, int E, size
         parts += (size_t)pp[e].n_particles;
     }
     L.tables = align256((size_t)smax * E * step_args_size(prec)) + align256((size_t)smax * E * push_args_size(prec)) +
-               align256((size_t)4 << 20) + align256((size_t)4 << 20) + align256((size_t)E * sizeof(BinArgs)) +
+               3 * align256((size_t)4 << 20) + align256((size_t)E * sizeof(BinArgs)) +
                3 * align256(tiles * 4) + align256((tiles / 1024 + 2) * 4) + align256(parts * 4 + 4) +
                align256(256 + ((size_t)smax + 2) * 8 + ((size_t)E + 1) * 8);
     const size_t ic = ic_scratch_bytes(nmax, fft_work);
@@ -186,6 +186,7 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
     b->step_args = A.take(align256((size_t)std::max(1, b->max_iter) * E * step_args_size(b->prec)));
     b->push_args = A.take(align256((size_t)std::max(1, b->max_iter) * E * push_args_size(b->prec)));
     b->tiles_dev = A.take((size_t)4 << 20);
+    b->gtiles_dev = A.take((size_t)4 << 20);
     b->pitems_dev = A.take((size_t)4 << 20);
     b->scratch = A.take(std::max(ic_scratch_bytes(nmax, b->fft_work), align256(sort_scratch_ints(nmax * nmax) * 4)));
     {
@@ -204,12 +205,30 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
         b->bin_perm = (int*)A.take(parts * 4 + 4);
         b->pers_ctrl = A.take(256 + ((size_t)std::max(1, b->max_iter) + 2) * 8 + ((size_t)E + 1) * 8);
     }
-    if (!b->step_args || !b->push_args || !b->tiles_dev || !b->pitems_dev || !b->scratch || !b->bins_dev ||
+    if (!b->step_args || !b->push_args || !b->tiles_dev || !b->gtiles_dev || !b->pitems_dev || !b->scratch || !b->bins_dev ||
         !b->bin_count || !b->bin_fill || !b->bin_start || !b->bin_totals || !b->bin_perm || !b->pers_ctrl) {
         delete b;
         return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
     }
     *out = b;
+    return GLASMA_OK;
+}
+
+// tile items of the chosen field variant, grouped by event
+static glasma_status build_gtiles(glasma_batch* b) {
+    int tx, ty, mb;
+    field_variant_shape(b->prec, b->fvar, &tx, &ty, &mb);
+    std::vector<TileItemH> tiles;
+    b->gtiles_upto.assign(b->E + 1, 0);
+    for (int i = 0; i < b->E; i++) {
+        const BatchEvent& x = b->ev[i];
+        for (int y0 = 0; y0 < x.n; y0 += ty)
+            for (int x0 = 0; x0 < x.n; x0 += tx) tiles.push_back({i, x0, y0});
+        b->gtiles_upto[i + 1] = (int)tiles.size();
+    }
+    if (tiles.size() * sizeof(TileItemH) > ((size_t)4 << 20)) return bfail(GLASMA_ERR_NOSPACE, "tile table exceeds its reserve");
+    BCK(cudaMemcpyAsync(b->gtiles_dev, tiles.data(), tiles.size() * sizeof(TileItemH), cudaMemcpyHostToDevice, b->st));
+    BCK(cudaStreamSynchronize(b->st));  // the host vector goes out of scope
     return GLASMA_OK;
 }
 
@@ -242,6 +261,11 @@ static glasma_status build_tables(glasma_batch* b) {
         BCK(cudaMemcpyAsync(b->bins_dev, ba.data(), ba.size() * sizeof(BinArgs), cudaMemcpyHostToDevice, b->st));
     }
     BCK(cudaMemcpyAsync(b->tiles_dev, tiles.data(), tiles.size() * sizeof(TileItemH), cudaMemcpyHostToDevice, b->st));
+    BCK(prepare_field_variants(b->prec));
+    {
+        glasma_status gs = build_gtiles(b);
+        if (gs != GLASMA_OK) return gs;
+    }
     BCK(cudaMemcpyAsync(b->pitems_dev, pits.data(), pits.size() * sizeof(PushItemH), cudaMemcpyHostToDevice, b->st));
     const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
     std::vector<char> hs((size_t)K * E * sa, 0), hp((size_t)K * E * pa, 0);
@@ -364,8 +388,8 @@ static cudaError_t enqueue_batched(glasma_batch* b) {
     for (int k = 0; k < b->max_iter; k++) {
         const int act = b->active[k];
         if (act == 0) break;
-        e = launch_field_step_batched(b->prec, (char*)b->step_args + (size_t)k * b->E * sa, b->tiles_dev,
-                                      b->tiles_upto[act], b->st);
+        e = launch_field_step_variant(b->prec, b->fvar, (char*)b->step_args + (size_t)k * b->E * sa, b->gtiles_dev,
+                                      b->gtiles_upto[act], b->st);
         if (e != cudaSuccess) return e;
         e = launch_push_batched(b->prec, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
                                 b->pitems_upto[act], b->st);
@@ -550,7 +574,7 @@ extern "C" glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, dou
             BCK(launch_fused_batched(b->prec, sargs, pargs, b->tiles_dev, b->tiles_upto[act], b->bin_start,
                                      b->bin_count, b->bin_perm, b->st));
         else
-            BCK(launch_field_step_batched(b->prec, sargs, b->tiles_dev, b->tiles_upto[act], b->st));
+            BCK(launch_field_step_variant(b->prec, b->fvar, sargs, b->gtiles_dev, b->gtiles_upto[act], b->st));
         BCK(cudaEventRecord(ev[4 * k + 1], b->st));
         BCK(cudaEventRecord(ev[4 * k + 2], b->st));
         if (fused)
@@ -577,6 +601,67 @@ extern "C" glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, dou
     if (main_particle_steps) *main_particle_steps = fused ? parts : 0;
     if (other_ms) *other_ms = om;
     return GLASMA_OK;
+}
+
+extern "C" int32_t glasma_field_tile_variants(int32_t precision) {
+    return field_variants(precision == GLASMA_FP64 ? 0 : 1);
+}
+extern "C" glasma_status glasma_field_tile_shape(int32_t precision, int32_t v, int32_t* tx, int32_t* ty,
+                                                 int32_t* min_ctas) {
+    const int prec = precision == GLASMA_FP64 ? 0 : 1;
+    if (v < 0 || v >= field_variants(prec) || !tx || !ty || !min_ctas) return bfail(GLASMA_ERR_INVALID, "bad arguments");
+    int a, c, m;
+    field_variant_shape(prec, v, &a, &c, &m);
+    *tx = a; *ty = c; *min_ctas = m;
+    return GLASMA_OK;
+}
+extern "C" int32_t glasma_batch_variant(const glasma_batch* b) { return b ? b->fvar : GLASMA_ERR_INVALID; }
+extern "C" glasma_status glasma_batch_set_variant(glasma_batch* b, int32_t v) {
+    if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    if (v < 0 || v >= field_variants(b->prec)) return bfail(GLASMA_ERR_INVALID, "no such tile variant");
+    if (v == b->fvar) return GLASMA_OK;
+    b->fvar = v;
+    if (b->graph_unfused_ready) {
+        cudaGraphExecDestroy(b->exec_unfused);
+        b->graph_unfused_ready = false;
+    }
+    return build_gtiles(b);
+}
+// times the batched field kernel of every variant over the first `steps` iterations
+// (from the initial state, one untimed warm-up iteration first) and keeps the fastest
+extern "C" glasma_status glasma_batch_tune(glasma_batch* b, int32_t steps, int32_t* chosen, double* ms) {
+    if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    if (steps < 1) return bfail(GLASMA_ERR_INVALID, "steps must be positive");
+    const int nv = field_variants(b->prec);
+    const int K = std::min<int>(steps + 1, b->max_iter);
+    const size_t sa = step_args_size(b->prec);
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    int best = 0;
+    double best_ms = 1e300;
+    for (int v = 0; v < nv; v++) {
+        glasma_status s = glasma_batch_set_variant(b, v);
+        if (s != GLASMA_OK) return s;
+        BCK(enqueue_restore(b));
+        float t = 0;
+        for (int k = 0; k < K; k++) {
+            const int act = b->active[k];
+            if (act == 0) break;
+            if (k == 1) BCK(cudaEventRecord(e0, b->st));
+            BCK(launch_field_step_variant(b->prec, v, (char*)b->step_args + (size_t)k * b->E * sa, b->gtiles_dev,
+                                          b->gtiles_upto[act], b->st));
+        }
+        BCK(cudaEventRecord(e1, b->st));
+        BCK(cudaEventSynchronize(e1));
+        if (K > 1) BCK(cudaEventElapsedTime(&t, e0, e1));
+        if (ms) ms[v] = t;
+        if (t < best_ms) { best_ms = t; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (chosen) *chosen = best;
+    return glasma_batch_set_variant(b, best);
 }
 
 // particles of event i after a run, original order (host arrays of n_particles; NULL skips)

@@ -36,10 +36,12 @@ struct glasma_batch {
     std::vector<int> pos;         // caller's event index -> position in ev
     void* step_args = nullptr;    // [max_iter][E] StepArgs
     void* push_args = nullptr;    // [max_iter][E] PushArgs
-    void* tiles_dev = nullptr;    // TileItem list, grouped by event
+    void* tiles_dev = nullptr;    // TileItem list, grouped by event (fused and persistent paths)
+    void* gtiles_dev = nullptr;   // TileItem list of the chosen field variant (graph and eager paths)
+    int fvar = 0;                 // FP32 field tile variant of the graph and eager paths
     void* pitems_dev = nullptr;   // PushItem list, grouped by event
     void* scratch = nullptr;      // initial-condition / sort scratch
-    std::vector<int> tiles_upto, pitems_upto, active;
+    std::vector<int> tiles_upto, gtiles_upto, pitems_upto, active;
     // tile bins of the fused path
     void* bins_dev = nullptr;     // BinArgs per event
     int* bin_count = nullptr;

@@ -96,6 +96,56 @@ cudaError_t launch_field_step_batched(int prec, const void* args, const void* it
     return prec ? batched_impl<float>(args, items, n_items, st) : batched_impl<double>(args, items, n_items, st);
 }
 
+// ---------------------------------------------------------------- FP32 tile variants
+// The batched FP32 field step compiled for several tile shapes; a batch picks one by
+// timing them on its own events (glasma_batch_tune).  The arithmetic per site is the
+// same in every shape, so the results are identical.
+template <int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
+k_field_step_tiles(const StepArgs<float>* __restrict__ args, const TileItem* __restrict__ items) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const TileItem it = items[blockIdx.x];
+    field_tile<float, TX, TY>(args[it.ev], it.x0, it.y0, smem);
+}
+struct FieldVariant {
+    int tx, ty, minb;
+    const void* fn;
+    size_t smem;
+};
+#define GL_FV(TX, TY, MB) {TX, TY, MB, (const void*)k_field_step_tiles<TX, TY, MB>, RecTile<float, TX, TY>::smem}
+static const FieldVariant g_fvar[] = {GL_FV(32, 4, 3), GL_FV(16, 8, 3), GL_FV(8, 16, 3),
+                                      GL_FV(32, 6, 2), GL_FV(16, 12, 2), GL_FV(32, 8, 2)};
+#undef GL_FV
+static constexpr int N_FVAR = (int)(sizeof(g_fvar) / sizeof(g_fvar[0]));
+
+int field_variants(int prec) { return prec ? N_FVAR : 1; }
+void field_variant_shape(int prec, int v, int* tx, int* ty, int* minb) {
+    if (!prec) { *tx = TileCfg<double>::TX; *ty = TileCfg<double>::TY; *minb = TileCfg<double>::MINB; return; }
+    *tx = g_fvar[v].tx; *ty = g_fvar[v].ty; *minb = g_fvar[v].minb;
+}
+// shared-memory limits of every variant (call outside stream capture)
+cudaError_t prepare_field_variants(int prec) {
+    if (!prec) return set_smem<double>();
+    cudaError_t e = set_smem<float>();
+    static bool done = false;
+    if (e != cudaSuccess || done) return e;
+    for (int v = 0; v < N_FVAR; v++) {
+        e = cudaFuncSetAttribute(g_fvar[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_fvar[v].smem);
+        if (e != cudaSuccess) return e;
+    }
+    done = true;
+    return cudaSuccess;
+}
+cudaError_t launch_field_step_variant(int prec, int v, const void* args, const void* items, int n_items,
+                                      cudaStream_t st) {
+    if (!prec) return launch_field_step_batched(prec, args, items, n_items, st);
+    if (v < 0 || v >= N_FVAR) return cudaErrorInvalidValue;
+    if (n_items <= 0 || !args) return cudaSuccess;
+    const FieldVariant& f = g_fvar[v];
+    void* kargs[2] = {(void*)&args, (void*)&items};
+    return cudaLaunchKernel(f.fn, dim3((unsigned)n_items), dim3(f.tx, f.ty), kargs, f.smem, st);
+}
+
 // ---------------------------------------------------------------- canonical layout
 template <class T>
 __global__ void k_from_canonical(const double* __restrict__ U, const double* __restrict__ E,

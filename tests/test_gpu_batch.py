@@ -109,6 +109,43 @@ def test_batch_fp32_matches_oracle():
         assert d[0] < 1e-5
 
 
+def test_tile_variants_are_bit_identical_and_tuning_picks_one():
+    """Every FP32 field tile shape (the lattices include sizes that are ragged against
+    each shape) gives the same particle states bit for bit: the per-site arithmetic
+    does not depend on the tile.  (The FP64 broadening sums and monitors are atomic
+    accumulations whose order varies from run to run: equal to 1e-12.)  The tuner
+    times every shape and keeps one."""
+    evs, pps = small_events(1, tol=1e-14)
+    B = G.Batch(evs, pps)
+    B.init()
+    nv = G.field_tile_variants(G.GLASMA_FP32)
+    assert nv >= 2 and G.field_tile_variants(G.GLASMA_FP64) == 1
+    shapes = [G.field_tile_shape(G.GLASMA_FP32, v) for v in range(nv)]
+    assert shapes[0] == (32, 4, 3) and len(set(shapes)) == nv
+    keys = ("x", "y", "eta", "px", "py", "peta", "Q")
+    ref = None
+    for v in range(nv):
+        B.set_variant(v)
+        assert B.variant == v
+        for mode in ("eager", "graph"):
+            B.run(mode)
+            parts = [B.get_particles(e) for e in range(len(evs))]
+            tabs = [B.broadening(e) for e in range(len(evs))]
+            mons = [B.diagnostics(e) for e in range(len(evs))]
+            if ref is None:
+                ref = (parts, tabs, mons)
+            for e in range(len(evs)):
+                for k in keys:
+                    assert np.array_equal(parts[e][k], ref[0][e][k]), (shapes[v], mode, e, k)
+                assert rel_err(tabs[e], ref[1][e]) < 1e-12, (shapes[v], mode, e)
+                assert rel_err(mons[e][:6], ref[2][e][:6]) < 1e-12, (shapes[v], mode, e)
+    chosen, ms = B.tune(steps=4)
+    print("tile variant times (ms):", {shapes[v]: round(ms[v], 3) for v in range(nv)}, "chosen", shapes[chosen])
+    assert 0 <= chosen < nv and B.variant == chosen and all(m > 0 for m in ms)
+    B.run("graph")
+    assert np.array_equal(B.get_particles(0)["px"], ref[0][0]["px"])
+
+
 def test_full_size_batch_sampled():
     """The benchmarked workload at full size, in the launch configuration bench.py times
     (graph mode, FP32): monitors of all 64 events, and event 0 (128^2, 10k charm)
@@ -118,6 +155,7 @@ def test_full_size_batch_sampled():
     B = G.Batch(evs, pps)
     fails = B.init()
     assert fails == 0
+    B.tune(steps=4)  # the tile shape bench.py runs with
     B.run("graph")
     for e in range(len(evs)):
         d = B.diagnostics(e)
