@@ -262,6 +262,7 @@ static glasma_status build_tables(glasma_batch* b) {
     }
     BCK(cudaMemcpyAsync(b->tiles_dev, tiles.data(), tiles.size() * sizeof(TileItemH), cudaMemcpyHostToDevice, b->st));
     BCK(prepare_field_variants(b->prec));
+    BCK(prepare_push_staged());
     {
         glasma_status gs = build_gtiles(b);
         if (gs != GLASMA_OK) return gs;

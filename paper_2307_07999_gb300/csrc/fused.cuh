@@ -39,17 +39,24 @@ template <class T, int TX, int TY> struct SmemSrc {
         else if (d > TY) d -= n;
         return d + 1;
     }
-    DEV M3<T> link(int d, int x, int y) const { return sm_link<T, FT::HS>(sU, d, hy(y) * FT::HX + hx(x)); }
-    DEV void links(int x, int y, M3<T>& ux, M3<T>& uy) const {
-        ux = link(0, x, y);
-        uy = link(1, x, y);
-    }
-    DEV Al<T> phi(int x, int y) const { return sm_alg<T, FT::HS>(sP, hy(y) * FT::HX + hx(x)); }
-    DEV Al<T> eavg(int d, int x, int y) const {
-        if (d == 0) return sm_alg<T, FT::SEX>(sEx, (hy(y) - 1) * (TX + 1) + hx(x));
-        return sm_alg<T, FT::SEY>(sEy, hy(y) * TX + hx(x) - 1);
-    }
-    DEV Al<T> piavg(int x, int y) const { return sm_alg<T, FT::SPI>(sPi, (hy(y) - 1) * TX + hx(x) - 1); }
+    // view of the fields around a cell of the tile: (dx, dy) offsets stay inside the halo
+    struct View {
+        const T *sU, *sP, *sEx, *sEy, *sPi;
+        int hcx, hcy;  // the cell's slot coordinates in the halo tile
+        DEV int h(int dx, int dy) const { return (hcy + dy) * FT::HX + hcx + dx; }
+        DEV M3<T> link(int d, int dx, int dy) const { return sm_link<T, FT::HS>(sU, d, h(dx, dy)); }
+        DEV void links(int dx, int dy, M3<T>& ux, M3<T>& uy) const {
+            ux = link(0, dx, dy);
+            uy = link(1, dx, dy);
+        }
+        DEV Al<T> phi(int dx, int dy) const { return sm_alg<T, FT::HS>(sP, h(dx, dy)); }
+        DEV Al<T> eavg(int d, int dx, int dy) const {
+            if (d == 0) return sm_alg<T, FT::SEX>(sEx, (hcy + dy - 1) * (TX + 1) + hcx + dx);
+            return sm_alg<T, FT::SEY>(sEy, (hcy + dy) * TX + hcx + dx - 1);
+        }
+        DEV Al<T> piavg() const { return sm_alg<T, FT::SPI>(sPi, (hcy - 1) * TX + hcx - 1); }
+    };
+    DEV View view(int cx, int cy) const { return View{sU, sP, sEx, sEy, sPi, hx(cx), hy(cy)}; }
 };
 
 template <class T, int TX, int TY>

@@ -33,6 +33,7 @@ int field_tile_y(int prec);
 int field_variants(int prec);
 void field_variant_shape(int prec, int v, int* tx, int* ty, int* minb);
 cudaError_t prepare_field_variants(int prec);
+cudaError_t prepare_push_staged();
 cudaError_t launch_field_step_variant(int prec, int v, const void* args, const void* items, int n_items,
                                       cudaStream_t st);
 size_t step_args_size(int prec);

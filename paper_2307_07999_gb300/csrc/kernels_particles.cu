@@ -46,11 +46,28 @@ void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out) {
     if (prec) *(PushArgs<float>*)out = push_args<float>(a, P);
     else *(PushArgs<double>*)out = push_args<double>(a, P);
 }
+// shared-memory limit of the staged push (call outside stream capture)
+cudaError_t prepare_push_staged() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_push_staged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)push_staged_smem<float>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_push_staged<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)push_staged_smem<double>());
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+// batched push of one step: the staged kernel (one 256-particle item per 256 / PUSH_PPB blocks)
 cudaError_t launch_push_batched(int prec, const void* args, const void* items, int n_items, cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
-    const unsigned nb = (unsigned)n_items * PUSH_SUB;
-    if (prec) k_push_batched<float><<<nb, PUSH_THREADS, 0, st>>>((const PushArgs<float>*)args, (const PushItem*)items);
-    else k_push_batched<double><<<nb, PUSH_THREADS, 0, st>>>((const PushArgs<double>*)args, (const PushItem*)items);
+    const unsigned nb = (unsigned)n_items * (256 / PUSH_PPB);
+    if (prec)
+        k_push_staged<float><<<nb, PUSH_PPB, push_staged_smem<float>(), st>>>((const PushArgs<float>*)args,
+                                                                            (const PushItem*)items);
+    else
+        k_push_staged<double><<<nb, PUSH_PPB, push_staged_smem<double>(), st>>>((const PushArgs<double>*)args,
+                                                                              (const PushItem*)items);
     return cudaGetLastError();
 }
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st) {

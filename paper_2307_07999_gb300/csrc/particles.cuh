@@ -54,75 +54,179 @@ template <class T> DEV T clamp_below_one(T v);
 template <> DEV float clamp_below_one<float>(float v) { return fminf(v, 0.99999994f); }
 template <> DEV double clamp_below_one<double>(double v) { return fmin(v, 0.99999999999999989); }
 
-// Field source of the unfused push: links, phi and time-averaged E, pi read from
-// the two global field buffers of step n.  Cells are given as (x, y) with the
-// neighbours already wrapped periodically.
+// Field sources of the push.  A source hands out, per particle, a view of the fields
+// around the particle's cell c; the view's accessors take the offset (dx, dy) in
+// {-1, 0, 1}^2 of a site from c (periodic neighbours):
+//   link(d, dx, dy), links(dx, dy, ux, uy)   links at the site (U_n)
+//   phi(dx, dy)                              phi at the site (phi_n)
+//   eavg(d, dx, dy), piavg()                 (E_i(tau_{n-1/2}) + E_i(tau_{n+1/2})) / 2 on
+//                                            the link site -> site + i, pi likewise at c
+// Global source of the unfused push: the two field buffers of step n.
 template <class T, bool CG = false> struct GlobalSrc {
     const T* fo;
     const T* fn;
     int n;
     size_t ns;
-    DEV size_t at(int x, int y) const { return (size_t)x + (size_t)n * y; }
-    DEV M3<T> link(int d, int x, int y) const { return load_link<T, CG>(fo, ns, d == 0 ? P_UX : P_UY, at(x, y)); }
-    DEV void links(int x, int y, M3<T>& ux, M3<T>& uy) const { load_links<T, CG>(fo, ns, at(x, y), ux, uy); }
-    DEV Al<T> phi(int x, int y) const { return load_alg<T, CG>(fo, ns, P_PHI, at(x, y)); }
-    // (E_i(tau_{n-1/2}) + E_i(tau_{n+1/2})) / 2 on the link (x, y) -> (x, y) + i
-    DEV Al<T> eavg(int d, int x, int y) const { return avg(d == 0 ? P_EX : P_EY, at(x, y)); }
-    DEV Al<T> piavg(int x, int y) const { return avg(P_PI, at(x, y)); }
-    DEV Al<T> avg(int p, size_t s) const {
-        Al<T> e = load_alg<T, CG>(fo, ns, p, s);
-        const Al<T> b = load_alg<T, CG>(fn, ns, p, s);
+    struct View {
+        const T* fo;
+        const T* fn;
+        size_t ns;
+        int n, cx, cy, xm, xp, ym, yp;
+        DEV size_t at(int dx, int dy) const {
+            const int x = dx < 0 ? xm : (dx > 0 ? xp : cx), y = dy < 0 ? ym : (dy > 0 ? yp : cy);
+            return (size_t)x + (size_t)n * y;
+        }
+        DEV M3<T> link(int d, int dx, int dy) const { return load_link<T, CG>(fo, ns, d == 0 ? P_UX : P_UY, at(dx, dy)); }
+        DEV void links(int dx, int dy, M3<T>& ux, M3<T>& uy) const { load_links<T, CG>(fo, ns, at(dx, dy), ux, uy); }
+        DEV Al<T> phi(int dx, int dy) const { return load_alg<T, CG>(fo, ns, P_PHI, at(dx, dy)); }
+        DEV Al<T> eavg(int d, int dx, int dy) const { return avg(d == 0 ? P_EX : P_EY, at(dx, dy)); }
+        DEV Al<T> piavg() const { return avg(P_PI, at(0, 0)); }
+        DEV Al<T> avg(int p, size_t s) const {
+            Al<T> e = load_alg<T, CG>(fo, ns, p, s);
+            const Al<T> b = load_alg<T, CG>(fn, ns, p, s);
 #pragma unroll
-        for (int a = 0; a < 8; a++) e.a[a] = T(0.5) * (e.a[a] + b.a[a]);
-        return e;
+            for (int a = 0; a < 8; a++) e.a[a] = T(0.5) * (e.a[a] + b.a[a]);
+            return e;
+        }
+    };
+    DEV View view(int cx, int cy) const {
+        return View{fo, fn, ns, n, cx, cy, cx == 0 ? n - 1 : cx - 1, cx == n - 1 ? 0 : cx + 1,
+                    cy == 0 ? n - 1 : cy - 1, cy == n - 1 ? 0 : cy + 1};
     }
 };
 
-// Q-contracted site-centred fields at cell (cx, cy) for the push of step n:
+// Staged source (FP32 batched push): the field groups one particle's gather reads,
+// copied beforehand into a per-thread shared-memory record.  Slots (8 reals each):
+//   c:      0-2 links, 3 E_x fo, 4 E_y fo, 5 E_x fn, 6 E_y fn, 7 phi, 8 pi fo, 9 pi fn
+//   c-x:    10-12 links, 13 E_x fo, 14 E_x fn, 15 phi
+//   c-y:    16-18 links, 19 E_y fo, 20 E_y fn, 21 phi
+//   c-x-y:  22-24 links
+//   c+x:    25-26 link groups 1, 2 (U_y), 27 phi
+//   c+y:    28-29 link groups 0, 1 (U_x), 30 phi
+//   c-x+y:  31-32 link groups 0, 1 (U_x)
+//   c+x-y:  33-34 link groups 1, 2 (U_y)
+// (fo: the buffer of step n, fn: of step n+1; groups as in the field buffer layout.)
+constexpr int STAGE_SLOTS = 35;
+// slot of field group g (0..6) of buffer b (0: fo, 1: fn) at offset (dx, dy); -1 if not staged
+__host__ __device__ constexpr int stage_slot(int dx, int dy, int g, int b) {
+    if (g <= 2) {  // links (fo only)
+        if (dx == 0 && dy == 0) return g;
+        if (dx == -1 && dy == 0) return 10 + g;
+        if (dx == 0 && dy == -1) return 16 + g;
+        if (dx == -1 && dy == -1) return 22 + g;
+        if (dx == 1 && dy == 0) return g >= 1 ? 24 + g : -1;
+        if (dx == 0 && dy == 1) return g <= 1 ? 28 + g : -1;
+        if (dx == -1 && dy == 1) return g <= 1 ? 31 + g : -1;
+        if (dx == 1 && dy == -1) return g >= 1 ? 32 + g : -1;
+        return -1;
+    }
+    if (g == 5) {  // phi (fo)
+        if (dx == 0 && dy == 0) return 7;
+        if (dx == -1 && dy == 0) return 15;
+        if (dx == 0 && dy == -1) return 21;
+        if (dx == 1 && dy == 0) return 27;
+        if (dx == 0 && dy == 1) return 30;
+        return -1;
+    }
+    if (g == 6) return (dx == 0 && dy == 0) ? 8 + b : -1;  // pi
+    // E_x (g = 3), E_y (g = 4)
+    if (dx == 0 && dy == 0) return 3 + (g - 3) + 2 * b;
+    if (dx == -1 && dy == 0 && g == 3) return 13 + b;
+    if (dx == 0 && dy == -1 && g == 4) return 19 + b;
+    return -1;
+}
+template <class T> struct StagedSrc {
+    static constexpr int STRIDE = STAGE_SLOTS * 8 + (sizeof(T) == 4 ? 4 : 2);  // bank-spread record stride
+    const T* rec;  // this thread's record
+    struct View {
+        const T* r;
+        DEV const T* grp(int dx, int dy, int g, int b = 0) const { return r + 8 * stage_slot(dx, dy, g, b); }
+        DEV M3<T> link(int d, int dx, int dy) const {
+            M3<T> U;
+            if (d == 0) {
+                const T* a = grp(dx, dy, 0);
+                const T* b = grp(dx, dy, 1);
+#pragma unroll
+                for (int e = 0; e < 4; e++) put_entry(U, e, a[2 * e], a[2 * e + 1]);
+                put_entry(U, 4, b[0], b[1]);
+                put_entry(U, 5, b[2], b[3]);
+            } else {
+                const T* a = grp(dx, dy, 1);
+                const T* b = grp(dx, dy, 2);
+                put_entry(U, 0, a[4], a[5]);
+                put_entry(U, 1, a[6], a[7]);
+#pragma unroll
+                for (int e = 0; e < 4; e++) put_entry(U, 2 + e, b[2 * e], b[2 * e + 1]);
+            }
+            complete_row2(U);
+            return U;
+        }
+        DEV void links(int dx, int dy, M3<T>& ux, M3<T>& uy) const {
+            ux = link(0, dx, dy);
+            uy = link(1, dx, dy);
+        }
+        DEV Al<T> phi(int dx, int dy) const { return ld(grp(dx, dy, 5)); }
+        DEV Al<T> eavg(int d, int dx, int dy) const { return avg(grp(dx, dy, 3 + d, 0), grp(dx, dy, 3 + d, 1)); }
+        DEV Al<T> piavg() const { return avg(grp(0, 0, 6, 0), grp(0, 0, 6, 1)); }
+        DEV static Al<T> ld(const T* p) {
+            Al<T> x;
+#pragma unroll
+            for (int a = 0; a < 8; a++) x.a[a] = p[a];
+            return x;
+        }
+        DEV static Al<T> avg(const T* p, const T* q) {
+            Al<T> x;
+#pragma unroll
+            for (int a = 0; a < 8; a++) x.a[a] = T(0.5) * (p[a] + q[a]);
+            return x;
+        }
+    };
+    DEV View view(int, int) const { return View{rec}; }
+};
+
+// Q-contracted site-centred fields at the particle's cell for the push of step n:
 // qE = Q.(E_x, E_y, E_z), qB = Q.(B_x, B_y, B_z)
-template <class T, class S>
-DEV void gather_qf_src(const S& F, int n, T te, int cx, int cy, const Al<T>& q, T qE[3], T qB[3]) {
-    const int xm = cx == 0 ? n - 1 : cx - 1, xp = cx == n - 1 ? 0 : cx + 1;
-    const int ym = cy == 0 ? n - 1 : cy - 1, yp = cy == n - 1 ? 0 : cy + 1;
+template <class T, class V>
+DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
     const T half = T(0.5);
     // cells whose two links are both used load them together (three sectors in FP32)
     M3<T> ux_c, uy_c, ux_xm, uy_xm, ux_ym, uy_ym;
-    F.links(cx, cy, ux_c, uy_c);
-    F.links(xm, cy, ux_xm, uy_xm);
-    F.links(cx, ym, ux_ym, uy_ym);
+    C.links(0, 0, ux_c, uy_c);
+    C.links(-1, 0, ux_xm, uy_xm);
+    C.links(0, -1, ux_ym, uy_ym);
     // electric: the two links touching c, time-centred, transported to c
     {
-        const Al<T> t = transport_alg(ux_xm, F.eavg(0, xm, cy));
-        qE[0] = half * (dot8(q, F.eavg(0, cx, cy)) + dot8(q, t)) / te;
+        const Al<T> t = transport_alg(ux_xm, C.eavg(0, -1, 0));
+        qE[0] = half * (dot8(q, C.eavg(0, 0, 0)) + dot8(q, t)) / te;
     }
     {
-        const Al<T> t = transport_alg(uy_ym, F.eavg(1, cx, ym));
-        qE[1] = half * (dot8(q, F.eavg(1, cx, cy)) + dot8(q, t)) / te;
+        const Al<T> t = transport_alg(uy_ym, C.eavg(1, 0, -1));
+        qE[1] = half * (dot8(q, C.eavg(1, 0, 0)) + dot8(q, t)) / te;
     }
-    qE[2] = dot8(q, F.piavg(cx, cy));
+    qE[2] = dot8(q, C.piavg());
     // magnetic from phi: covariant central differences
     {
-        const Al<T> fw = conj_alg(ux_c, F.phi(xp, cy));
-        const Al<T> bw = transport_alg(ux_xm, F.phi(xm, cy));
+        const Al<T> fw = conj_alg(ux_c, C.phi(1, 0));
+        const Al<T> bw = transport_alg(ux_xm, C.phi(-1, 0));
         qB[1] = half * (dot8(q, fw) - dot8(q, bw)) / te;    // B_y = +D_x phi / tau
     }
     {
-        const Al<T> fw = conj_alg(uy_c, F.phi(cx, yp));
-        const Al<T> bw = transport_alg(uy_ym, F.phi(cx, ym));
+        const Al<T> fw = conj_alg(uy_c, C.phi(0, 1));
+        const Al<T> bw = transport_alg(uy_ym, C.phi(0, -1));
         qB[0] = -half * (dot8(q, fw) - dot8(q, bw)) / te;   // B_x = -D_y phi / tau
     }
     // B_z = -F_xy, F_xy = clover average of the four plaquettes based at c
     {
-        Al<T> acc = im_tl(mul_nd(mul(ux_c, F.link(1, xp, cy)), mul(uy_c, F.link(0, cx, yp))));  // +x,+y
+        Al<T> acc = im_tl(mul_nd(mul(ux_c, C.link(1, 1, 0)), mul(uy_c, C.link(0, 0, 1))));  // +x,+y
         {   // +y,-x: U_y(c) [U_y(c-x) U_x(c-x+y)]^dag U_x(c-x)
-            const M3<T> B = mul(uy_xm, F.link(0, xm, yp));
+            const M3<T> B = mul(uy_xm, C.link(0, -1, 1));
             const Al<T> t = im_tl(mul(mul_nd(uy_c, B), ux_xm));
 #pragma unroll
             for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
         }
         {   // -x,-y: [U_y(c-x-y) U_x(c-x)]^dag [U_x(c-x-y) U_y(c-y)]
             M3<T> ux_xmym, uy_xmym;
-            F.links(xm, ym, ux_xmym, uy_xmym);
+            C.links(-1, -1, ux_xmym, uy_xmym);
             const M3<T> B1 = mul(uy_xmym, ux_xm);
             const M3<T> B2 = mul(ux_xmym, uy_ym);
             const Al<T> t = im_tl(mul_dn(B1, B2));
@@ -130,7 +234,7 @@ DEV void gather_qf_src(const S& F, int n, T te, int cx, int cy, const Al<T>& q, 
             for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
         }
         {   // -y,+x: U_y(c-y)^dag [U_x(c-y) U_y(c+x-y)] U_x(c)^dag
-            const M3<T> B = mul(ux_ym, F.link(1, xp, ym));
+            const M3<T> B = mul(ux_ym, C.link(1, 1, -1));
             const Al<T> t = im_tl(mul_nd(mul_dn(uy_ym, B), ux_c));
 #pragma unroll
             for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
@@ -138,13 +242,6 @@ DEV void gather_qf_src(const S& F, int n, T te, int cx, int cy, const Al<T>& q, 
         qB[2] = -T(0.25) * dot8(q, acc);
     }
 }
-
-template <class T>
-DEV void gather_qf(const PushArgs<T>& A, int cx, int cy, const Al<T>& q, T qE[3], T qB[3]) {
-    GlobalSrc<T> F{A.fo, A.fn, A.n, (size_t)A.n * A.n};
-    gather_qf_src(F, A.n, A.te, cx, cy, q, qE, qB);
-}
-
 
 // one particle: gather, kick, drift, color transport; returns its broadening terms
 template <class T, class S, bool CG = false>
@@ -157,7 +254,8 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
 #pragma unroll
     for (int a = 0; a < 8; a++) q.a[a] = CG ? __ldcg(P.Q + (size_t)a * P.qs + j) : P.Q[(size_t)a * P.qs + j];
     T qE[3], qB[3];
-    gather_qf_src(F, n, A.te, cx, cy, q, qE, qB);
+    const auto C = F.view(cx, cy);
+    gather_qf_view(C, A.te, q, qE, qB);
     const T p0x = P.p0x[j], p0y = P.p0y[j];  // constant during a run
     T dpx = CG ? __ldcg(P.dpx + j) : P.dpx[j], dpy = CG ? __ldcg(P.dpy + j) : P.dpy[j];
     T pz = CG ? __ldcg(P.peta + j) : P.peta[j];
@@ -181,28 +279,30 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
     // color: rotation along eta at the old cell, then across the x face, then the y face
     {
         Al<T> e;
-        const Al<T> ph = F.phi(cx, cy);
+        const Al<T> ph = C.phi(0, 0);
 #pragma unroll
         for (int a = 0; a < 8; a++) e.a[a] = -deta * ph.a[a];
         q = alg(conj_by(expi(herm(e)), herm(q)));
     }
-    int nx = cx, ny = cy;
+    int nx = cx, ny = cy, ddx = 0;
     if (ox >= T(1)) {
-        q = transport_alg(F.link(0, cx, cy), q);
+        q = transport_alg(C.link(0, 0, 0), q);
         ox -= T(1);
         nx = cx == n - 1 ? 0 : cx + 1;
+        ddx = 1;
     } else if (ox < T(0)) {
         nx = cx == 0 ? n - 1 : cx - 1;
-        q = conj_alg(F.link(0, nx, cy), q);
+        ddx = -1;
+        q = conj_alg(C.link(0, -1, 0), q);
         ox = clamp_below_one(ox + T(1));
     }
     if (oy >= T(1)) {
-        q = transport_alg(F.link(1, nx, cy), q);
+        q = transport_alg(C.link(1, ddx, 0), q);
         oy -= T(1);
         ny = cy == n - 1 ? 0 : cy + 1;
     } else if (oy < T(0)) {
         ny = cy == 0 ? n - 1 : cy - 1;
-        q = conj_alg(F.link(1, nx, ny), q);
+        q = conj_alg(C.link(1, ddx, -1), q);
         oy = clamp_below_one(oy + T(1));
     }
     const T eta = (CG ? __ldcg(P.eta + j) : P.eta[j]) + deta;
@@ -283,6 +383,84 @@ k_push_batched(const PushArgs<T>* __restrict__ args, const PushItem* __restrict_
     const int j = it.j0 + (int)(blockIdx.x % PUSH_SUB) * PUSH_THREADS + threadIdx.x;
     double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
     if (j < A.np) push_one(A, j, sx, sy, sz, sc);
+    block_acc4(sx, sy, sz, sc, A.acc);
+}
+
+// ---------------------------------------------------------------- staged batched push
+// Each thread first copies the 35 field groups of its particle's gather (StagedSrc) into
+// its shared-memory record with cp.async, all copies in flight at once, then pushes
+// from shared memory: the scattered loads overlap instead of waiting in turn.
+struct StageEntry { int dx, dy, g, b; };
+// the field group in slot k: offset (dx, dy) of its site, group g, buffer b
+__host__ __device__ constexpr StageEntry stage_entry(int k) {
+    constexpr int E[STAGE_SLOTS][4] = {
+        {0, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 2, 0}, {0, 0, 3, 0}, {0, 0, 4, 0}, {0, 0, 3, 1}, {0, 0, 4, 1},
+        {0, 0, 5, 0}, {0, 0, 6, 0}, {0, 0, 6, 1},
+        {-1, 0, 0, 0}, {-1, 0, 1, 0}, {-1, 0, 2, 0}, {-1, 0, 3, 0}, {-1, 0, 3, 1}, {-1, 0, 5, 0},
+        {0, -1, 0, 0}, {0, -1, 1, 0}, {0, -1, 2, 0}, {0, -1, 4, 0}, {0, -1, 4, 1}, {0, -1, 5, 0},
+        {-1, -1, 0, 0}, {-1, -1, 1, 0}, {-1, -1, 2, 0},
+        {1, 0, 1, 0}, {1, 0, 2, 0}, {1, 0, 5, 0},
+        {0, 1, 0, 0}, {0, 1, 1, 0}, {0, 1, 5, 0},
+        {-1, 1, 0, 0}, {-1, 1, 1, 0},
+        {1, -1, 1, 0}, {1, -1, 2, 0}};
+    return StageEntry{E[k][0], E[k][1], E[k][2], E[k][3]};
+}
+constexpr bool stage_table_consistent() {
+    for (int k = 0; k < STAGE_SLOTS; k++) {
+        const StageEntry e = stage_entry(k);
+        if (stage_slot(e.dx, e.dy, e.g, e.b) != k) return false;
+    }
+    return true;
+}
+static_assert(stage_table_consistent(), "staged gather: slot table and lookup disagree");
+
+DEV void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+DEV void cp_async_wait_all() { asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory"); }
+
+#ifndef GLASMA_PUSH_PPB
+#define GLASMA_PUSH_PPB 32
+#endif
+#ifndef GLASMA_PUSH_PPB_MINB
+#define GLASMA_PUSH_PPB_MINB 6
+#endif
+constexpr int PUSH_PPB = GLASMA_PUSH_PPB;
+static_assert(256 % PUSH_PPB == 0 && PUSH_PPB % 32 == 0, "staged push block");
+template <class T> constexpr size_t push_staged_smem() { return (size_t)PUSH_PPB * StagedSrc<T>::STRIDE * sizeof(T); }
+
+template <class T>
+__global__ void __launch_bounds__(GLASMA_PUSH_PPB, GLASMA_PUSH_PPB_MINB)
+k_push_staged(const PushArgs<T>* __restrict__ args, const PushItem* __restrict__ items) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int SUB = 256 / PUSH_PPB;
+    const PushItem it = items[blockIdx.x / SUB];
+    const PushArgs<T> A = args[it.ev];
+    if (A.acc == nullptr) return;  // uniform over the block
+    const int j = it.j0 + (int)(blockIdx.x % SUB) * PUSH_PPB + threadIdx.x;
+    T* rec = reinterpret_cast<T*>(smem) + (size_t)threadIdx.x * StagedSrc<T>::STRIDE;
+    double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
+    if (j < A.np) {
+        const int n = A.n;
+        const size_t ns = (size_t)n * n;
+        const int cell = A.P.cell[j];
+        const int cx = cell % n, cy = cell / n;
+        const int xm = cx == 0 ? n - 1 : cx - 1, xp = cx == n - 1 ? 0 : cx + 1;
+        const int ym = cy == 0 ? n - 1 : cy - 1, yp = cy == n - 1 ? 0 : cy + 1;
+        constexpr int CH = 16 / sizeof(T);  // reals per 16-byte chunk
+#pragma unroll
+        for (int k = 0; k < STAGE_SLOTS; k++) {
+            const StageEntry e = stage_entry(k);
+            const int x = e.dx < 0 ? xm : (e.dx > 0 ? xp : cx), y = e.dy < 0 ? ym : (e.dy > 0 ? yp : cy);
+            const T* src = (e.b ? A.fn : A.fo) + fidx(8 * e.g, (size_t)x + (size_t)n * y, ns);
+#pragma unroll
+            for (int c = 0; c < 8; c += CH) cp_async16(rec + 8 * k + c, src + c);
+        }
+        cp_async_wait_all();
+        const StagedSrc<T> F{rec};
+        push_one_src<T, StagedSrc<T>>(A, F, j, sx, sy, sz, sc);
+    }
     block_acc4(sx, sy, sz, sc, A.acc);
 }
 

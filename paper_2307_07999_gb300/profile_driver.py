@@ -3,6 +3,7 @@
   python -m paper_2307_07999_gb300.profile_driver field 512          # 4 FP32 field steps on 512^2
   python -m paper_2307_07999_gb300.profile_driver push 512 100000    # + a 100k-particle push
   python -m paper_2307_07999_gb300.profile_driver batch              # one graph run of the 64-event batch
+  python -m paper_2307_07999_gb300.profile_driver batch8             # 8 events of 384^2, 10k charm each
 """
 import sys
 
@@ -14,8 +15,8 @@ from . import workloads as W
 
 def main(argv):
     what = argv[1] if len(argv) > 1 else "field"
-    if what == "batch":
-        evs, pps = W.batched_uneven()
+    if what in ("batch", "batch8"):
+        evs, pps = W.batched_uneven() if what == "batch" else W.batched_uneven(n_events=8, sizes=(384,))
         B = Batch(evs, pps)
         B.init()
         B.run("graph")
