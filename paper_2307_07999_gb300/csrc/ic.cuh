@@ -150,24 +150,67 @@ DEV bool solve8(double J[8][8], double b[8], double d[8]) {
 // Small-field series of the solution's offset from U1 U2: U = exp(i d.t) U1 U2 with
 //   d = -c/2 - (3/8) i[a1, c] - (1/8) i[a2, c] + O(a^4),  a_k = im_tl(U_k), c = i[a1, a2]
 // (obtained by expanding the matching condition order by order in the link fields).
-struct IcSeries {
-    Al<double> a1, a2, c, cubic;  // cubic = d + c/2
+template <class T> struct IcSeries {
+    Al<T> a1, a2, c, cubic;  // cubic = d + c/2
 };
-DEV IcSeries ic_series(const M3<double>& U1, const M3<double>& U2) {
-    IcSeries q;
+template <class T> DEV IcSeries<T> ic_series(const M3<T>& U1, const M3<T>& U2) {
+    IcSeries<T> q;
     q.a1 = im_tl(U1);
     q.a2 = im_tl(U2);
     q.c = icomm(q.a1, q.a2);
-    const Al<double> c1 = icomm(q.a1, q.c), c2 = icomm(q.a2, q.c);
+    const Al<T> c1 = icomm(q.a1, q.c), c2 = icomm(q.a2, q.c);
 #pragma unroll
-    for (int a = 0; a < 8; a++) q.cubic.a[a] = -0.375 * c1.a[a] - 0.125 * c2.a[a];
+    for (int a = 0; a < 8; a++) q.cubic.a[a] = T(-0.375) * c1.a[a] - T(0.125) * c2.a[a];
     return q;
 }
-DEV Al<double> series_offset(const IcSeries& q) {
-    Al<double> d;
+template <class T> DEV Al<T> series_offset(const IcSeries<T>& q) {
+    Al<T> d;
 #pragma unroll
-    for (int a = 0; a < 8; a++) d.a[a] = -0.5 * q.c.a[a] + q.cubic.a[a];
+    for (int a = 0; a < 8; a++) d.a[a] = T(-0.5) * q.c.a[a] + q.cubic.a[a];
     return d;
+}
+// FP32 copy of an FP64 matrix (warm-start inputs need no more)
+DEV M3<float> to_f32(const M3<double>& A) {
+    M3<float> B;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) B.m[i][j] = mk((float)A.m[i][j].r, (float)A.m[i][j].i);
+    return B;
+}
+// One Newton step with step halving on U (residual norm rn at U on entry).  Returns
+// false when the Jacobian is singular (U unchanged); otherwise U and rn hold the new
+// iterate and *stalled tells whether no halving reduced the residual.
+DEV bool newton_step(const M3<double>& S, M3<double>& U, Al<double>& r, double& rn, bool* stalled) {
+    // J_ab = -Re Tr[t^a (S U^dag) t^b] = -(1/2) re_comp(S U^dag t^b)^a
+    const M3<double> SU = mul_nd(S, U);
+    double J[8][8], b[8], d[8];
+    for (int bb = 0; bb < 8; bb++) {
+        const Al<double> col = re_comp(mul(SU, gen(bb)));
+#pragma unroll
+        for (int a = 0; a < 8; a++) J[a][bb] = -0.5 * col.a[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 8; a++) b[a] = -r.a[a];
+    if (!solve8(J, b, d)) return false;
+    double lam = 1.0, rnn = 0.0;
+    M3<double> Un = U;
+    Al<double> rnew = r;
+    for (int h = 0; h < 12; h++) {
+        Al<double> dx;
+#pragma unroll
+        for (int a = 0; a < 8; a++) dx.a[a] = lam * d[a];
+        Un = mul(expi(herm(dx)), U);
+        rnew = ic_residual(S, Un);
+        rnn = nrm8(rnew);
+        if (rnn < rn) break;
+        lam *= 0.5;
+    }
+    *stalled = !(rnn < rn);
+    U = Un;
+    r = rnew;
+    rn = rnn;
+    return true;
 }
 // Newton with step halving from the given U; returns iterations or -1
 DEV int newton_link(const M3<double>& U1, const M3<double>& U2, M3<double>& U, double tol, int max_iter,
@@ -177,35 +220,9 @@ DEV int newton_link(const M3<double>& U1, const M3<double>& U2, M3<double>& U, d
     double rn = nrm8(r);
     int it = 0;
     while (rn > tol && it < max_iter) {
-        // J_ab = -Re Tr[t^a (S U^dag) t^b] = -(1/2) re_comp(S U^dag t^b)^a
-        const M3<double> SU = mul_nd(S, U);
-        double J[8][8], b[8], d[8];
-        for (int bb = 0; bb < 8; bb++) {
-            const Al<double> col = re_comp(mul(SU, gen(bb)));
-#pragma unroll
-            for (int a = 0; a < 8; a++) J[a][bb] = -0.5 * col.a[a];
-        }
-#pragma unroll
-        for (int a = 0; a < 8; a++) b[a] = -r.a[a];
-        if (!solve8(J, b, d)) break;
-        double lam = 1.0, rnn = 0.0;
-        M3<double> Un = U;
-        Al<double> rnew = r;
-        for (int h = 0; h < 12; h++) {
-            Al<double> dx;
-#pragma unroll
-            for (int a = 0; a < 8; a++) dx.a[a] = lam * d[a];
-            Un = mul(expi(herm(dx)), U);
-            rnew = ic_residual(S, Un);
-            rnn = nrm8(rnew);
-            if (rnn < rn) break;
-            lam *= 0.5;
-        }
+        bool stalled = false;
+        if (!newton_step(S, U, r, rn, &stalled)) break;
         it++;
-        U = Un;
-        r = rnew;
-        const bool stalled = !(rnn < rn);
-        rn = rnn;
         if (stalled) break;
     }
     res = rn;

@@ -92,7 +92,8 @@ cudaError_t launch_casimir_drift(int prec, const PartHost& P, int np, double q2,
 // ---------------- initial conditions (FP64 scratch)
 struct ICScratch {
     double* V1; double* V2;   // [ns][18]
-    double* fft;              // complex [8][ns]
+    double* fft;              // real [8][ns]: charges rho, then Lambda
+    double* spec;             // complex [8][n][n/2 + 1]: their half spectrum
     double* U;                // [ns][2][18]
     double* pi0;              // [ns][8]
     int* iters;               // [2 ns]
@@ -100,6 +101,9 @@ struct ICScratch {
     void* fft_work; size_t fft_work_bytes;
     float* X;                 // [2 ns][36] warm-start features
     float* D;                 // [2 ns][8]  predicted starting corrections
+    double* ktab;             // [n] lattice momenta 4 sin^2(pi k / n)
+    int* nwt;                 // Newton passes: attempt [2 ns], iterations in it [2 ns], two link lists [2][2 ns]
+    int* ncnt;                // list lengths [2]
 };
 size_t ic_scratch_bytes(int n, size_t fft_work_bytes);
 ICScratch ic_layout(void* base, int n, size_t fft_work_bytes);

@@ -2,6 +2,8 @@
 // Philox charges -> Poisson (cuFFT) -> Wilson lines -> pure-gauge nucleus links
 // -> Newton solve of the tau = 0+ links -> pi(0) -> state at step 1.
 #include <cufft.h>
+
+#include <algorithm>
 #include <vector>
 
 #include "ic.cuh"
@@ -9,11 +11,14 @@
 
 namespace glasma {
 
+// half-spectrum elements of one real n x n transform
+static size_t spec_elems(int n) { return (size_t)n * (size_t)(n / 2 + 1); }
 size_t ic_scratch_bytes(int n, size_t fft_work_bytes) {
     const size_t ns = (size_t)n * n;
-    return 2 * align256(ns * 18 * 8) + align256(ns * 8 * 16) + align256(ns * 36 * 8) + align256(ns * 8 * 8) +
+    return 2 * align256(ns * 18 * 8) + align256(ns * 8 * 8) + align256(spec_elems(n) * 8 * 16) +
+           align256(ns * 36 * 8) + align256(ns * 8 * 8) +
            align256(2 * ns * 4) + align256(2 * ns * 8) + align256(fft_work_bytes) + align256(2 * ns * 36 * 4) +
-           align256(2 * ns * 8 * 4) + 256;
+           align256(2 * ns * 8 * 4) + align256((size_t)n * 8) + align256(4 * 2 * ns * 4) + align256(16) + 256;
 }
 ICScratch ic_layout(void* base, int n, size_t fft_work_bytes) {
     const size_t ns = (size_t)n * n;
@@ -21,7 +26,8 @@ ICScratch ic_layout(void* base, int n, size_t fft_work_bytes) {
     ICScratch s;
     s.V1 = (double*)p; p += align256(ns * 18 * 8);
     s.V2 = (double*)p; p += align256(ns * 18 * 8);
-    s.fft = (double*)p; p += align256(ns * 8 * 16);
+    s.fft = (double*)p; p += align256(ns * 8 * 8);
+    s.spec = (double*)p; p += align256(spec_elems(n) * 8 * 16);
     s.U = (double*)p; p += align256(ns * 36 * 8);
     s.pi0 = (double*)p; p += align256(ns * 8 * 8);
     s.iters = (int*)p; p += align256(2 * ns * 4);
@@ -30,31 +36,52 @@ ICScratch ic_layout(void* base, int n, size_t fft_work_bytes) {
     s.fft_work_bytes = fft_work_bytes;
     p += align256(fft_work_bytes);
     s.X = (float*)p; p += align256(2 * ns * 36 * 4);
-    s.D = (float*)p;
+    s.D = (float*)p; p += align256(2 * ns * 8 * 4);
+    s.ktab = (double*)p; p += align256((size_t)n * 8);
+    s.nwt = (int*)p; p += align256(4 * 2 * ns * 4);
+    s.ncnt = (int*)p;
     return s;
 }
 
-static bool make_plan(int n, cufftHandle* plan, size_t* work, const char** err) {
-    if (cufftCreate(plan) != CUFFT_SUCCESS) { *err = "cufftCreate failed"; return false; }
-    if (cufftSetAutoAllocation(*plan, 0) != CUFFT_SUCCESS) { *err = "cufftSetAutoAllocation failed"; cufftDestroy(*plan); return false; }
+// real-to-complex forward and complex-to-real inverse 2-D transforms, 8 color
+// components per call (the charges and Lambda are real)
+struct Plans {
+    cufftHandle fwd = 0, inv = 0;
+    bool ok_fwd = false, ok_inv = false;
+    ~Plans() {
+        if (ok_fwd) cufftDestroy(fwd);
+        if (ok_inv) cufftDestroy(inv);
+    }
+};
+static bool make_plans(int n, Plans& P, size_t* work, const char** err) {
     int dims[2] = {n, n};
-    if (cufftMakePlanMany(*plan, 2, dims, nullptr, 1, n * n, nullptr, 1, n * n, CUFFT_Z2Z, 8, work) != CUFFT_SUCCESS) {
-        *err = "cufftMakePlanMany failed";
-        cufftDestroy(*plan);
+    const int ns = n * n, nh = n * (n / 2 + 1);
+    size_t w1 = 0, w2 = 0;
+    if (cufftCreate(&P.fwd) != CUFFT_SUCCESS) { *err = "cufftCreate failed"; return false; }
+    P.ok_fwd = true;
+    if (cufftCreate(&P.inv) != CUFFT_SUCCESS) { *err = "cufftCreate failed"; return false; }
+    P.ok_inv = true;
+    if (cufftSetAutoAllocation(P.fwd, 0) != CUFFT_SUCCESS || cufftSetAutoAllocation(P.inv, 0) != CUFFT_SUCCESS) {
+        *err = "cufftSetAutoAllocation failed";
         return false;
     }
+    if (cufftMakePlanMany(P.fwd, 2, dims, nullptr, 1, ns, nullptr, 1, nh, CUFFT_D2Z, 8, &w1) != CUFFT_SUCCESS ||
+        cufftMakePlanMany(P.inv, 2, dims, nullptr, 1, nh, nullptr, 1, ns, CUFFT_Z2D, 8, &w2) != CUFFT_SUCCESS) {
+        *err = "cufftMakePlanMany failed";
+        return false;
+    }
+    *work = std::max(w1, w2);
     return true;
 }
 size_t ic_fft_work_bytes(int n, const char** err) {
-    cufftHandle plan;
+    Plans P;
     size_t work = 0;
-    if (!make_plan(n, &plan, &work, err)) return (size_t)-1;
-    cufftDestroy(plan);
+    if (!make_plans(n, P, &work, err)) return (size_t)-1;
     return work;
 }
 
-// rho^a for one (nucleus, sheet): buf[a][s] complex, imaginary part 0
-__global__ void k_mv_charges(double2* __restrict__ buf, int n, int n_sheets, double sigma, uint2 key, int nucleus,
+// rho^a for one (nucleus, sheet): buf[a][s]
+__global__ void k_mv_charges(double* __restrict__ buf, int n, int n_sheets, double sigma, uint2 key, int nucleus,
                              int sheet) {
     const size_t ns = (size_t)n * n;
     const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -65,23 +92,33 @@ __global__ void k_mv_charges(double2* __restrict__ buf, int n, int n_sheets, dou
         double g0, g1, g2, g3;
         box_muller(r.x, r.y, g0, g1);
         box_muller(r.z, r.w, g2, g3);
-        buf[(size_t)(4 * k + 0) * ns + s] = make_double2(sigma * g0, 0.0);
-        buf[(size_t)(4 * k + 1) * ns + s] = make_double2(sigma * g1, 0.0);
-        buf[(size_t)(4 * k + 2) * ns + s] = make_double2(sigma * g2, 0.0);
-        buf[(size_t)(4 * k + 3) * ns + s] = make_double2(sigma * g3, 0.0);
+        buf[(size_t)(4 * k + 0) * ns + s] = sigma * g0;
+        buf[(size_t)(4 * k + 1) * ns + s] = sigma * g1;
+        buf[(size_t)(4 * k + 2) * ns + s] = sigma * g2;
+        buf[(size_t)(4 * k + 3) * ns + s] = sigma * g3;
     }
 }
-// divide by (k~^2 + m^2) N^2 (the inverse transform is unnormalised); zero mode -> 0
-__global__ void k_poisson_scale(double2* __restrict__ buf, int n, double m2) {
-    const size_t ns = (size_t)n * n;
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= 8 * ns) return;
-    const size_t s = i % ns;
-    const int kx = (int)(s % n), ky = (int)(s / n);
-    if (kx == 0 && ky == 0) { buf[i] = make_double2(0.0, 0.0); return; }
-    const double sx = sinpi((double)kx / n), sy = sinpi((double)ky / n);
-    const double f = 1.0 / ((4.0 * sx * sx + 4.0 * sy * sy + m2) * (double)ns);
-    buf[i] = make_double2(buf[i].x * f, buf[i].y * f);
+// lattice momenta k~_i^2 = 4 sin^2(pi k_i / n), once per solve
+__global__ void k_lattice_momenta(double* __restrict__ ktab, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double s = sinpi((double)k / n);
+    ktab[k] = 4.0 * s * s;
+}
+// divide the half spectrum by (k~^2 + m^2) N^2 (the inverse transform is
+// unnormalised); zero mode -> 0.  One thread per momentum, all 8 color components.
+__global__ void k_poisson_scale(double2* __restrict__ spec, const double* __restrict__ ktab, int n, double m2) {
+    const int nh = n / 2 + 1;
+    const size_t ne = (size_t)n * nh;
+    const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (s >= ne) return;
+    const int kx = (int)(s % nh), ky = (int)(s / nh);
+    const double f = (kx == 0 && ky == 0) ? 0.0 : 1.0 / ((ktab[kx] + ktab[ky] + m2) * ((double)n * n));
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+        const double2 v = spec[(size_t)a * ne + s];
+        spec[(size_t)a * ne + s] = make_double2(v.x * f, v.y * f);
+    }
 }
 __global__ void k_set_identity(double* __restrict__ V, size_t count) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -89,13 +126,13 @@ __global__ void k_set_identity(double* __restrict__ V, size_t count) {
     st18(V + 18 * i, ident());
 }
 // V <- exp(-i Lambda) V
-__global__ void k_wilson_accum(const double2* __restrict__ lam, double* __restrict__ V, int n) {
+__global__ void k_wilson_accum(const double* __restrict__ lam, double* __restrict__ V, int n) {
     const size_t ns = (size_t)n * n;
     const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (s >= ns) return;
     Al<double> x;
 #pragma unroll
-    for (int a = 0; a < 8; a++) x.a[a] = -lam[(size_t)a * ns + s].x;
+    for (int a = 0; a < 8; a++) x.a[a] = -lam[(size_t)a * ns + s];
     st18(V + 18 * s, mul(expi(herm(x)), ld18(V + 18 * s)));
 }
 DEV M3<double> nucleus_link(const double* V, int n, int x, int y, int d) {
@@ -103,50 +140,106 @@ DEV M3<double> nucleus_link(const double* V, int n, int x, int y, int d) {
     const int yn = d == 1 ? (y == n - 1 ? 0 : y + 1) : y;
     return mul_nd(ld18(V + 18 * (x + (size_t)n * y)), ld18(V + 18 * (xn + (size_t)n * yn)));
 }
-// Newton solve per link.  Start: exp(i (d_s + delta).t) U1 U2 when a predicted
-// correction delta is given (d_s the third-order series of ic.cuh), else U1 U2; on
-// a stall, restart from U1 U2 (after a warm start) and then from 1.  The iteration
-// count includes every attempt.
-__global__ void k_links_solve(const double* __restrict__ V1, const double* __restrict__ V2, int n, double tol,
-                              int max_iter, double* __restrict__ U, int* __restrict__ iters,
-                              double* __restrict__ res, const float* __restrict__ delta) {
-    const size_t ns = (size_t)n * n;
+// Newton solve of every link, in passes over a compacted list of the links not yet
+// converged, one Newton step per link and pass (links that need few steps cost only
+// those: no warp waits for a slower neighbour).  Attempts per link: the start
+// exp(i (d_s + delta).t) U1 U2 when a predicted correction delta is given (d_s the
+// third-order series of ic.cuh), then U1 U2, then 1; an attempt ends when it
+// converges, stalls, meets a singular Jacobian or reaches max_iter steps, and a failed
+// attempt counts max_iter towards the link's total.  iters[l] holds the attempts'
+// spent count while the link is active and its total (or -1) once it is done.
+struct NewtonState {
+    const double *V1, *V2;
+    int n;
+    double tol;
+    int max_iter;
+    double* U;     // [ns][2][18]
+    int* iters;    // [2 ns]
+    double* res;   // [2 ns]
+    int* att;      // [2 ns] attempt: 0 warm start, 1 U1 U2, 2 identity
+    int* ita;      // [2 ns] steps of the current attempt
+};
+DEV void link_pair(const NewtonState& N, size_t l, M3<double>& U1, M3<double>& U2) {
+    const size_t s = l >> 1;
+    const int d = (int)(l & 1), x = (int)(s % N.n), y = (int)(s / N.n);
+    U1 = nucleus_link(N.V1, N.n, x, y, d);
+    U2 = nucleus_link(N.V2, N.n, x, y, d);
+}
+// start attempt a of link l at u; done (converged) -> iters final, else queued
+DEV void newton_begin(const NewtonState& N, size_t l, int a, int spent, const M3<double>& S, const M3<double>& u,
+                      int* out, int* out_n) {
+    const double rn = nrm8(ic_residual(S, u));
+    st18(N.U + 18 * l, u);
+    N.res[l] = rn;
+    N.att[l] = a;
+    N.ita[l] = 0;
+    if (rn <= N.tol) {
+        N.iters[l] = spent;
+    } else {
+        N.iters[l] = spent;
+        out[atomicAdd(out_n, 1)] = (int)l;
+    }
+}
+__global__ void k_newton_start(NewtonState N, const float* __restrict__ delta, int* __restrict__ out,
+                               int* __restrict__ out_n) {
+    const size_t ns = (size_t)N.n * N.n;
     const size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (l >= 2 * ns) return;
-    const size_t s = l >> 1;
-    const int d = (int)(l & 1);
-    const int x = (int)(s % n), y = (int)(s / n);
-    const M3<double> U1 = nucleus_link(V1, n, x, y, d), U2 = nucleus_link(V2, n, x, y, d);
-    const M3<double> P = mul(U1, U2);
-    M3<double> u = P;
-    int spent = 0;
-    double r;
-    int it;
+    M3<double> U1, U2;
+    link_pair(N, l, U1, U2);
+    const M3<double> S = addm(U1, U2), P = mul(U1, U2);
     if (delta) {
-        Al<double> dl = series_offset(ic_series(U1, U2));
+        // the series in FP32: the start needs no more than the network's accuracy
+        const Al<float> sf = series_offset(ic_series(to_f32(U1), to_f32(U2)));
+        Al<double> dl;
 #pragma unroll
-        for (int a = 0; a < 8; a++) dl.a[a] += (double)delta[8 * l + a];
-        u = mul(expi(herm(dl)), P);
-        it = newton_link(U1, U2, u, tol, max_iter, r);
-        if (it < 0) {
-            spent = max_iter;
-            u = P;
-            it = newton_link(U1, U2, u, tol, max_iter, r);
-        }
+        for (int a = 0; a < 8; a++) dl.a[a] = (double)sf.a[a] + (double)delta[8 * l + a];
+        newton_begin(N, l, 0, 0, S, mul(expi(herm(dl)), P), out, out_n);
     } else {
-        it = newton_link(U1, U2, u, tol, max_iter, r);
+        newton_begin(N, l, 1, 0, S, P, out, out_n);
     }
-    if (it < 0) {
-        spent += max_iter;
-        u = ident();
-        it = newton_link(U1, U2, u, tol, max_iter, r);
-    }
-    if (it >= 0) it += spent;
-    st18(U + 36 * s + 18 * d, u);
-    iters[l] = it;
-    res[l] = r;
 }
-// pi(0) = -(i/4) sum_i {[(U-1)(U2^dag-U1^dag) - h.c.](x) + [(U^dag-1)(U2-U1) - h.c.](x-i)}
+__global__ void k_newton_pass(NewtonState N, const int* __restrict__ in, const int* __restrict__ in_n,
+                              int* __restrict__ out, int* __restrict__ out_n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *in_n) return;
+    const size_t l = (size_t)in[k];
+    M3<double> U1, U2;
+    link_pair(N, l, U1, U2);
+    const M3<double> S = addm(U1, U2);
+    M3<double> u = ld18(N.U + 18 * l);
+    Al<double> r = ic_residual(S, u);
+    double rn = N.res[l];
+    bool stalled = false;
+    const bool exhausted = N.ita[l] >= N.max_iter;
+    const bool ok = !exhausted && newton_step(S, u, r, rn, &stalled);
+    const int it = N.ita[l] + (ok ? 1 : 0);
+    const int spent = N.iters[l];
+    if (ok && rn <= N.tol) {  // converged
+        st18(N.U + 18 * l, u);
+        N.res[l] = rn;
+        N.iters[l] = spent + it;
+        return;
+    }
+    if (!ok || stalled || it >= N.max_iter) {  // this attempt failed: next start, or give up
+        const int a = N.att[l] + 1;
+        if (a == 1) {
+            newton_begin(N, l, 1, spent + N.max_iter, S, mul(U1, U2), out, out_n);
+        } else if (a == 2) {
+            newton_begin(N, l, 2, spent + N.max_iter, S, ident(), out, out_n);
+        } else {
+            st18(N.U + 18 * l, u);
+            N.res[l] = rn;
+            N.iters[l] = -1;
+        }
+        return;
+    }
+    st18(N.U + 18 * l, u);
+    N.res[l] = rn;
+    N.ita[l] = it;
+    out[atomicAdd(out_n, 1)] = (int)l;
+}
+
 __global__ void k_pi0(const double* __restrict__ V1, const double* __restrict__ V2, const double* __restrict__ U,
                       int n, double* __restrict__ pi) {
     const size_t ns = (size_t)n * n;
@@ -218,40 +311,56 @@ int ic_run(int prec, int n, int n_sheets, double g2mua, double m_ir_a, uint64_t 
     const uint2 key = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
     const double sigma = g2mua / sqrt((double)n_sheets);
     const int nb = (int)((ns + 255) / 256);
-    cufftHandle plan;
+    Plans plan;
     size_t work = 0;
     std::vector<int> it_h;
-    if (!make_plan(n, &plan, &work, err)) return -2;
-    if (work > s.fft_work_bytes) { *err = "cuFFT work area larger than reserved"; cufftDestroy(plan); return -6; }
-    if (cufftSetWorkArea(plan, s.fft_work) != CUFFT_SUCCESS || cufftSetStream(plan, st) != CUFFT_SUCCESS) {
+    if (!make_plans(n, plan, &work, err)) return -2;
+    if (work > s.fft_work_bytes) { *err = "cuFFT work area larger than reserved"; return -6; }
+    if (cufftSetWorkArea(plan.fwd, s.fft_work) != CUFFT_SUCCESS || cufftSetStream(plan.fwd, st) != CUFFT_SUCCESS ||
+        cufftSetWorkArea(plan.inv, s.fft_work) != CUFFT_SUCCESS || cufftSetStream(plan.inv, st) != CUFFT_SUCCESS) {
         *err = "cufftSetWorkArea/SetStream failed";
-        cufftDestroy(plan);
         return -2;
     }
+    k_lattice_momenta<<<(n + 255) / 256, 256, 0, st>>>(s.ktab, n);
     for (int A = 0; A < 2; A++) {
         double* V = A == 0 ? s.V1 : s.V2;
         k_set_identity<<<nb, 256, 0, st>>>(V, ns);
         for (int sh = 0; sh < n_sheets; sh++) {
-            double2* fb = (double2*)s.fft;
-            k_mv_charges<<<nb, 256, 0, st>>>(fb, n, n_sheets, sigma, key, A, sh);
-            if (cufftExecZ2Z(plan, (cufftDoubleComplex*)fb, (cufftDoubleComplex*)fb, CUFFT_FORWARD) != CUFFT_SUCCESS) {
-                *err = "cufftExecZ2Z forward failed";
-                goto fail;
+            k_mv_charges<<<nb, 256, 0, st>>>(s.fft, n, n_sheets, sigma, key, A, sh);
+            if (cufftExecD2Z(plan.fwd, (cufftDoubleReal*)s.fft, (cufftDoubleComplex*)s.spec) != CUFFT_SUCCESS) {
+                *err = "cufftExecD2Z failed";
+                return -2;
             }
-            k_poisson_scale<<<(int)((8 * ns + 255) / 256), 256, 0, st>>>(fb, n, m_ir_a * m_ir_a);
-            if (cufftExecZ2Z(plan, (cufftDoubleComplex*)fb, (cufftDoubleComplex*)fb, CUFFT_INVERSE) != CUFFT_SUCCESS) {
-                *err = "cufftExecZ2Z inverse failed";
-                goto fail;
+            k_poisson_scale<<<(int)((spec_elems(n) + 255) / 256), 256, 0, st>>>((double2*)s.spec, s.ktab, n,
+                                                                             m_ir_a * m_ir_a);
+            if (cufftExecZ2D(plan.inv, (cufftDoubleComplex*)s.spec, (cufftDoubleReal*)s.fft) != CUFFT_SUCCESS) {
+                *err = "cufftExecZ2D failed";
+                return -2;
             }
-            k_wilson_accum<<<nb, 256, 0, st>>>(fb, V, n);
+            k_wilson_accum<<<nb, 256, 0, st>>>(s.fft, V, n);
         }
     }
     if (mlp) {
         IC_CHECK(launch_ic_features(s, n, s.X, nullptr, st));
         IC_CHECK(mlp_predict_dev(mlp, s.X, (int64_t)(2 * ns), s.D, st));
     }
-    k_links_solve<<<(int)((2 * ns + 63) / 64), 64, 0, st>>>(s.V1, s.V2, n, tol, max_iter, s.U, s.iters, s.res,
-                                                            mlp ? s.D : nullptr);
+    {
+        const NewtonState N{s.V1, s.V2, n, tol, max_iter, s.U, s.iters, s.res, s.nwt, s.nwt + 2 * ns};
+        int* list[2] = {s.nwt + 4 * ns, s.nwt + 6 * ns};
+        IC_CHECK(cudaMemsetAsync(s.ncnt, 0, 2 * sizeof(int), st));
+        k_newton_start<<<(int)((2 * ns + 127) / 128), 128, 0, st>>>(N, mlp ? s.D : nullptr, list[0], s.ncnt);
+        // every pass advances each listed link by one step; a link takes at most
+        // 3 * max_iter steps, and the host reads the list length between passes
+        for (int pass = 0, cur = 0; pass <= 3 * max_iter + 3; pass++, cur ^= 1) {
+            int cnt = 0;
+            IC_CHECK(cudaMemcpyAsync(&cnt, s.ncnt + cur, sizeof(int), cudaMemcpyDeviceToHost, st));
+            IC_CHECK(cudaStreamSynchronize(st));
+            if (cnt == 0) break;
+            IC_CHECK(cudaMemsetAsync(s.ncnt + (cur ^ 1), 0, sizeof(int), st));
+            k_newton_pass<<<(cnt + 127) / 128, 128, 0, st>>>(N, list[cur], s.ncnt + cur, list[cur ^ 1],
+                                                            s.ncnt + (cur ^ 1));
+        }
+    }
     k_pi0<<<nb, 256, 0, st>>>(s.V1, s.V2, s.U, n, s.pi0);
     if (prec) k_ic_finalize<float><<<nb, 256, 0, st>>>(s.U, s.pi0, n, dtau, (float*)buf);
     else k_ic_finalize<double><<<nb, 256, 0, st>>>(s.U, s.pi0, n, dtau, (double*)buf);
@@ -270,10 +379,8 @@ int ic_run(int prec, int n, int n_sheets, double g2mua, double m_ir_a, uint64_t 
         *mean_it = (2 * ns - f) > 0 ? (double)sum / (double)(2 * ns - f) : 0.0;
         *max_it = mx;
     }
-    cufftDestroy(plan);
     return 0;
 fail:
-    cufftDestroy(plan);
     return -2;
 }
 

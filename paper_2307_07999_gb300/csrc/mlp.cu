@@ -22,6 +22,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <random>
 #include <vector>
@@ -73,19 +74,29 @@ DEV void afrag_from_acc(const float c0[4], const float c1[4], uint32_t a[4]) {
     a[3] = pack_bf16(c1[2], c1[3]);
 }
 
-struct MlpSmem {
+struct MlpSmem {  // training: activations and gradients of the CTA's rows
     __nv_bfloat16 w1[MH * MK1], w2[MH * MH], w3[MO * MH], w2t[MH * MH], w3t[MH * MO];
     __nv_bfloat16 x[MROWS * MK1], h1[MROWS * MH], h2[MROWS * MH], d2[MROWS * MH], d1[MROWS * MH];
     float dy[MROWS * MO];
     float b1[MH], b2[MH], b3[MO];
 };
+struct MlpSmemInfer {  // inference: weights and one row tile (layers chain in registers)
+    __nv_bfloat16 w1[MH * MK1], w2[MH * MH], w3[MO * MH];
+    __nv_bfloat16 x[MROWS * MK1];
+    float b1[MH], b2[MH], b3[MO];
+};
+template <bool TRAIN> struct MlpSmemOf { using type = MlpSmem; };
+template <> struct MlpSmemOf<false> { using type = MlpSmemInfer; };
 
+// Training (TRAIN): one 64-row tile per CTA, forward and backward.  Inference: a
+// persistent grid, weights loaded once per CTA, row tiles strided over the grid.
 template <bool TRAIN>
 __global__ void __launch_bounds__(128) k_mlp(MlpDev m, const float* __restrict__ X, const float* __restrict__ Tg,
                                               int N, float* __restrict__ Y, float* __restrict__ grad,
                                               double* __restrict__ loss) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    MlpSmem& S = *reinterpret_cast<MlpSmem*>(smraw);
+    using SM = typename MlpSmemOf<TRAIN>::type;
+    SM& S = *reinterpret_cast<SM*>(smraw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
     // weights and biases into shared memory
     {
@@ -94,14 +105,19 @@ __global__ void __launch_bounds__(128) k_mlp(MlpDev m, const float* __restrict__
         const int cnt[3] = {MH * MK1 / 8, MH * MH / 8, MO * MH / 8};
         for (int q = 0; q < 3; q++)
             for (int i = tid; i < cnt[q]; i += 128) dst[q][i] = src[q][i];
-        if (TRAIN) {
+        if constexpr (TRAIN) {
             for (int i = tid; i < MH * MH / 8; i += 128) ((uint4*)S.w2t)[i] = ((const uint4*)m.w2t)[i];
             for (int i = tid; i < MH * MO / 8; i += 128) ((uint4*)S.w3t)[i] = ((const uint4*)m.w3t)[i];
         }
         for (int i = tid; i < MH; i += 128) { S.b1[i] = m.p[O_B1 + i]; S.b2[i] = m.p[O_B2 + i]; }
         if (tid < MO) S.b3[tid] = m.p[O_B3 + tid];
+    }
+    const int ntiles = (N + MROWS - 1) / MROWS;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();  // weights in place; the previous tile's inputs consumed
+    {
         // input rows (scaled, BF16, zero padded)
-        const int r0 = blockIdx.x * MROWS;
+        const int r0 = tile * MROWS;
         for (int i = tid; i < MROWS * MK1; i += 128) {
             const int r = i / MK1, k = i % MK1;
             const float v = (r0 + r < N && k < MI) ? X[(size_t)(r0 + r) * MI + k] * m.x_inv : 0.0f;
@@ -110,7 +126,7 @@ __global__ void __launch_bounds__(128) k_mlp(MlpDev m, const float* __restrict__
     }
     __syncthreads();
     const int rw = warp * 16;  // this warp's rows within the CTA
-    const int row0 = blockIdx.x * MROWS + rw;
+    const int row0 = tile * MROWS + rw;
     // ---- layer 1
     float c1[16][4];
 #pragma unroll
@@ -137,7 +153,7 @@ __global__ void __launch_bounds__(128) k_mlp(MlpDev m, const float* __restrict__
     for (int nt = 0; nt < 16; nt++)
 #pragma unroll
         for (int q = 0; q < 4; q++) c1[nt][q] = tanhf(c1[nt][q]);
-    if (TRAIN) {
+    if constexpr (TRAIN) {
 #pragma unroll
         for (int nt = 0; nt < 16; nt++) {
             const int col = nt * 8 + 2 * t;
@@ -167,7 +183,7 @@ __global__ void __launch_bounds__(128) k_mlp(MlpDev m, const float* __restrict__
     for (int nt = 0; nt < 16; nt++)
 #pragma unroll
         for (int q = 0; q < 4; q++) c2[nt][q] = tanhf(c2[nt][q]);
-    if (TRAIN) {
+    if constexpr (TRAIN) {
 #pragma unroll
         for (int nt = 0; nt < 16; nt++) {
             const int col = nt * 8 + 2 * t;
@@ -194,7 +210,7 @@ __global__ void __launch_bounds__(128) k_mlp(MlpDev m, const float* __restrict__
         }
     }
     const int ra = row0 + g, rb = row0 + g + 8;
-    if (!TRAIN) {
+    if constexpr (!TRAIN) {
         // outputs 0..7 (n-tile 0): delta = y * y_scale
         if (ra < N) {
             Y[(size_t)ra * 8 + 2 * t] = c3[0][0] * m.y_scale;
@@ -204,8 +220,7 @@ __global__ void __launch_bounds__(128) k_mlp(MlpDev m, const float* __restrict__
             Y[(size_t)rb * 8 + 2 * t] = c3[0][2] * m.y_scale;
             Y[(size_t)rb * 8 + 2 * t + 1] = c3[0][3] * m.y_scale;
         }
-        return;
-    }
+    } else {
     // ---- loss and dY = 2 (y - target) / (N * 16); targets of outputs 8..15 are 0
     const float norm = 2.0f / ((float)N * MO);
     double lsum = 0.0;
@@ -338,6 +353,8 @@ __global__ void __launch_bounds__(128) k_mlp(MlpDev m, const float* __restrict__
             for (int i = 0; i < 16; i++) atomicAdd(grad + O_W3 + o3 * MH + c0 + i, acc[i]);
         }
     }
+    }  // TRAIN
+    }  // tiles
 }
 
 // Adam on the FP32 master parameters, then the BF16 copies (padded / transposed)
@@ -387,22 +404,8 @@ __global__ void k_sumsq(const float* __restrict__ a, size_t n, double* out) {
 }
 
 // ---------------------------------------------------------------- features, targets, warm starts
-DEV M3<double> nucleus_link_v(const double* V, int n, int x, int y, int d) {
-    const int xn = d == 0 ? (x == n - 1 ? 0 : x + 1) : x;
-    const int yn = d == 1 ? (y == n - 1 ? 0 : y + 1) : y;
-    return mul_nd(ld18(V + 18 * (x + (size_t)n * y)), ld18(V + 18 * (xn + (size_t)n * yn)));
-}
-__global__ void k_ic_features(const double* __restrict__ V1, const double* __restrict__ V2, int n,
-                              const double* __restrict__ U, float* __restrict__ X, float* __restrict__ T) {
-    const size_t ns = (size_t)n * n;
-    const size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (l >= 2 * ns) return;
-    const size_t s = l >> 1;
-    const int d = (int)(l & 1), x = (int)(s % n), y = (int)(s / n);
-    const M3<double> U1 = nucleus_link_v(V1, n, x, y, d), U2 = nucleus_link_v(V2, n, x, y, d);
-    const IcSeries q = ic_series(U1, U2);
-    float* f = X + 36 * l;
-    double s11 = 0, s22 = 0, s12 = 0, scc = 0;
+template <class T> DEV void put_features(const IcSeries<T>& q, float* f) {
+    T s11 = 0, s22 = 0, s12 = 0, scc = 0;
 #pragma unroll
     for (int a = 0; a < 8; a++) {
         f[a] = (float)q.a1.a[a];
@@ -418,12 +421,33 @@ __global__ void k_ic_features(const double* __restrict__ V1, const double* __res
     f[33] = (float)s22;
     f[34] = (float)s12;
     f[35] = (float)scc;
+}
+// features of every link; with T (training data) also the targets, then in FP64
+// throughout (the targets are differences of nearly equal offsets); without, in FP32
+__global__ void k_ic_features(const double* __restrict__ V1, const double* __restrict__ V2, int n,
+                              const double* __restrict__ U, float* __restrict__ X, float* __restrict__ T) {
+    const size_t ns = (size_t)n * n;
+    const size_t l = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (l >= 2 * ns) return;
+    const size_t s = l >> 1;
+    const int d = (int)(l & 1), x = (int)(s % n), y = (int)(s / n);
+    const int xn = d == 0 ? (x == n - 1 ? 0 : x + 1) : x;
+    const int yn = d == 1 ? (y == n - 1 ? 0 : y + 1) : y;
+    const size_t s2 = xn + (size_t)n * yn;
     if (T) {
+        const M3<double> U1 = mul_nd(ld18(V1 + 18 * s), ld18(V1 + 18 * s2));
+        const M3<double> U2 = mul_nd(ld18(V2 + 18 * s), ld18(V2 + 18 * s2));
+        const IcSeries<double> q = ic_series(U1, U2);
+        put_features(q, X + 36 * l);
         // d^a = 2 Im Tr[t^a U (U1 U2)^dag] minus the series
         const Al<double> dl = im_tl(mul_nd(ld18(U + 36 * s + 18 * d), mul(U1, U2)));
         const Al<double> ds = series_offset(q);
 #pragma unroll
         for (int a = 0; a < 8; a++) T[8 * l + a] = (float)(dl.a[a] - ds.a[a]);
+    } else {
+        const M3<float> U1 = mul_nd(to_f32(ld18(V1 + 18 * s)), to_f32(ld18(V1 + 18 * s2)));
+        const M3<float> U2 = mul_nd(to_f32(ld18(V2 + 18 * s)), to_f32(ld18(V2 + 18 * s2)));
+        put_features(ic_series(U1, U2), X + 36 * l);
     }
 }
 
@@ -512,16 +536,25 @@ static MlpDev dev_view(const glasma_mlp* M) {
 }
 template <bool TRAIN> static cudaError_t launch_mlp(const glasma_mlp* M, const float* X, const float* T, int64_t N,
                                                     float* Y, cudaStream_t st) {
+    using SM = typename MlpSmemOf<TRAIN>::type;
     static bool attr = false;
+    static int grid_cap = 0;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(MlpSmem));
+        cudaError_t e = cudaFuncSetAttribute(k_mlp<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM));
         if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mlp<TRAIN>, 128, sizeof(SM))) != cudaSuccess)
+            return e;
+        grid_cap = std::max(1, sms * per);
         attr = true;
     }
     if (N <= 0) return cudaSuccess;
-    const unsigned nb = (unsigned)((N + MROWS - 1) / MROWS);
-    k_mlp<TRAIN><<<nb, 128, sizeof(MlpSmem), st>>>(dev_view(M), X, T, (int)N, Y, M->g, M->dsc);
+    const long long tiles = (N + MROWS - 1) / MROWS;
+    // training: one tile per CTA (the gradients are per-CTA sums); inference: a persistent grid
+    const unsigned nb = (unsigned)(TRAIN ? tiles : std::min<long long>(tiles, grid_cap));
+    k_mlp<TRAIN><<<nb, 128, sizeof(SM), st>>>(dev_view(M), X, T, (int)N, Y, M->g, M->dsc);
     return cudaGetLastError();
 }
 

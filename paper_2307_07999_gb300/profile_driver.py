@@ -4,6 +4,7 @@
   python -m paper_2307_07999_gb300.profile_driver push 512 100000    # + a 100k-particle push
   python -m paper_2307_07999_gb300.profile_driver batch              # one graph run of the 64-event batch
   python -m paper_2307_07999_gb300.profile_driver batch8             # 8 events of 384^2, 10k charm each
+  python -m paper_2307_07999_gb300.profile_driver ic 1024            # tau = 0+ solve: cold, then warm start
 """
 import sys
 
@@ -24,6 +25,18 @@ def main(argv):
         print("ok")
         return
     n = int(argv[2]) if len(argv) > 2 else 512
+    if what == "ic":
+        from . import WarmStartNet, ic_dataset, init_warm
+        g = Glasma(n, 10.0, precision=1, tau_end_fm=1.0, seed=3)
+        g.init()
+        net = WarmStartNet(seed=1)
+        X, T = ic_dataset(g)  # a quick fit on this event's own links (profiling only)
+        net.fit_scales(X, T)
+        net.train(X, T, epochs=2, batch=16384, lr=2e-3)
+        init_warm(Glasma(n, 10.0, precision=1, tau_end_fm=1.0, seed=3), net)
+        torch.cuda.synchronize()
+        print("ok")
+        return
     g = Glasma(n, 10.0, precision=1, tau_end_fm=1.0, seed=3)
     g.init()
     g.step(4)

@@ -1,0 +1,51 @@
+"""Multi-GPU runs are independent replicas (the method has no exchange step): each
+rank evolves its own batch with its own seeds, and bench.py only needs a barrier
+and a max over ranks of the timed interval.  That host logic, on two gloo ranks."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2307_07999_gb300 import workloads as W
+
+    got_ws, got_rank, local = bench.dist_setup()
+    assert (got_ws, got_rank, local) == (ws, rank, rank)
+    bench.barrier(ws)
+    # the slowest rank's interval is the job's
+    t = bench.max_over_ranks(10.0 + rank, ws)
+    evs, pps = W.batched_uneven(rank=rank)
+    seeds = [e.seed for e in evs] + [p.seed for p in pps]
+    out[rank] = (t, seeds)
+    bench.barrier(ws)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_replicas_barrier_max_and_distinct_seeds():
+    ws = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(ws, port, out), nprocs=ws, join=True)
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 11.0
+    s0, s1 = set(res[0][1]), set(res[1][1])
+    assert len(s0) == len(res[0][1]) and not (s0 & s1)  # every event of every replica is its own
