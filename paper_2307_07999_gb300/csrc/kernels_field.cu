@@ -113,8 +113,8 @@ struct FieldVariant {
     size_t smem;
 };
 #define GL_FV(TX, TY, MB) {TX, TY, MB, (const void*)k_field_step_tiles<TX, TY, MB>, RecTile<float, TX, TY>::smem}
-static const FieldVariant g_fvar[] = {GL_FV(32, 4, 3), GL_FV(16, 8, 3), GL_FV(8, 16, 3),
-                                      GL_FV(32, 6, 2), GL_FV(16, 12, 2), GL_FV(32, 8, 2)};
+static const FieldVariant g_fvar[] = {GL_FV(32, 4, 3), GL_FV(16, 8, 3), GL_FV(8, 16, 3), GL_FV(32, 6, 2),
+                                      GL_FV(16, 12, 2), GL_FV(32, 8, 2), GL_FV(32, 4, 4), GL_FV(16, 8, 4)};
 #undef GL_FV
 static constexpr int N_FVAR = (int)(sizeof(g_fvar) / sizeof(g_fvar[0]));
 
