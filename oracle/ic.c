@@ -5,8 +5,7 @@
  * carry random charges rho^a(x) with <rho rho> ~ Qs^2 (McLerran-Venugopalan
  * model); the Glasma fields after the collision are solved on the transverse
  * lattice in terms of gauge links.  The paper defers the lattice formulas to its
- * companion paper, so the following standard readings are used (each listed in
- * the design doc):
+ * companion paper, so the following standard readings are used:
  *   - rho^a_{A,n}(x) ~ N(0, (g^2 mu a)^2 / Ns), independent per nucleus A,
  *     longitudinal sheet n, site and color;
  *   - Lambda = (-lattice Laplacian + m^2)^-1 rho by FFT, lattice momentum

@@ -18,7 +18,7 @@
  *   - U[s][d][9] (d = 0: x-link, d = 1: y-link), E[s][d][8], phi[s][8], pi[s][8].
  *   - Staggering: U, phi live at tau_n = n*dtau; E, pi live at tau_{n-1/2}.
  *
- * Parity status per function is given in the .c files and in the design doc.
+ * Parity status per function is given in the header comment of each .c file.
  */
 #ifndef GLASMA_ORACLE_H
 #define GLASMA_ORACLE_H
