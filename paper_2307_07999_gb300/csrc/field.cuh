@@ -118,9 +118,8 @@ template <class T, bool CG = false> DEV M3<T> load_link(const T* __restrict__ f,
     complete_row2(U);
     return U;
 }
-// both links of a site from its three link groups
-template <class T, bool CG = false> DEV void load_links(const T* __restrict__ f, size_t ns, size_t s, M3<T>& ux, M3<T>& uy) {
-    const V8<T> a = ld8<CG>(f + fidx(0, s, ns)), b = ld8<CG>(f + fidx(8, s, ns)), c = ld8<CG>(f + fidx(16, s, ns));
+// both links of a site from its three link groups (planes 0-7, 8-15, 16-23)
+template <class T> DEV void links_from_groups(const V8<T>& a, const V8<T>& b, const V8<T>& c, M3<T>& ux, M3<T>& uy) {
 #pragma unroll
     for (int e = 0; e < 4; e++) put_entry(ux, e, a.v[2 * e], a.v[2 * e + 1]);
     put_entry(ux, 4, b.v[0], b.v[1]);
@@ -131,6 +130,9 @@ template <class T, bool CG = false> DEV void load_links(const T* __restrict__ f,
     for (int e = 0; e < 4; e++) put_entry(uy, 2 + e, c.v[2 * e], c.v[2 * e + 1]);
     complete_row2(ux);
     complete_row2(uy);
+}
+template <class T, bool CG = false> DEV void load_links(const T* __restrict__ f, size_t ns, size_t s, M3<T>& ux, M3<T>& uy) {
+    links_from_groups(ld8<CG>(f + fidx(0, s, ns)), ld8<CG>(f + fidx(8, s, ns)), ld8<CG>(f + fidx(16, s, ns)), ux, uy);
 }
 template <class T> DEV void store_links(T* __restrict__ f, size_t ns, size_t s, const M3<T>& ux, const M3<T>& uy) {
     V8<T> a, b, c;
@@ -260,15 +262,37 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     const size_t s = active ? (size_t)x + (size_t)n * y : 0;
     Al<T> Ex = load_alg<T, CG>(src, ns, P_EX, s), Ey = load_alg<T, CG>(src, ns, P_EY, s), pi = load_alg<T, CG>(src, ns, P_PI, s);
 
-    // phase 1: links (completed to 3 rows) and phi of the tile plus a one-site halo
-    for (int h = tid; h < HS; h += TX * TY) {
-        const int hx = h % HX, hy = h / HX;
-        const size_t g = (size_t)wrapi(x0 - 1 + hx, n) + (size_t)n * wrapi(y0 - 1 + hy, n);
-        M3<T> ux, uy;
-        load_links<T, CG>(src, ns, g, ux, uy);
-        rec_put_link(sUx, h, ux);
-        rec_put_link(sUy, h, uy);
-        rec_put_alg(sP, h, load_alg<T, CG>(src, ns, P_PHI, g));
+    // phase 1: links (completed to 3 rows) and phi of the tile plus a one-site halo.
+    // Every load of the thread is issued before the first store, so the CTA waits for
+    // memory once per tile, not once per pass over the halo.
+    {
+        constexpr int NT = TX * TY, NIT = (HS + NT - 1) / NT;
+        V8<T> raw[NIT][4];
+#pragma unroll
+        for (int it = 0; it < NIT; it++) {
+            const int h = tid + it * NT;
+            if (h < HS) {
+                const int hx = h % HX, hy = h / HX;
+                const size_t g = (size_t)wrapi(x0 - 1 + hx, n) + (size_t)n * wrapi(y0 - 1 + hy, n);
+#pragma unroll
+                for (int k = 0; k < 3; k++) raw[it][k] = ld8<CG>(src + fidx(8 * k, g, ns));
+                raw[it][3] = ld8<CG>(src + fidx(P_PHI, g, ns));
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < NIT; it++) {
+            const int h = tid + it * NT;
+            if (h < HS) {
+                M3<T> ux, uy;
+                links_from_groups(raw[it][0], raw[it][1], raw[it][2], ux, uy);
+                rec_put_link(sUx, h, ux);
+                rec_put_link(sUy, h, uy);
+                Al<T> ph;
+#pragma unroll
+                for (int a = 0; a < 8; a++) ph.a[a] = raw[it][3].v[a];
+                rec_put_alg(sP, h, ph);
+            }
+        }
     }
     __syncthreads();
 
