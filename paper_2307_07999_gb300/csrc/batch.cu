@@ -210,6 +210,12 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
         delete b;
         return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
     }
+    // the persistent kernel's counters and error word start cleared (the workspace is
+    // the caller's uninitialised memory)
+    if (cudaMemsetAsync(b->pers_ctrl, 0, 256, b->st) != cudaSuccess || cudaStreamSynchronize(b->st) != cudaSuccess) {
+        delete b;
+        return bfail(GLASMA_ERR_CUDA, "clearing the persistent control block failed");
+    }
     *out = b;
     return GLASMA_OK;
 }

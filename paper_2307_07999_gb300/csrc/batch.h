@@ -56,6 +56,7 @@ struct glasma_batch {
     void* pers_ctrl = nullptr;    // barrier counters + error word + per-iteration prefixes (device)
     int pers_blocks = 0;
     int pers_timeout = 0;
+    bool pers_launched = false;   // the error word is meaningful only after a persistent run
 };
 
 void glasma_set_error(const char* msg);

@@ -311,31 +311,44 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     const int h = (threadIdx.y + 1) * HX + threadIdx.x + 1;
     const int f = (threadIdx.y + 1) * FX + threadIdx.x + 1;
     const Al<T> phi = rec_alg(sP, h);
-    const M3<T> ux = rec_link(sUx, h), uy = rec_link(sUy, h);
-    const M3<T> uxm = rec_link(sUx, h - 1), uym = rec_link(sUy, h - HX);
     const T dt = A.dtau, tb = A.tb, tp = A.tp;
-
-    const Al<T> psx = conj_alg(ux, rec_alg(sP, h + 1));
-    const Al<T> psy = conj_alg(uy, rec_alg(sP, h + HX));
-    {
-        const Al<T> chx = transport_alg(uxm, rec_alg(sP, h - 1));
-        const Al<T> chy = transport_alg(uym, rec_alg(sP, h - HX));
-#pragma unroll
-        for (int a = 0; a < 8; a++)
-            pi.a[a] += dt * tp * (psx.a[a] + chx.a[a] + psy.a[a] + chy.a[a] - T(4) * phi.a[a]);
-    }
-    const Al<T> F0 = rec_alg(sF, f);
-    {
+    // Each link is read from shared memory where it is used and its terms are folded
+    // into the increments at once, which keeps few values live per thread.
+    Al<T> dEx, dEy, dpi;
+    {  // forward x link: U phi(x+x) U^dag, and its commutator with phi (E_x)
+        const Al<T> psx = conj_alg(rec_link(sUx, h), rec_alg(sP, h + 1));
         const Al<T> cm = icomm(phi, psx);
-        const Al<T> t1 = transport_alg(uym, rec_alg(sF, f - FX));
 #pragma unroll
-        for (int a = 0; a < 8; a++) Ex.a[a] += dt * (tb * (t1.a[a] - F0.a[a]) - tp * cm.a[a]);
+        for (int a = 0; a < 8; a++) { dpi.a[a] = psx.a[a]; dEx.a[a] = -tp * cm.a[a]; }
     }
-    {
+    {  // forward y link (E_y)
+        const Al<T> psy = conj_alg(rec_link(sUy, h), rec_alg(sP, h + HX));
         const Al<T> cm = icomm(phi, psy);
+#pragma unroll
+        for (int a = 0; a < 8; a++) { dpi.a[a] += psy.a[a]; dEy.a[a] = -tp * cm.a[a]; }
+    }
+    {  // backward x link: phi(x-x) and the plaquette at x-x carried to x
+        const M3<T> uxm = rec_link(sUx, h - 1);
+        const Al<T> chx = transport_alg(uxm, rec_alg(sP, h - 1));
         const Al<T> t2 = transport_alg(uxm, rec_alg(sF, f - 1));
 #pragma unroll
-        for (int a = 0; a < 8; a++) Ey.a[a] += dt * (tb * (F0.a[a] - t2.a[a]) - tp * cm.a[a]);
+        for (int a = 0; a < 8; a++) { dpi.a[a] += chx.a[a]; dEy.a[a] -= tb * t2.a[a]; }
+    }
+    {  // backward y link: phi(x-y) and the plaquette at x-y carried to x
+        const M3<T> uym = rec_link(sUy, h - HX);
+        const Al<T> chy = transport_alg(uym, rec_alg(sP, h - HX));
+        const Al<T> t1 = transport_alg(uym, rec_alg(sF, f - FX));
+#pragma unroll
+        for (int a = 0; a < 8; a++) { dpi.a[a] += chy.a[a]; dEx.a[a] += tb * t1.a[a]; }
+    }
+    {
+        const Al<T> F0 = rec_alg(sF, f);
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            Ex.a[a] += dt * (dEx.a[a] - tb * F0.a[a]);
+            Ey.a[a] += dt * (dEy.a[a] + tb * F0.a[a]);
+            pi.a[a] += dt * tp * (dpi.a[a] - T(4) * phi.a[a]);
+        }
     }
     T* __restrict__ dst = A.dst;
     store_alg(dst, ns, P_EX, s, Ex);
@@ -353,7 +366,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
 #pragma unroll
         for (int a = 0; a < 8; a++) e.a[a] *= A.ue;
         const M3<T> W = expi(herm(e));
-        const M3<T>& U = d == 0 ? ux : uy;
+        const M3<T> U = rec_link(d == 0 ? sUx : sUy, h);
         M3<T> V;
 #pragma unroll
         for (int r = 0; r < 2; r++)

@@ -159,6 +159,7 @@ template <class T> static glasma_status run_impl(glasma_batch* b) {
     void* args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_persistent<T>, dim3(b->pers_blocks), dim3(TX, TY), args,
                                                 sm, b->st);
+    if (e == cudaSuccess) b->pers_launched = true;
     return e == cudaSuccess ? GLASMA_OK : GLASMA_ERR_CUDA;
 }
 
@@ -190,7 +191,7 @@ glasma_status batch_run_persistent(glasma_batch* b) {
 }
 
 bool batch_timed_out(glasma_batch* b) {
-    if (!b->pers_ctrl) return false;
+    if (!b->pers_ctrl || !b->pers_launched) return false;
     int err = 0;
     if (cudaMemcpy(&err, (char*)b->pers_ctrl + 8, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
     if (err) cudaMemset((char*)b->pers_ctrl + 8, 0, sizeof(int));
