@@ -4,6 +4,8 @@
   python -m paper_2307_07999_gb300.profile_driver push 512 100000    # + a 100k-particle push
   python -m paper_2307_07999_gb300.profile_driver batch              # one graph run of the 64-event batch
   python -m paper_2307_07999_gb300.profile_driver batch8             # 8 events of 384^2, 10k charm each
+    (both batch workloads tune the field tile shape first: 8 variants x 5 field launches;
+     a last argument v=<k> sets field tile variant k instead, without tuning)
   python -m paper_2307_07999_gb300.profile_driver ic 1024            # tau = 0+ solve: cold, then warm start
 """
 import sys
@@ -20,6 +22,11 @@ def main(argv):
         evs, pps = W.batched_uneven() if what == "batch" else W.batched_uneven(n_events=8, sizes=(384,))
         B = Batch(evs, pps)
         B.init()
+        fixed = [a for a in argv[2:] if a.startswith("v=")]
+        if fixed:
+            B.set_variant(int(fixed[0][2:]))
+        else:
+            B.tune(steps=4)  # the tile shape bench.py would run (8 variants x 5 launches first)
         B.run("graph")
         torch.cuda.synchronize()
         print("ok")
