@@ -361,6 +361,8 @@ def run_ours(args, ws, rank, local):
             "particle_steps_per_s": pvalue,
             "config": {"workload": WORKLOAD, "mode": mode,
                        "field_tile": f"{tile[0]}x{tile[1]}, {tile[2]} CTAs/SM (autotuned)",
+                       "push_kernel": ("fields staged in shared memory (32-thread blocks)" if B.push_variant == 1
+                                       else "fields through L1 (128-thread blocks)") + " (autotuned)",
                        "tile_tuning_ms_per_8_steps": {f"{a}x{b}/{c}": round(t, 3) for (a, b, c), t in zip(shapes, tile_ms)},
                        "site_updates_per_step": su,
                        "particle_steps_per_step": ps, "l2": "inputs larger than L2 (3.5 GB of field state)",

@@ -308,6 +308,14 @@ glasma_status glasma_field_tile_shape(int32_t precision, int32_t variant, int32_
 int32_t glasma_batch_variant(const glasma_batch* b);
 glasma_status glasma_batch_set_variant(glasma_batch* b, int32_t variant);
 glasma_status glasma_batch_tune(glasma_batch* b, int32_t steps, int32_t* chosen, double* ms);
+/* Batched push kernels (graph and eager modes): 0 reads the fields through L1 (128-thread
+ * blocks), 1 stages each particle's fields in shared memory first (cp.async).  Same
+ * arithmetic (results equal to FP32 rounding: the two kernels may contract
+ * multiply-adds differently).  glasma_batch_tune also times them, over `steps`
+ * iterations after the particles of every event are formed, and keeps the faster. */
+int32_t glasma_push_variants(void);
+int32_t glasma_batch_push_variant(const glasma_batch* b);
+glasma_status glasma_batch_set_push_variant(glasma_batch* b, int32_t variant);
 void glasma_batch_destroy(glasma_batch* b);
 
 const char* glasma_last_error(void);

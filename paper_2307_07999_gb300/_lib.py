@@ -107,6 +107,9 @@ SIGNATURES = {
     "glasma_batch_variant": (_i32, [_p]),
     "glasma_batch_set_variant": (C.c_int, [_p, _i32]),
     "glasma_batch_tune": (C.c_int, [_p, _i32, C.POINTER(_i32), C.POINTER(_d)]),
+    "glasma_push_variants": (_i32, []),
+    "glasma_batch_push_variant": (_i32, [_p]),
+    "glasma_batch_set_push_variant": (C.c_int, [_p, _i32]),
     "glasma_batch_get_particles": (C.c_int, [_p, _i32] + [_p] * 7),
     "glasma_batch_destroy": (None, [_p]),
     "glasma_diagnostics_noalloc": (C.c_int, [_p, _i32, _i32, _i32, _d, _p, _p]),

@@ -339,9 +339,17 @@ class Batch:
     def set_variant(self, v):
         check(lib().glasma_batch_set_variant(self.handle, v))
 
+    @property
+    def push_variant(self):
+        return lib().glasma_batch_push_variant(self.handle)
+
+    def set_push_variant(self, v):
+        check(lib().glasma_batch_set_push_variant(self.handle, v))
+
     def tune(self, steps=8):
-        """glasma_batch_tune: time every field tile variant, keep the fastest.
-        Returns (chosen variant, [ms per variant])."""
+        """glasma_batch_tune: time every field tile variant and every push kernel, keep the
+        fastest of each.  Returns (chosen field variant, [ms per field variant]); the push
+        kernel chosen is `push_variant`."""
         nv = lib().glasma_field_tile_variants(self.ev[0].precision)
         ms = (C.c_double * nv)()
         ch = C.c_int32()

@@ -398,7 +398,7 @@ static cudaError_t enqueue_batched(glasma_batch* b) {
         e = launch_field_step_variant(b->prec, b->fvar, (char*)b->step_args + (size_t)k * b->E * sa, b->gtiles_dev,
                                       b->gtiles_upto[act], b->st);
         if (e != cudaSuccess) return e;
-        e = launch_push_batched(b->prec, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
+        e = launch_push_batched(b->prec, b->pvar, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
                                 b->pitems_upto[act], b->st);
         if (e != cudaSuccess) return e;
     }
@@ -588,7 +588,7 @@ extern "C" glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, dou
             BCK(launch_rebin(b->bins_dev, b->pitems_dev, b->pitems_upto[act], b->tiles_upto[act], b->bin_count,
                              b->bin_fill, b->bin_start, b->bin_totals, b->bin_perm, b->st));
         else
-            BCK(launch_push_batched(b->prec, pargs, b->pitems_dev, b->pitems_upto[act], b->st));
+            BCK(launch_push_batched(b->prec, b->pvar, pargs, b->pitems_dev, b->pitems_upto[act], b->st));
         BCK(cudaEventRecord(ev[4 * k + 3], b->st));
         used = k + 1;
     }
@@ -634,14 +634,29 @@ extern "C" glasma_status glasma_batch_set_variant(glasma_batch* b, int32_t v) {
     }
     return build_gtiles(b);
 }
+extern "C" int32_t glasma_push_variants(void) { return push_variants(); }
+extern "C" int32_t glasma_batch_push_variant(const glasma_batch* b) { return b ? b->pvar : GLASMA_ERR_INVALID; }
+extern "C" glasma_status glasma_batch_set_push_variant(glasma_batch* b, int32_t v) {
+    if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    if (v < 0 || v >= push_variants()) return bfail(GLASMA_ERR_INVALID, "no such push variant");
+    if (v == b->pvar) return GLASMA_OK;
+    b->pvar = v;
+    if (b->graph_unfused_ready) {
+        cudaGraphExecDestroy(b->exec_unfused);
+        b->graph_unfused_ready = false;
+    }
+    return GLASMA_OK;
+}
 // times the batched field kernel of every variant over the first `steps` iterations
-// (from the initial state, one untimed warm-up iteration first) and keeps the fastest
+// (from the initial state, one untimed warm-up iteration first) and keeps the fastest;
+// then times every push kernel over `steps` iterations starting where the particles of
+// every event are formed, and keeps the fastest
 extern "C" glasma_status glasma_batch_tune(glasma_batch* b, int32_t steps, int32_t* chosen, double* ms) {
     if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
     if (steps < 1) return bfail(GLASMA_ERR_INVALID, "steps must be positive");
     const int nv = field_variants(b->prec);
     const int K = std::min<int>(steps + 1, b->max_iter);
-    const size_t sa = step_args_size(b->prec);
+    const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
@@ -665,10 +680,43 @@ extern "C" glasma_status glasma_batch_tune(glasma_batch* b, int32_t steps, int32
         if (ms) ms[v] = t;
         if (t < best_ms) { best_ms = t; best = v; }
     }
+    if (chosen) *chosen = best;
+    glasma_status s = glasma_batch_set_variant(b, best);
+    if (s != GLASMA_OK) return s;
+    // push kernels: the window of `steps` iterations after the latest formation step
+    int k0 = 0;
+    for (const auto& x : b->ev) k0 = std::max(k0, x.n_form - 1);
+    k0 = std::min(k0, std::max(0, b->max_iter - steps));
+    const int k1 = std::min(b->max_iter, k0 + steps);
+    int pbest = 0;
+    double pbest_ms = 1e300;
+    std::vector<cudaEvent_t> ev(2 * (size_t)std::max(1, k1 - k0));
+    for (auto& x : ev) BCK(cudaEventCreate(&x));
+    for (int v = 0; v < push_variants(); v++) {
+        BCK(enqueue_restore(b));
+        for (int k = 0; k < k1; k++) {
+            const int act = b->active[k];
+            if (act == 0) break;
+            BCK(launch_field_step_variant(b->prec, b->fvar, (char*)b->step_args + (size_t)k * b->E * sa,
+                                          b->gtiles_dev, b->gtiles_upto[act], b->st));
+            if (k >= k0) BCK(cudaEventRecord(ev[2 * (k - k0)], b->st));
+            BCK(launch_push_batched(b->prec, v, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
+                                    b->pitems_upto[act], b->st));
+            if (k >= k0) BCK(cudaEventRecord(ev[2 * (k - k0) + 1], b->st));
+        }
+        BCK(cudaStreamSynchronize(b->st));
+        double t = 0;
+        for (int k = k0; k < k1 && b->active[k]; k++) {
+            float a = 0;
+            BCK(cudaEventElapsedTime(&a, ev[2 * (k - k0)], ev[2 * (k - k0) + 1]));
+            t += a;
+        }
+        if (t < pbest_ms) { pbest_ms = t; pbest = v; }
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (chosen) *chosen = best;
-    return glasma_batch_set_variant(b, best);
+    return glasma_batch_set_push_variant(b, pbest);
 }
 
 // particles of event i after a run, original order (host arrays of n_particles; NULL skips)

@@ -39,6 +39,7 @@ struct glasma_batch {
     void* tiles_dev = nullptr;    // TileItem list, grouped by event (fused and persistent paths)
     void* gtiles_dev = nullptr;   // TileItem list of the chosen field variant (graph and eager paths)
     int fvar = 0;                 // FP32 field tile variant of the graph and eager paths
+    int pvar = 0;                 // batched push kernel of the graph and eager paths
     void* pitems_dev = nullptr;   // PushItem list, grouped by event
     void* scratch = nullptr;      // initial-condition / sort scratch
     std::vector<int> tiles_upto, gtiles_upto, pitems_upto, active;

@@ -66,7 +66,9 @@ cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStre
 // batched push: args[n_ev] (acc == nullptr: event idle this step), items {ev, j0} of 256 particles
 size_t push_args_size(int prec);
 void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out);
-cudaError_t launch_push_batched(int prec, const void* args_dev, const void* items_dev, int n_items, cudaStream_t st);
+int push_variants();
+cudaError_t launch_push_batched(int prec, int variant, const void* args_dev, const void* items_dev, int n_items,
+                                cudaStream_t st);
 struct PushItemH { int ev, j0; };
 struct TileItemH { int ev, x0, y0; };
 // fused field step + push (one CTA per tile; particles listed per tile by perm/start/count)

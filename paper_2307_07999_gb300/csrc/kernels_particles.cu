@@ -46,6 +46,10 @@ void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out) {
     if (prec) *(PushArgs<float>*)out = push_args<float>(a, P);
     else *(PushArgs<double>*)out = push_args<double>(a, P);
 }
+// Batched push kernels, chosen per batch by measurement (glasma_batch_tune):
+//   0: 128-thread blocks, 3 per SM, fields read through L1
+//   1: 32-thread blocks, 6 per SM, each particle's fields staged in shared memory first
+int push_variants() { return 2; }
 // shared-memory limit of the staged push (call outside stream capture)
 cudaError_t prepare_push_staged() {
     static bool done = false;
@@ -58,17 +62,21 @@ cudaError_t prepare_push_staged() {
     if (e == cudaSuccess) done = true;
     return e;
 }
-// batched push of one step: the staged kernel (one 256-particle item per 256 / PUSH_PPB blocks)
-cudaError_t launch_push_batched(int prec, const void* args, const void* items, int n_items, cudaStream_t st) {
-    if (n_items <= 0) return cudaSuccess;
-    const unsigned nb = (unsigned)n_items * (256 / PUSH_PPB);
-    if (prec)
-        k_push_staged<float><<<nb, PUSH_PPB, push_staged_smem<float>(), st>>>((const PushArgs<float>*)args,
-                                                                            (const PushItem*)items);
+template <class T>
+static cudaError_t push_batched_impl(int v, const void* args, const void* items, int n_items, cudaStream_t st) {
+    const PushArgs<T>* a = (const PushArgs<T>*)args;
+    const PushItem* it = (const PushItem*)items;
+    if (v == 1)
+        k_push_staged<T><<<(unsigned)n_items * (256 / PUSH_PPB), PUSH_PPB, push_staged_smem<T>(), st>>>(a, it);
     else
-        k_push_staged<double><<<nb, PUSH_PPB, push_staged_smem<double>(), st>>>((const PushArgs<double>*)args,
-                                                                              (const PushItem*)items);
+        k_push_batched<T, 128, 3><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
     return cudaGetLastError();
+}
+cudaError_t launch_push_batched(int prec, int v, const void* args, const void* items, int n_items, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    if (v < 0 || v >= push_variants()) return cudaErrorInvalidValue;
+    return prec ? push_batched_impl<float>(v, args, items, n_items, st)
+                : push_batched_impl<double>(v, args, items, n_items, st);
 }
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st) {
     if (a.np <= 0) return cudaSuccess;

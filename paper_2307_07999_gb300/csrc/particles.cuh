@@ -188,59 +188,28 @@ template <class T> struct StagedSrc {
 // qE = Q.(E_x, E_y, E_z), qB = Q.(B_x, B_y, B_z)
 template <class T, class V>
 DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
+    // Every field is read from the view where it is used and contracted with Q at once
+    // (Q.X is linear in X), so that few 3x3 matrices are live at a time.
     const T half = T(0.5);
-    // cells whose two links are both used load them together (three sectors in FP32)
-    M3<T> ux_c, uy_c, ux_xm, uy_xm, ux_ym, uy_ym;
-    C.links(0, 0, ux_c, uy_c);
-    C.links(-1, 0, ux_xm, uy_xm);
-    C.links(0, -1, ux_ym, uy_ym);
     // electric: the two links touching c, time-centred, transported to c
-    {
-        const Al<T> t = transport_alg(ux_xm, C.eavg(0, -1, 0));
-        qE[0] = half * (dot8(q, C.eavg(0, 0, 0)) + dot8(q, t)) / te;
-    }
-    {
-        const Al<T> t = transport_alg(uy_ym, C.eavg(1, 0, -1));
-        qE[1] = half * (dot8(q, C.eavg(1, 0, 0)) + dot8(q, t)) / te;
-    }
+    qE[0] = half * (dot8(q, C.eavg(0, 0, 0)) + dot8(q, transport_alg(C.link(0, -1, 0), C.eavg(0, -1, 0)))) / te;
+    qE[1] = half * (dot8(q, C.eavg(1, 0, 0)) + dot8(q, transport_alg(C.link(1, 0, -1), C.eavg(1, 0, -1)))) / te;
     qE[2] = dot8(q, C.piavg());
     // magnetic from phi: covariant central differences
-    {
-        const Al<T> fw = conj_alg(ux_c, C.phi(1, 0));
-        const Al<T> bw = transport_alg(ux_xm, C.phi(-1, 0));
-        qB[1] = half * (dot8(q, fw) - dot8(q, bw)) / te;    // B_y = +D_x phi / tau
-    }
-    {
-        const Al<T> fw = conj_alg(uy_c, C.phi(0, 1));
-        const Al<T> bw = transport_alg(uy_ym, C.phi(0, -1));
-        qB[0] = -half * (dot8(q, fw) - dot8(q, bw)) / te;   // B_x = -D_y phi / tau
-    }
+    // B_y = +D_x phi / tau,  B_x = -D_y phi / tau
+    qB[1] = half * (dot8(q, conj_alg(C.link(0, 0, 0), C.phi(1, 0))) -
+                    dot8(q, transport_alg(C.link(0, -1, 0), C.phi(-1, 0)))) / te;
+    qB[0] = -half * (dot8(q, conj_alg(C.link(1, 0, 0), C.phi(0, 1))) -
+                     dot8(q, transport_alg(C.link(1, 0, -1), C.phi(0, -1)))) / te;
     // B_z = -F_xy, F_xy = clover average of the four plaquettes based at c
-    {
-        Al<T> acc = im_tl(mul_nd(mul(ux_c, C.link(1, 1, 0)), mul(uy_c, C.link(0, 0, 1))));  // +x,+y
-        {   // +y,-x: U_y(c) [U_y(c-x) U_x(c-x+y)]^dag U_x(c-x)
-            const M3<T> B = mul(uy_xm, C.link(0, -1, 1));
-            const Al<T> t = im_tl(mul(mul_nd(uy_c, B), ux_xm));
-#pragma unroll
-            for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
-        }
-        {   // -x,-y: [U_y(c-x-y) U_x(c-x)]^dag [U_x(c-x-y) U_y(c-y)]
-            M3<T> ux_xmym, uy_xmym;
-            C.links(-1, -1, ux_xmym, uy_xmym);
-            const M3<T> B1 = mul(uy_xmym, ux_xm);
-            const M3<T> B2 = mul(ux_xmym, uy_ym);
-            const Al<T> t = im_tl(mul_dn(B1, B2));
-#pragma unroll
-            for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
-        }
-        {   // -y,+x: U_y(c-y)^dag [U_x(c-y) U_y(c+x-y)] U_x(c)^dag
-            const M3<T> B = mul(ux_ym, C.link(1, 1, -1));
-            const Al<T> t = im_tl(mul_nd(mul_dn(uy_ym, B), ux_c));
-#pragma unroll
-            for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
-        }
-        qB[2] = -T(0.25) * dot8(q, acc);
-    }
+    T bz = dot8(q, im_tl(mul_nd(mul(C.link(0, 0, 0), C.link(1, 1, 0)), mul(C.link(1, 0, 0), C.link(0, 0, 1)))));
+    // +y,-x: U_y(c) [U_y(c-x) U_x(c-x+y)]^dag U_x(c-x)
+    bz += dot8(q, im_tl(mul(mul_nd(C.link(1, 0, 0), mul(C.link(1, -1, 0), C.link(0, -1, 1))), C.link(0, -1, 0))));
+    // -x,-y: [U_y(c-x-y) U_x(c-x)]^dag [U_x(c-x-y) U_y(c-y)]
+    bz += dot8(q, im_tl(mul_dn(mul(C.link(1, -1, -1), C.link(0, -1, 0)), mul(C.link(0, -1, -1), C.link(1, 0, -1)))));
+    // -y,+x: U_y(c-y)^dag [U_x(c-y) U_y(c+x-y)] U_x(c)^dag
+    bz += dot8(q, im_tl(mul_nd(mul_dn(C.link(1, 0, -1), mul(C.link(0, 0, -1), C.link(1, 1, -1))), C.link(0, 0, 0))));
+    qB[2] = -T(0.25) * bz;
 }
 
 // one particle: gather, kick, drift, color transport; returns its broadening terms
@@ -362,25 +331,19 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<T> A) {
     block_acc4(sx, sy, sz, sc, A.acc);
 }
 
-// batched over events: one item per 256 particles of an event, pushed by
-// 256 / PUSH_THREADS blocks; args[ev] of this step (acc == nullptr marks an event
-// whose particles are not pushed at this step)
-#ifndef GLASMA_PUSH_THREADS
-#define GLASMA_PUSH_THREADS 256
-#endif
-#ifndef GLASMA_PUSH_MINB
-#define GLASMA_PUSH_MINB 1
-#endif
-constexpr int PUSH_THREADS = GLASMA_PUSH_THREADS, PUSH_SUB = 256 / GLASMA_PUSH_THREADS;
-static_assert(256 % GLASMA_PUSH_THREADS == 0 && GLASMA_PUSH_THREADS % 32 == 0, "push block");
+// batched over events: one item per 256 particles of an event, pushed by 256 / NT blocks
+// of NT threads; args[ev] of this step (acc == nullptr marks an event whose particles
+// are not pushed at this step)
 struct PushItem { int ev, j0; };
-template <class T>
-__global__ void __launch_bounds__(GLASMA_PUSH_THREADS, GLASMA_PUSH_MINB)
-k_push_batched(const PushArgs<T>* __restrict__ args, const PushItem* __restrict__ items) {
-    const PushItem it = items[blockIdx.x / PUSH_SUB];
+template <class T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_push_batched(const PushArgs<T>* __restrict__ args,
+                                                           const PushItem* __restrict__ items) {
+    static_assert(256 % NT == 0 && NT % 32 == 0, "push block");
+    constexpr int SUB = 256 / NT;
+    const PushItem it = items[blockIdx.x / SUB];
     const PushArgs<T> A = args[it.ev];
     if (A.acc == nullptr) return;
-    const int j = it.j0 + (int)(blockIdx.x % PUSH_SUB) * PUSH_THREADS + threadIdx.x;
+    const int j = it.j0 + (int)(blockIdx.x % SUB) * NT + threadIdx.x;
     double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
     if (j < A.np) push_one(A, j, sx, sy, sz, sc);
     block_acc4(sx, sy, sz, sc, A.acc);
@@ -420,18 +383,12 @@ DEV void cp_async16(void* smem_dst, const void* gsrc) {
 }
 DEV void cp_async_wait_all() { asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory"); }
 
-#ifndef GLASMA_PUSH_PPB
-#define GLASMA_PUSH_PPB 32
-#endif
-#ifndef GLASMA_PUSH_PPB_MINB
-#define GLASMA_PUSH_PPB_MINB 6
-#endif
-constexpr int PUSH_PPB = GLASMA_PUSH_PPB;
+constexpr int PUSH_PPB = 32;  // particles (threads) per block of the staged push; 6 blocks per SM
 static_assert(256 % PUSH_PPB == 0 && PUSH_PPB % 32 == 0, "staged push block");
 template <class T> constexpr size_t push_staged_smem() { return (size_t)PUSH_PPB * StagedSrc<T>::STRIDE * sizeof(T); }
 
 template <class T>
-__global__ void __launch_bounds__(GLASMA_PUSH_PPB, GLASMA_PUSH_PPB_MINB)
+__global__ void __launch_bounds__(PUSH_PPB, 6)
 k_push_staged(const PushArgs<T>* __restrict__ args, const PushItem* __restrict__ items) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int SUB = 256 / PUSH_PPB;
