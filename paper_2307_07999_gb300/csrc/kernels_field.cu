@@ -114,7 +114,8 @@ struct FieldVariant {
 };
 #define GL_FV(TX, TY, MB) {TX, TY, MB, (const void*)k_field_step_tiles<TX, TY, MB>, RecTile<float, TX, TY>::smem}
 static const FieldVariant g_fvar[] = {GL_FV(32, 4, 3), GL_FV(16, 8, 3), GL_FV(8, 16, 3), GL_FV(32, 6, 2),
-                                      GL_FV(16, 12, 2), GL_FV(32, 8, 2), GL_FV(32, 4, 4), GL_FV(16, 8, 4)};
+                                      GL_FV(16, 12, 2), GL_FV(32, 8, 2), GL_FV(32, 4, 4), GL_FV(16, 8, 4),
+                                      GL_FV(8, 8, 8), GL_FV(8, 16, 4), GL_FV(16, 16, 2)};
 #undef GL_FV
 static constexpr int N_FVAR = (int)(sizeof(g_fvar) / sizeof(g_fvar[0]));
 
