@@ -67,6 +67,7 @@ def _declare(L):
         "o_particles_init": (None, [_i, _i, _d, _i, _d, _d, _d, _d, _u64] + [_p] * 7),
         "o_q0_cartan": (None, [_d, _d, _p]),
         "o_gather": (None, [_i, _d, _i, _p, _p, _p, _p, _p, _p, _i, _i, _p]),
+        "o_corr_step": (None, [_i, _i, _d, _i] + [_p] * 9 + [_i, _i, _p]),
         "o_push": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p]),
         "o_casimirs": (None, [_p, _p, _p]),
         "o_pz_lab": (_d, [_d, _d, _d, _d, _d]),
@@ -388,6 +389,32 @@ def gather(old, new, cx, cy, dtau, expanding=1):
     lib().o_gather(old.n, tau, expanding, _ptr(old.U), _ptr(old.E), _ptr(new.E), _ptr(old.phi),
                    _ptr(old.pi), _ptr(new.pi), cx, cy, _ptr(F))
     return F
+
+
+class Correlators:
+    """Running static (Eq. 4) and lightlike (Eq. 5) estimators of one event (correlators.c),
+    started at the step of the first call; the lightlike paths start at offset ox0 in
+    their cells."""
+
+    def __init__(self, n, ox0=0.5):
+        self.n, self.ox0, self.m = n, ox0, 0
+        self.Istat = rz(n * n, 3, 8)
+        self.W = np.ascontiguousarray(np.broadcast_to(np.eye(3, dtype=np.complex128), (n * n, 3, 3)))
+        self.J = rz(n * n, 3, 8)
+
+    def crossings(self, m, dtau):
+        return int(np.floor(self.ox0 + m * dtau))
+
+    def step(self, old, new, dtau, expanding=1):
+        """One step (old: the fields of step n, new: of step n+1); returns the static
+        <dp_x^2>, <dp_y^2>, <dp_z^2> and the lightlike ones, in lattice units."""
+        out = rz(6)
+        k0, k1 = self.crossings(self.m, dtau), self.crossings(self.m + 1, dtau)
+        lib().o_corr_step(self.n, expanding, dtau, old.step, _ptr(old.U), _ptr(old.E), _ptr(new.E), _ptr(old.phi),
+                          _ptr(old.pi), _ptr(new.pi), _ptr(self.Istat), _ptr(self.W), _ptr(self.J), k0, k1,
+                          _ptr(out))
+        self.m += 1
+        return out
 
 
 def push(P, old, new, dtau, mass, expanding=1):

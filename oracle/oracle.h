@@ -106,6 +106,13 @@ void o_push(int np, int n, int expanding, double dtau, int step, double mass,
 void o_casimirs(const double Q[8], double *q2, double *q3);
 double o_pz_lab(double mass, double px, double py, double peta, double eta);
 
+/* ---------------- correlators.c : Eqs. 4 and 5 ---------------- */
+/* one step of the static (Istat[s][3][8]) and lightlike (W[s][9], J[s][3][8])
+ * estimators; out = {<dp_x^2>, <dp_y^2>, <dp_z^2>} static, then lightlike */
+void o_corr_step(int n, int expanding, double dtau, int step, const cplx *U, const double *Eo,
+                 const double *En, const double *phi, const double *pio, const double *pin,
+                 double *Istat, cplx *W, double *J, int k_now, int k_next, double out[6]);
+
 /* ---------------- mlp.c : learned warm-start network ---------------- */
 void o_mlp_forward(int batch, const double *x, const double *W1, const double *b1,
                    const double *W2, const double *b2, const double *W3,

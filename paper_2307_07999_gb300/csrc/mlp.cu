@@ -114,246 +114,246 @@ __global__ void __launch_bounds__(128) k_mlp(MlpDev m, const float* __restrict__
     }
     const int ntiles = (N + MROWS - 1) / MROWS;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    __syncthreads();  // weights in place; the previous tile's inputs consumed
-    {
-        // input rows (scaled, BF16, zero padded)
-        const int r0 = tile * MROWS;
-        for (int i = tid; i < MROWS * MK1; i += 128) {
-            const int r = i / MK1, k = i % MK1;
-            const float v = (r0 + r < N && k < MI) ? X[(size_t)(r0 + r) * MI + k] * m.x_inv : 0.0f;
-            S.x[i] = __float2bfloat16_rn(v);
-        }
-    }
-    __syncthreads();
-    const int rw = warp * 16;  // this warp's rows within the CTA
-    const int row0 = tile * MROWS + rw;
-    // ---- layer 1
-    float c1[16][4];
-#pragma unroll
-    for (int nt = 0; nt < 16; nt++) {
-        const float b0 = S.b1[nt * 8 + 2 * t], b1v = S.b1[nt * 8 + 2 * t + 1];
-        c1[nt][0] = b0; c1[nt][1] = b1v; c1[nt][2] = b0; c1[nt][3] = b1v;
-    }
-#pragma unroll
-    for (int kt = 0; kt < MK1 / 16; kt++) {
-        uint32_t a[4];
-        const __nv_bfloat16* xr = S.x + (rw + g) * MK1 + kt * 16 + 2 * t;
-        a[0] = *reinterpret_cast<const uint32_t*>(xr);
-        a[1] = *reinterpret_cast<const uint32_t*>(xr + 8 * MK1);
-        a[2] = *reinterpret_cast<const uint32_t*>(xr + 8);
-        a[3] = *reinterpret_cast<const uint32_t*>(xr + 8 * MK1 + 8);
-#pragma unroll
-        for (int nt = 0; nt < 16; nt++) {
-            uint32_t b0, b1;
-            bfrag(S.w1, MK1, nt, kt, g, t, b0, b1);
-            mma_bf16(c1[nt], a, b0, b1);
-        }
-    }
-#pragma unroll
-    for (int nt = 0; nt < 16; nt++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) c1[nt][q] = tanhf(c1[nt][q]);
-    if constexpr (TRAIN) {
-#pragma unroll
-        for (int nt = 0; nt < 16; nt++) {
-            const int col = nt * 8 + 2 * t;
-            *reinterpret_cast<uint32_t*>(S.h1 + (rw + g) * MH + col) = pack_bf16(c1[nt][0], c1[nt][1]);
-            *reinterpret_cast<uint32_t*>(S.h1 + (rw + g + 8) * MH + col) = pack_bf16(c1[nt][2], c1[nt][3]);
-        }
-    }
-    // ---- layer 2
-    float c2[16][4];
-#pragma unroll
-    for (int nt = 0; nt < 16; nt++) {
-        const float b0 = S.b2[nt * 8 + 2 * t], b1v = S.b2[nt * 8 + 2 * t + 1];
-        c2[nt][0] = b0; c2[nt][1] = b1v; c2[nt][2] = b0; c2[nt][3] = b1v;
-    }
-#pragma unroll
-    for (int kt = 0; kt < MH / 16; kt++) {
-        uint32_t a[4];
-        afrag_from_acc(c1[2 * kt], c1[2 * kt + 1], a);
-#pragma unroll
-        for (int nt = 0; nt < 16; nt++) {
-            uint32_t b0, b1;
-            bfrag(S.w2, MH, nt, kt, g, t, b0, b1);
-            mma_bf16(c2[nt], a, b0, b1);
-        }
-    }
-#pragma unroll
-    for (int nt = 0; nt < 16; nt++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) c2[nt][q] = tanhf(c2[nt][q]);
-    if constexpr (TRAIN) {
-#pragma unroll
-        for (int nt = 0; nt < 16; nt++) {
-            const int col = nt * 8 + 2 * t;
-            *reinterpret_cast<uint32_t*>(S.h2 + (rw + g) * MH + col) = pack_bf16(c2[nt][0], c2[nt][1]);
-            *reinterpret_cast<uint32_t*>(S.h2 + (rw + g + 8) * MH + col) = pack_bf16(c2[nt][2], c2[nt][3]);
-        }
-    }
-    // ---- layer 3
-    float c3[2][4];
-#pragma unroll
-    for (int nt = 0; nt < 2; nt++) {
-        const float b0 = S.b3[nt * 8 + 2 * t], b1v = S.b3[nt * 8 + 2 * t + 1];
-        c3[nt][0] = b0; c3[nt][1] = b1v; c3[nt][2] = b0; c3[nt][3] = b1v;
-    }
-#pragma unroll
-    for (int kt = 0; kt < MH / 16; kt++) {
-        uint32_t a[4];
-        afrag_from_acc(c2[2 * kt], c2[2 * kt + 1], a);
-#pragma unroll
-        for (int nt = 0; nt < 2; nt++) {
-            uint32_t b0, b1;
-            bfrag(S.w3, MH, nt, kt, g, t, b0, b1);
-            mma_bf16(c3[nt], a, b0, b1);
-        }
-    }
-    const int ra = row0 + g, rb = row0 + g + 8;
-    if constexpr (!TRAIN) {
-        // outputs 0..7 (n-tile 0): delta = y * y_scale
-        if (ra < N) {
-            Y[(size_t)ra * 8 + 2 * t] = c3[0][0] * m.y_scale;
-            Y[(size_t)ra * 8 + 2 * t + 1] = c3[0][1] * m.y_scale;
-        }
-        if (rb < N) {
-            Y[(size_t)rb * 8 + 2 * t] = c3[0][2] * m.y_scale;
-            Y[(size_t)rb * 8 + 2 * t + 1] = c3[0][3] * m.y_scale;
-        }
-    } else {
-    // ---- loss and dY = 2 (y - target) / (N * 16); targets of outputs 8..15 are 0
-    const float norm = 2.0f / ((float)N * MO);
-    double lsum = 0.0;
-    float dyf[2][4];
-#pragma unroll
-    for (int nt = 0; nt < 2; nt++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int r = (q < 2) ? ra : rb;
-            const int col = nt * 8 + 2 * t + (q & 1);
-            float d = 0.0f;
-            if (r < N) {
-                const float tg = (nt == 0) ? Tg[(size_t)r * 8 + col] / m.y_scale : 0.0f;
-                const float e = c3[nt][q] - tg;
-                lsum += (double)e * e;
-                d = norm * e;
+        __syncthreads();  // weights in place; the previous tile's inputs consumed
+        {
+            // input rows (scaled, BF16, zero padded)
+            const int r0 = tile * MROWS;
+            for (int i = tid; i < MROWS * MK1; i += 128) {
+                const int r = i / MK1, k = i % MK1;
+                const float v = (r0 + r < N && k < MI) ? X[(size_t)(r0 + r) * MI + k] * m.x_inv : 0.0f;
+                S.x[i] = __float2bfloat16_rn(v);
             }
-            dyf[nt][q] = d;
-            S.dy[(rw + g + ((q < 2) ? 0 : 8)) * MO + col] = d;
         }
-    // dH2 = (dY W3) * (1 - h2^2)
-    {
-        float d2[16][4];
-        uint32_t a[4];
-        afrag_from_acc(dyf[0], dyf[1], a);
+        __syncthreads();
+        const int rw = warp * 16;  // this warp's rows within the CTA
+        const int row0 = tile * MROWS + rw;
+        // ---- layer 1
+        float c1[16][4];
 #pragma unroll
         for (int nt = 0; nt < 16; nt++) {
-            d2[nt][0] = d2[nt][1] = d2[nt][2] = d2[nt][3] = 0.0f;
-            uint32_t b0, b1;
-            bfrag(S.w3t, MO, nt, 0, g, t, b0, b1);
-            mma_bf16(d2[nt], a, b0, b1);
-#pragma unroll
-            for (int q = 0; q < 4; q++) d2[nt][q] *= 1.0f - c2[nt][q] * c2[nt][q];
-            const int col = nt * 8 + 2 * t;
-            *reinterpret_cast<uint32_t*>(S.d2 + (rw + g) * MH + col) = pack_bf16(d2[nt][0], d2[nt][1]);
-            *reinterpret_cast<uint32_t*>(S.d2 + (rw + g + 8) * MH + col) = pack_bf16(d2[nt][2], d2[nt][3]);
+            const float b0 = S.b1[nt * 8 + 2 * t], b1v = S.b1[nt * 8 + 2 * t + 1];
+            c1[nt][0] = b0; c1[nt][1] = b1v; c1[nt][2] = b0; c1[nt][3] = b1v;
         }
-    }
-    __syncwarp();  // this warp's rows of S.d2 are complete
-    // dH1 = (dH2 W2) * (1 - h1^2); dH2 operands and h1 come back from shared memory
-    {
-        float d1[16][4];
 #pragma unroll
-        for (int nt = 0; nt < 16; nt++) d1[nt][0] = d1[nt][1] = d1[nt][2] = d1[nt][3] = 0.0f;
-#pragma unroll
-        for (int kt = 0; kt < MH / 16; kt++) {
+        for (int kt = 0; kt < MK1 / 16; kt++) {
             uint32_t a[4];
-            const __nv_bfloat16* dr = S.d2 + (rw + g) * MH + kt * 16 + 2 * t;
-            a[0] = *reinterpret_cast<const uint32_t*>(dr);
-            a[1] = *reinterpret_cast<const uint32_t*>(dr + 8 * MH);
-            a[2] = *reinterpret_cast<const uint32_t*>(dr + 8);
-            a[3] = *reinterpret_cast<const uint32_t*>(dr + 8 * MH + 8);
+            const __nv_bfloat16* xr = S.x + (rw + g) * MK1 + kt * 16 + 2 * t;
+            a[0] = *reinterpret_cast<const uint32_t*>(xr);
+            a[1] = *reinterpret_cast<const uint32_t*>(xr + 8 * MK1);
+            a[2] = *reinterpret_cast<const uint32_t*>(xr + 8);
+            a[3] = *reinterpret_cast<const uint32_t*>(xr + 8 * MK1 + 8);
 #pragma unroll
             for (int nt = 0; nt < 16; nt++) {
                 uint32_t b0, b1;
-                bfrag(S.w2t, MH, nt, kt, g, t, b0, b1);
-                mma_bf16(d1[nt], a, b0, b1);
+                bfrag(S.w1, MK1, nt, kt, g, t, b0, b1);
+                mma_bf16(c1[nt], a, b0, b1);
             }
         }
+#pragma unroll
+        for (int nt = 0; nt < 16; nt++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) c1[nt][q] = tanhf(c1[nt][q]);
+        if constexpr (TRAIN) {
+#pragma unroll
+            for (int nt = 0; nt < 16; nt++) {
+                const int col = nt * 8 + 2 * t;
+                *reinterpret_cast<uint32_t*>(S.h1 + (rw + g) * MH + col) = pack_bf16(c1[nt][0], c1[nt][1]);
+                *reinterpret_cast<uint32_t*>(S.h1 + (rw + g + 8) * MH + col) = pack_bf16(c1[nt][2], c1[nt][3]);
+            }
+        }
+        // ---- layer 2
+        float c2[16][4];
 #pragma unroll
         for (int nt = 0; nt < 16; nt++) {
-            const int col = nt * 8 + 2 * t;
-            const float h00 = __bfloat162float(S.h1[(rw + g) * MH + col]);
-            const float h01 = __bfloat162float(S.h1[(rw + g) * MH + col + 1]);
-            const float h10 = __bfloat162float(S.h1[(rw + g + 8) * MH + col]);
-            const float h11 = __bfloat162float(S.h1[(rw + g + 8) * MH + col + 1]);
-            d1[nt][0] *= 1.0f - h00 * h00;
-            d1[nt][1] *= 1.0f - h01 * h01;
-            d1[nt][2] *= 1.0f - h10 * h10;
-            d1[nt][3] *= 1.0f - h11 * h11;
-            *reinterpret_cast<uint32_t*>(S.d1 + (rw + g) * MH + col) = pack_bf16(d1[nt][0], d1[nt][1]);
-            *reinterpret_cast<uint32_t*>(S.d1 + (rw + g + 8) * MH + col) = pack_bf16(d1[nt][2], d1[nt][3]);
+            const float b0 = S.b2[nt * 8 + 2 * t], b1v = S.b2[nt * 8 + 2 * t + 1];
+            c2[nt][0] = b0; c2[nt][1] = b1v; c2[nt][2] = b0; c2[nt][3] = b1v;
         }
-    }
-    // loss: warp sum -> one atomic per warp
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
-    if (lane == 0) atomicAdd(loss, lsum / ((double)N * MO));
-    __syncthreads();
-    // ---- weight gradients over this CTA's rows (FP32 accumulation from BF16 activations)
-    {
-        // W2 and b2: thread o = tid, columns in chunks of 32
-        const int o = tid;
-        float gb = 0.0f;
-        for (int r = 0; r < MROWS; r++) gb += __bfloat162float(S.d2[r * MH + o]);
-        atomicAdd(grad + O_B2 + o, gb);
-        for (int c0 = 0; c0 < MH; c0 += 32) {
-            float acc[32];
+        for (int kt = 0; kt < MH / 16; kt++) {
+            uint32_t a[4];
+            afrag_from_acc(c1[2 * kt], c1[2 * kt + 1], a);
 #pragma unroll
-            for (int i = 0; i < 32; i++) acc[i] = 0.0f;
-            for (int r = 0; r < MROWS; r++) {
-                const float d = __bfloat162float(S.d2[r * MH + o]);
-#pragma unroll
-                for (int i = 0; i < 32; i++) acc[i] = fmaf(d, __bfloat162float(S.h1[r * MH + c0 + i]), acc[i]);
+            for (int nt = 0; nt < 16; nt++) {
+                uint32_t b0, b1;
+                bfrag(S.w2, MH, nt, kt, g, t, b0, b1);
+                mma_bf16(c2[nt], a, b0, b1);
             }
-#pragma unroll
-            for (int i = 0; i < 32; i++) atomicAdd(grad + O_W2 + o * MH + c0 + i, acc[i]);
         }
-        // W1 and b1
-        {
-            float acc[MI];
-            float gb1 = 0.0f;
 #pragma unroll
-            for (int k = 0; k < MI; k++) acc[k] = 0.0f;
-            for (int r = 0; r < MROWS; r++) {
-                const float d = __bfloat162float(S.d1[r * MH + o]);
-                gb1 += d;
+        for (int nt = 0; nt < 16; nt++)
 #pragma unroll
-                for (int k = 0; k < MI; k++) acc[k] = fmaf(d, __bfloat162float(S.x[r * MK1 + k]), acc[k]);
+            for (int q = 0; q < 4; q++) c2[nt][q] = tanhf(c2[nt][q]);
+        if constexpr (TRAIN) {
+#pragma unroll
+            for (int nt = 0; nt < 16; nt++) {
+                const int col = nt * 8 + 2 * t;
+                *reinterpret_cast<uint32_t*>(S.h2 + (rw + g) * MH + col) = pack_bf16(c2[nt][0], c2[nt][1]);
+                *reinterpret_cast<uint32_t*>(S.h2 + (rw + g + 8) * MH + col) = pack_bf16(c2[nt][2], c2[nt][3]);
             }
-            atomicAdd(grad + O_B1 + o, gb1);
-#pragma unroll
-            for (int k = 0; k < MI; k++) atomicAdd(grad + O_W1 + o * MI + k, acc[k]);
         }
-        // W3 and b3: o3 = tid & 15, columns (tid >> 4) * 16 .. + 16
-        {
-            const int o3 = tid & 15, c0 = (tid >> 4) * 16;
-            float acc[16];
-            float gb3 = 0.0f;
+        // ---- layer 3
+        float c3[2][4];
 #pragma unroll
-            for (int i = 0; i < 16; i++) acc[i] = 0.0f;
-            for (int r = 0; r < MROWS; r++) {
-                const float d = S.dy[r * MO + o3];
-                gb3 += d;
+        for (int nt = 0; nt < 2; nt++) {
+            const float b0 = S.b3[nt * 8 + 2 * t], b1v = S.b3[nt * 8 + 2 * t + 1];
+            c3[nt][0] = b0; c3[nt][1] = b1v; c3[nt][2] = b0; c3[nt][3] = b1v;
+        }
 #pragma unroll
-                for (int i = 0; i < 16; i++) acc[i] = fmaf(d, __bfloat162float(S.h2[r * MH + c0 + i]), acc[i]);
+        for (int kt = 0; kt < MH / 16; kt++) {
+            uint32_t a[4];
+            afrag_from_acc(c2[2 * kt], c2[2 * kt + 1], a);
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+                uint32_t b0, b1;
+                bfrag(S.w3, MH, nt, kt, g, t, b0, b1);
+                mma_bf16(c3[nt], a, b0, b1);
             }
-            if (c0 == 0) atomicAdd(grad + O_B3 + o3, gb3);
-#pragma unroll
-            for (int i = 0; i < 16; i++) atomicAdd(grad + O_W3 + o3 * MH + c0 + i, acc[i]);
         }
-    }
-    }  // TRAIN
+        const int ra = row0 + g, rb = row0 + g + 8;
+        if constexpr (!TRAIN) {
+            // outputs 0..7 (n-tile 0): delta = y * y_scale
+            if (ra < N) {
+                Y[(size_t)ra * 8 + 2 * t] = c3[0][0] * m.y_scale;
+                Y[(size_t)ra * 8 + 2 * t + 1] = c3[0][1] * m.y_scale;
+            }
+            if (rb < N) {
+                Y[(size_t)rb * 8 + 2 * t] = c3[0][2] * m.y_scale;
+                Y[(size_t)rb * 8 + 2 * t + 1] = c3[0][3] * m.y_scale;
+            }
+        } else {
+            // ---- loss and dY = 2 (y - target) / (N * 16); targets of outputs 8..15 are 0
+            const float norm = 2.0f / ((float)N * MO);
+            double lsum = 0.0;
+            float dyf[2][4];
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int r = (q < 2) ? ra : rb;
+                    const int col = nt * 8 + 2 * t + (q & 1);
+                    float d = 0.0f;
+                    if (r < N) {
+                        const float tg = (nt == 0) ? Tg[(size_t)r * 8 + col] / m.y_scale : 0.0f;
+                        const float e = c3[nt][q] - tg;
+                        lsum += (double)e * e;
+                        d = norm * e;
+                    }
+                    dyf[nt][q] = d;
+                    S.dy[(rw + g + ((q < 2) ? 0 : 8)) * MO + col] = d;
+                }
+            // dH2 = (dY W3) * (1 - h2^2)
+            {
+                float d2[16][4];
+                uint32_t a[4];
+                afrag_from_acc(dyf[0], dyf[1], a);
+#pragma unroll
+                for (int nt = 0; nt < 16; nt++) {
+                    d2[nt][0] = d2[nt][1] = d2[nt][2] = d2[nt][3] = 0.0f;
+                    uint32_t b0, b1;
+                    bfrag(S.w3t, MO, nt, 0, g, t, b0, b1);
+                    mma_bf16(d2[nt], a, b0, b1);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) d2[nt][q] *= 1.0f - c2[nt][q] * c2[nt][q];
+                    const int col = nt * 8 + 2 * t;
+                    *reinterpret_cast<uint32_t*>(S.d2 + (rw + g) * MH + col) = pack_bf16(d2[nt][0], d2[nt][1]);
+                    *reinterpret_cast<uint32_t*>(S.d2 + (rw + g + 8) * MH + col) = pack_bf16(d2[nt][2], d2[nt][3]);
+                }
+            }
+            __syncwarp();  // this warp's rows of S.d2 are complete
+            // dH1 = (dH2 W2) * (1 - h1^2); dH2 operands and h1 come back from shared memory
+            {
+                float d1[16][4];
+#pragma unroll
+                for (int nt = 0; nt < 16; nt++) d1[nt][0] = d1[nt][1] = d1[nt][2] = d1[nt][3] = 0.0f;
+#pragma unroll
+                for (int kt = 0; kt < MH / 16; kt++) {
+                    uint32_t a[4];
+                    const __nv_bfloat16* dr = S.d2 + (rw + g) * MH + kt * 16 + 2 * t;
+                    a[0] = *reinterpret_cast<const uint32_t*>(dr);
+                    a[1] = *reinterpret_cast<const uint32_t*>(dr + 8 * MH);
+                    a[2] = *reinterpret_cast<const uint32_t*>(dr + 8);
+                    a[3] = *reinterpret_cast<const uint32_t*>(dr + 8 * MH + 8);
+#pragma unroll
+                    for (int nt = 0; nt < 16; nt++) {
+                        uint32_t b0, b1;
+                        bfrag(S.w2t, MH, nt, kt, g, t, b0, b1);
+                        mma_bf16(d1[nt], a, b0, b1);
+                    }
+                }
+#pragma unroll
+                for (int nt = 0; nt < 16; nt++) {
+                    const int col = nt * 8 + 2 * t;
+                    const float h00 = __bfloat162float(S.h1[(rw + g) * MH + col]);
+                    const float h01 = __bfloat162float(S.h1[(rw + g) * MH + col + 1]);
+                    const float h10 = __bfloat162float(S.h1[(rw + g + 8) * MH + col]);
+                    const float h11 = __bfloat162float(S.h1[(rw + g + 8) * MH + col + 1]);
+                    d1[nt][0] *= 1.0f - h00 * h00;
+                    d1[nt][1] *= 1.0f - h01 * h01;
+                    d1[nt][2] *= 1.0f - h10 * h10;
+                    d1[nt][3] *= 1.0f - h11 * h11;
+                    *reinterpret_cast<uint32_t*>(S.d1 + (rw + g) * MH + col) = pack_bf16(d1[nt][0], d1[nt][1]);
+                    *reinterpret_cast<uint32_t*>(S.d1 + (rw + g + 8) * MH + col) = pack_bf16(d1[nt][2], d1[nt][3]);
+                }
+            }
+            // loss: warp sum -> one atomic per warp
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+            if (lane == 0) atomicAdd(loss, lsum / ((double)N * MO));
+            __syncthreads();
+            // ---- weight gradients over this CTA's rows (FP32 accumulation from BF16 activations)
+            {
+                // W2 and b2: thread o = tid, columns in chunks of 32
+                const int o = tid;
+                float gb = 0.0f;
+                for (int r = 0; r < MROWS; r++) gb += __bfloat162float(S.d2[r * MH + o]);
+                atomicAdd(grad + O_B2 + o, gb);
+                for (int c0 = 0; c0 < MH; c0 += 32) {
+                    float acc[32];
+#pragma unroll
+                    for (int i = 0; i < 32; i++) acc[i] = 0.0f;
+                    for (int r = 0; r < MROWS; r++) {
+                        const float d = __bfloat162float(S.d2[r * MH + o]);
+#pragma unroll
+                        for (int i = 0; i < 32; i++) acc[i] = fmaf(d, __bfloat162float(S.h1[r * MH + c0 + i]), acc[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 32; i++) atomicAdd(grad + O_W2 + o * MH + c0 + i, acc[i]);
+                }
+                // W1 and b1
+                {
+                    float acc[MI];
+                    float gb1 = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < MI; k++) acc[k] = 0.0f;
+                    for (int r = 0; r < MROWS; r++) {
+                        const float d = __bfloat162float(S.d1[r * MH + o]);
+                        gb1 += d;
+#pragma unroll
+                        for (int k = 0; k < MI; k++) acc[k] = fmaf(d, __bfloat162float(S.x[r * MK1 + k]), acc[k]);
+                    }
+                    atomicAdd(grad + O_B1 + o, gb1);
+#pragma unroll
+                    for (int k = 0; k < MI; k++) atomicAdd(grad + O_W1 + o * MI + k, acc[k]);
+                }
+                // W3 and b3: o3 = tid & 15, columns (tid >> 4) * 16 .. + 16
+                {
+                    const int o3 = tid & 15, c0 = (tid >> 4) * 16;
+                    float acc[16];
+                    float gb3 = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 16; i++) acc[i] = 0.0f;
+                    for (int r = 0; r < MROWS; r++) {
+                        const float d = S.dy[r * MO + o3];
+                        gb3 += d;
+#pragma unroll
+                        for (int i = 0; i < 16; i++) acc[i] = fmaf(d, __bfloat162float(S.h2[r * MH + c0 + i]), acc[i]);
+                    }
+                    if (c0 == 0) atomicAdd(grad + O_B3 + o3, gb3);
+#pragma unroll
+                    for (int i = 0; i < 16; i++) atomicAdd(grad + O_W3 + o3 * MH + c0 + i, acc[i]);
+                }
+            }
+        }  // TRAIN
     }  // tiles
 }
 
