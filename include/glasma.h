@@ -84,8 +84,15 @@ typedef struct {
     uint64_t seed;           /* Philox key of positions, momenta and Haar rotations */
 } cpic_params;
 
+/* Lattice-correlator estimators (Sec. 2, "Lattice correlators", Eqs. 4 and 5). */
+typedef struct {
+    double tau_start_fm;     /* first step = round(tau_start / dtau) (as for particles formed then), >= 1 */
+    double ox0;              /* offset of the lightlike paths in their start cells, [0, 1) */
+} corr_params;
+
 typedef struct glasma_ctx glasma_ctx;
 typedef struct cpic_ctx cpic_ctx;
+typedef struct glasma_corr glasma_corr;
 typedef struct glasma_batch glasma_batch;
 typedef struct glasma_mlp glasma_mlp;
 
@@ -198,6 +205,30 @@ glasma_status broadening_accumulate(cpic_ctx* c, double* host_out, int64_t cap_r
 glasma_status cpic_casimir_drift(cpic_ctx* c, double out[2]);
 
 void cpic_destroy(cpic_ctx* c);
+
+/* ------------------------------------------------------------------ lattice correlators
+ * The momentum broadening of static quarks (m -> infinity, Eq. 4) and of lightlike jets
+ * along +x (p_x -> infinity, Eq. 5) from the Glasma fields alone, for every site:
+ *   static:    I_i(x) = sum over steps of dtau E_i(x),  <dp_i^2> = <Tr I_i^2>_x
+ *   lightlike: the path from x0 moves one lattice unit of x per unit of tau from offset
+ *              ox0; J_i(x0) = sum of dtau W F_i W^dag with F = (E_x, E_y - B_z, E_z + B_y)
+ *              at the path's cell and W the product of the x-links the path crossed;
+ *              <dp_i^2> = <Tr J_i^2>_x0
+ * with the site-centred fields of the particle push (time-centred E_x, E_y averaged over
+ * the two links at the site, E_z = pi, clover B_z, covariant differences of phi).  These
+ * are the Q-averaged limits of the Wong push (a charge Q parallel transported along the
+ * path collects Q.J).  The estimator attaches to a field context and advances with every
+ * field step of glasma_step and cpic_push from its first step; one per context.
+ * Workspace: caller-owned device memory, 256-byte aligned (66 reals per site in the
+ * context's precision, plus FP64 sums).  Destroy it before its context. */
+int64_t corr_workspace_bytes(const glasma_params* p);
+glasma_status corr_create(glasma_ctx* g, const corr_params* p, void* workspace, int64_t workspace_bytes,
+                          glasma_corr** out);
+/* host_out [rows][7] = {tau_fm, static <dp_x^2>, <dp_y^2>, <dp_z^2>, lightlike <dp_x^2>,
+ * <dp_y^2>, <dp_z^2>} in GeV^2, FP64, from the first step (zeros) to the current one.
+ * Synchronises. */
+glasma_status corr_table(glasma_corr* c, double* host_out, int64_t cap, int64_t* n_rows);
+void corr_destroy(glasma_corr* c);
 
 /* ------------------------------------------------------------------ learned warm start
  * A 36 -> 128 -> 128 -> 16 tanh network (BF16 weights, FP32 accumulation) that

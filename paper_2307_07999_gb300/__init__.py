@@ -19,6 +19,7 @@ from ._lib import (  # noqa: F401
 from .api import (  # noqa: F401
     CPIC,
     Batch,
+    Correlators,
     Glasma,
     HBARC,
     WarmStartNet,

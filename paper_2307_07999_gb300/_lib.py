@@ -49,6 +49,10 @@ class GlasmaParams(C.Structure):
     ]
 
 
+class CorrParams(C.Structure):
+    _fields_ = [("tau_start_fm", C.c_double), ("ox0", C.c_double)]
+
+
 class CpicParams(C.Structure):
     _fields_ = [
         ("n_particles", C.c_int32),
@@ -108,6 +112,10 @@ SIGNATURES = {
     "glasma_batch_set_variant": (C.c_int, [_p, _i32]),
     "glasma_batch_tune": (C.c_int, [_p, _i32, C.POINTER(_i32), C.POINTER(_d)]),
     "glasma_push_variants": (_i32, []),
+    "corr_workspace_bytes": (_i64, [_p]),
+    "corr_create": (C.c_int, [_p, _p, _p, _i64, C.POINTER(_p)]),
+    "corr_table": (C.c_int, [_p, _p, _i64, C.POINTER(_i64)]),
+    "corr_destroy": (None, [_p]),
     "glasma_batch_push_variant": (_i32, [_p]),
     "glasma_batch_set_push_variant": (C.c_int, [_p, _i32]),
     "glasma_batch_get_particles": (C.c_int, [_p, _i32] + [_p] * 7),

@@ -9,7 +9,7 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import CpicParams, GlasmaParams, check, lib
+from ._lib import CorrParams, CpicParams, GlasmaParams, check, lib
 
 HBARC = 0.1973269804  # GeV fm
 
@@ -211,6 +211,35 @@ def init_warm(glasma, net):
     if st not in (0, -5):
         check(st)
     return glasma.ic_stats()
+
+
+class Correlators:
+    """Lattice-correlator estimators (static quarks, Eq. 4; lightlike jets along +x,
+    Eq. 5) attached to a Glasma context: they advance with its field steps."""
+
+    def __init__(self, glasma, tau_start_fm=0.0, ox0=0.5, device="cuda"):
+        self.glasma = glasma
+        self.params = CorrParams(tau_start_fm, ox0)
+        nb = lib().corr_workspace_bytes(C.byref(glasma.params))
+        check(0 if nb >= 0 else nb)
+        self._ws, ptr = _workspace(nb, device)
+        h = C.c_void_p()
+        check(lib().corr_create(glasma.handle, C.byref(self.params), C.c_void_p(ptr), nb, C.byref(h)))
+        self.handle = h
+
+    def table(self, cap=1 << 16):
+        """Rows {tau_fm, static <dp_x^2>, <dp_y^2>, <dp_z^2>, lightlike <dp_x^2>, <dp_y^2>,
+        <dp_z^2>} in GeV^2."""
+        out = np.zeros((cap, 7))
+        n = C.c_int64()
+        check(lib().corr_table(self.handle, _dp(out), cap, C.byref(n)))
+        return out[: n.value]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib().corr_destroy(h)
+            self.handle = None
 
 
 class CPIC:

@@ -45,7 +45,9 @@ struct Arena {
     }
 };
 
+struct glasma_corr;
 struct glasma_ctx {
+    glasma_corr* corr = nullptr;  // attached lattice-correlator estimators (advance with every field step)
     glasma_params p;
     int n;
     size_t ns;
@@ -123,7 +125,12 @@ extern "C" glasma_status glasma_create(const glasma_params* p, void* ws, int64_t
     return GLASMA_OK;
 }
 
-extern "C" void glasma_destroy(glasma_ctx* g) { delete g; }
+static void corr_detach(glasma_ctx* g);
+extern "C" void glasma_destroy(glasma_ctx* g) {
+    if (!g) return;
+    corr_detach(g);
+    delete g;
+}
 
 static glasma_status init_impl(glasma_ctx* g, glasma_mlp* mlp) {
     if (!g) return fail(GLASMA_ERR_INVALID, "null context");
@@ -202,10 +209,15 @@ extern "C" glasma_status glasma_get_state(glasma_ctx* g, double* U, double* E, d
     return GLASMA_OK;
 }
 
+static glasma_status corr_after_step(glasma_ctx* g, const void* fo, const void* fn);
 static glasma_status one_field_step(glasma_ctx* g) {
     const int reunit = g->p.reunit_every > 0 && ((g->step + 1) % g->p.reunit_every == 0);
     const StepHost a = step_coeffs(g->buf[g->cur], g->buf[g->cur ^ 1], g->n, g->step, g->dtau, g->p.expanding, reunit);
     CK(launch_field_step(g->prec, a, g->st));
+    if (g->corr) {
+        glasma_status s = corr_after_step(g, g->buf[g->cur], g->buf[g->cur ^ 1]);
+        if (s != GLASMA_OK) return s;
+    }
     g->cur ^= 1;
     g->step++;
     return GLASMA_OK;
@@ -436,4 +448,90 @@ extern "C" glasma_status cpic_casimir_drift(cpic_ctx* c, double out[2]) {
     CK(cudaMemcpyAsync(out, c->cas, 16, cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
     return GLASMA_OK;
+}
+
+// ---------------------------------------------------------------- lattice correlators
+struct glasma_corr {
+    glasma_ctx* g;
+    corr_params p;
+    int first_step;  // the first step whose fields enter (as the particles formed then)
+    int rows;        // accumulator rows: one per step number
+    void* state;     // I, J, W planes
+    double* acc;     // [rows][6] FP64 sums
+};
+
+static int corr_rows(const glasma_params* gp) { return total_steps(gp) + 2; }
+
+extern "C" int64_t corr_workspace_bytes(const glasma_params* gp) {
+    glasma_status s = check_params(gp);
+    if (s != GLASMA_OK) return s;
+    return (int64_t)(align256(corr_state_bytes(gp->precision == GLASMA_FP32, gp->n)) +
+                     align256((size_t)corr_rows(gp) * 6 * 8) + 512);
+}
+
+extern "C" glasma_status corr_create(glasma_ctx* g, const corr_params* p, void* ws, int64_t ws_bytes,
+                                     glasma_corr** out) {
+    if (!g || !p || !out) return fail(GLASMA_ERR_INVALID, "null argument");
+    if (!ws || ((uintptr_t)ws & 255)) return fail(GLASMA_ERR_INVALID, "workspace must be non-null, 256-byte aligned");
+    if (!(p->tau_start_fm >= 0) || !(p->ox0 >= 0) || !(p->ox0 < 1)) return fail(GLASMA_ERR_INVALID, "bad corr_params");
+    if (g->corr) return fail(GLASMA_ERR_INVALID, "the context has a correlator attached already");
+    if (g->step < 1) return fail(GLASMA_ERR_INVALID, "field state not initialised");
+    if (ws_bytes < corr_workspace_bytes(&g->p)) return fail(GLASMA_ERR_NOSPACE, "workspace too small");
+    glasma_corr* c = new (std::nothrow) glasma_corr();
+    if (!c) return fail(GLASMA_ERR_INVALID, "host allocation failed");
+    c->g = g;
+    c->p = *p;
+    c->rows = corr_rows(&g->p);
+    c->first_step = std::max(g->step, std::max(1, (int)llround(p->tau_start_fm / (g->dtau * g->a_fm))));
+    char* b = (char*)ws;
+    c->state = b;
+    c->acc = (double*)(b + align256(corr_state_bytes(g->prec, g->n)));
+    CK(launch_corr_reset(g->prec, c->state, g->n, g->st));
+    CK(cudaMemsetAsync(c->acc, 0, (size_t)c->rows * 6 * 8, g->st));
+    g->corr = c;
+    *out = c;
+    return GLASMA_OK;
+}
+
+static glasma_status corr_after_step(glasma_ctx* g, const void* fo, const void* fn) {
+    glasma_corr* c = g->corr;
+    const int n_step = g->step;
+    if (n_step < c->first_step || n_step + 1 >= c->rows) return GLASMA_OK;
+    const int m = n_step - c->first_step;
+    const int k0 = (int)floor(c->p.ox0 + m * g->dtau), k1 = (int)floor(c->p.ox0 + (m + 1) * g->dtau);
+    const double te = g->p.expanding ? n_step * g->dtau : 1.0;
+    CK(launch_corr_step(g->prec, fo, fn, g->n, te, g->dtau, c->state, k0, k1, c->acc + 6 * (size_t)(n_step + 1),
+                        g->st));
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status corr_table(glasma_corr* c, double* out, int64_t cap, int64_t* n_rows) {
+    if (!c || !out || !n_rows) return fail(GLASMA_ERR_INVALID, "null argument");
+    glasma_ctx* g = c->g;
+    if (!g) return fail(GLASMA_ERR_INVALID, "the field context was destroyed");
+    std::vector<double> h((size_t)c->rows * 6);
+    CK(cudaMemcpyAsync(h.data(), c->acc, h.size() * 8, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    const double conv = 1.0 / (g->a_gev * g->a_gev) / ((double)g->n * g->n);  // site mean, lattice -> GeV^2
+    int64_t k = 0;
+    for (int r = c->first_step; r <= g->step && r < c->rows; r++) {
+        if (k >= cap) return fail(GLASMA_ERR_NOSPACE, "host_out too small");
+        double* o = out + 7 * k;
+        o[0] = r * g->dtau * g->a_fm;
+        for (int i = 0; i < 6; i++) o[1 + i] = r == c->first_step ? 0.0 : h[6 * (size_t)r + i] * conv;
+        k++;
+    }
+    *n_rows = k;
+    return GLASMA_OK;
+}
+
+static void corr_detach(glasma_ctx* g) {
+    if (g->corr) g->corr->g = nullptr;
+    g->corr = nullptr;
+}
+
+extern "C" void corr_destroy(glasma_corr* c) {
+    if (!c) return;
+    if (c->g && c->g->corr == c) c->g->corr = nullptr;
+    delete c;
 }

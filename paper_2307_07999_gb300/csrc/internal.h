@@ -67,6 +67,11 @@ cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStre
 size_t push_args_size(int prec);
 void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out);
 int push_variants();
+// lattice-correlator estimators (kernels_corr.cu): state = I [24][ns], J [24][ns], W [18][ns]
+size_t corr_state_bytes(int prec, int n);
+cudaError_t launch_corr_reset(int prec, void* state, int n, cudaStream_t st);
+cudaError_t launch_corr_step(int prec, const void* fo, const void* fn, int n, double te, double dtau, void* state,
+                             int k_now, int k_next, double* acc, cudaStream_t st);
 cudaError_t launch_push_batched(int prec, int variant, const void* args_dev, const void* items_dev, int n_items,
                                 cudaStream_t st);
 struct PushItemH { int ev, j0; };

@@ -212,6 +212,45 @@ DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
     qB[2] = -T(0.25) * bz;
 }
 
+// The site-centred fields at the view's cell, as 8-vectors (the same formulas as
+// gather_qf_view, which contracts each with Q as soon as it is read):
+// E = (E_x, E_y, E_z), B = (B_x, B_y, B_z)
+template <class T, class V> DEV void site_E(const V& C, T te, Al<T> E[3]) {
+    const T half = T(0.5);
+    {
+        const Al<T> a = C.eavg(0, 0, 0), b = transport_alg(C.link(0, -1, 0), C.eavg(0, -1, 0));
+#pragma unroll
+        for (int k = 0; k < 8; k++) E[0].a[k] = half * (a.a[k] + b.a[k]) / te;
+    }
+    {
+        const Al<T> a = C.eavg(1, 0, 0), b = transport_alg(C.link(1, 0, -1), C.eavg(1, 0, -1));
+#pragma unroll
+        for (int k = 0; k < 8; k++) E[1].a[k] = half * (a.a[k] + b.a[k]) / te;
+    }
+    E[2] = C.piavg();
+}
+template <class T, class V> DEV void site_fields(const V& C, T te, Al<T> E[3], Al<T> B[3]) {
+    const T half = T(0.5);
+    site_E(C, te, E);
+    {
+        const Al<T> fw = conj_alg(C.link(0, 0, 0), C.phi(1, 0)), bw = transport_alg(C.link(0, -1, 0), C.phi(-1, 0));
+#pragma unroll
+        for (int k = 0; k < 8; k++) B[1].a[k] = half * (fw.a[k] - bw.a[k]) / te;  // +D_x phi / tau
+    }
+    {
+        const Al<T> fw = conj_alg(C.link(1, 0, 0), C.phi(0, 1)), bw = transport_alg(C.link(1, 0, -1), C.phi(0, -1));
+#pragma unroll
+        for (int k = 0; k < 8; k++) B[0].a[k] = -half * (fw.a[k] - bw.a[k]) / te;  // -D_y phi / tau
+    }
+    Al<T> acc = im_tl(mul_nd(mul(C.link(0, 0, 0), C.link(1, 1, 0)), mul(C.link(1, 0, 0), C.link(0, 0, 1))));
+    const Al<T> t2 = im_tl(mul(mul_nd(C.link(1, 0, 0), mul(C.link(1, -1, 0), C.link(0, -1, 1))), C.link(0, -1, 0)));
+    const Al<T> t3 =
+        im_tl(mul_dn(mul(C.link(1, -1, -1), C.link(0, -1, 0)), mul(C.link(0, -1, -1), C.link(1, 0, -1))));
+    const Al<T> t4 = im_tl(mul_nd(mul_dn(C.link(1, 0, -1), mul(C.link(0, 0, -1), C.link(1, 1, -1))), C.link(0, 0, 0)));
+#pragma unroll
+    for (int k = 0; k < 8; k++) B[2].a[k] = -T(0.25) * (acc.a[k] + t2.a[k] + t3.a[k] + t4.a[k]);
+}
+
 // one particle: gather, kick, drift, color transport; returns its broadening terms
 template <class T, class S, bool CG = false>
 DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, double& sy, double& sz, double& sc) {
