@@ -48,9 +48,10 @@ def parse():
     p.add_argument("--mode", default="auto", choices=["auto", "graph", "persistent", "eager", "per_event", "fused"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
-    p.add_argument("--workload", default="batch", choices=["batch", "warm_start"],
+    p.add_argument("--workload", default="batch", choices=["batch", "warm_start", "correlators"],
                    help="batch: the 64-event coupled evolution (default); warm_start: the tau = 0+ link "
-                        "solve of 16 events at 1024^2, cold vs learned warm start")
+                        "solve of 16 events at 1024^2, cold vs learned warm start; correlators: the lattice-"
+                        "correlator estimators of Eqs. 4-5 on a 1024^2 event")
     return p.parse_args()
 
 
@@ -471,6 +472,71 @@ def run_warm_start(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- lattice-correlator estimators
+CORR_BYTES_PER_SITE = 10 * 32 + 2 * 48 * 4 + 18 * 4  # field groups read, I and J read + written, W read (FP32)
+
+
+def run_correlators(args, ws, rank, local):
+    """One FP32 MV event at 1024^2 (L = 10 fm) evolved to 1 fm/c with the static and
+    lightlike estimators attached from tau = dtau: time per step of the field step alone
+    and of field step + estimators (CUDA events, inputs > L2), and the estimators at the
+    end of the Glasma stage."""
+    import torch
+
+    import paper_2307_07999_gb300 as G
+
+    torch.cuda.set_device(local)
+    n, L = 1024, 10.0
+    stream = torch.cuda.Stream()
+
+    def event():
+        g = G.Glasma(n, L, precision=G.GLASMA_FP32, tau_end_fm=1.0, seed=(5 << 32) + 500 + rank, reunit_every=64,
+                     stream=stream)
+        assert g.init()[0] == 0
+        return g
+
+    def timed(g, k):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    g = event()
+    g.step(args.warmup)
+    ms_field = timed(g, 100)
+    del g
+    g = event()
+    c = G.Correlators(g, tau_start_fm=0.0, ox0=0.5)
+    g.step(args.warmup)
+    ms_both = timed(g, 100)
+    n_steps = int(math.ceil(1.0 / (0.125 * L / n) - 1e-9))
+    g.step(n_steps - (1 + args.warmup + 100))  # the state is at step 1 after init
+    tab = c.table()
+    ms_corr = ms_both - ms_field
+    achieved = CORR_BYTES_PER_SITE * n * n / (ms_corr / 1000.0) / 1e9
+    peak, kind = measured_peak()
+    i03 = int(np.argmin(np.abs(tab[:, 0] - 0.3)))
+    if rank == 0:
+        line = {
+            "metric": "lattice-correlator estimators (Eqs. 4-5): site-steps/s", "value": n * n / (ms_corr / 1000.0),
+            "unit": "site-steps/s", "n_gpus": ws, "steps": 100, "warmup": args.warmup, "ms_per_step": ms_corr,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 sums)",
+            "data": "synthetic",
+            "config": {"workload": f"one MV event at {n}^2 (L={L} fm, g2mu=2 GeV), static + lightlike estimators "
+                                   "at every site, tau_start = dtau", "l2": "inputs larger than L2"},
+            "field_step_ms": ms_field, "field_plus_estimators_ms": ms_both,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "algorithmic_bytes_per_site": CORR_BYTES_PER_SITE,
+                         "peak_kind": f"{kind} HBM copy (burst)"},
+            "estimators_at_tau_0.3fm_GeV2": {"tau_fm": tab[i03, 0], "static": tab[i03, 1:4].tolist(),
+                                             "lightlike": tab[i03, 4:7].tolist()},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -478,6 +544,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "warm_start":
         run_warm_start(args, ws, rank, local)
+    elif args.workload == "correlators":
+        run_correlators(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:
