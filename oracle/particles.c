@@ -196,6 +196,49 @@ void o_push(int np, int n, int expanding, double dtau, int step, double mass, co
             const double *Eo, const double *En, const double *phi, const double *pio,
             const double *pin, double *x, double *y, double *eta, double *px, double *py,
             double *peta, double *Q, const double *p0, double acc[4]) {
+    o_push_int(np, n, expanding, dtau, step, mass, U, Eo, En, phi, pio, pin, x, y, eta, px, py, peta, Q,
+               p0, acc, 0);
+}
+
+/* The momentum kick of one step with the charge-contracted fields qE, qB (both
+ * integrators; the Christoffel term -p_eta^/tau acts only when expanding).
+ *   explicit (0): p += dtau [qE + (p / p^tau) x qB] - dtau p_eta^/tau_n e_eta (first order)
+ *   Boris (1):    p_eta^ *= tau_n / tau_{n+1/2} (exact decay over the first half step);
+ *                 p- = p + dtau/2 qE;  rotation of p- about qB by the angle of
+ *                 t = (dtau/2) qB / p^tau(p-):  p' = p- + p- x t,  p+ = p- + p' x 2t/(1 + t.t)
+ *                 (|p+| = |p-| exactly);  p = p+ + dtau/2 qE;
+ *                 p_eta^ *= tau_{n+1/2} / tau_{n+1}   (second order, Boris 1970) */
+static void kick(int integrator, int expanding, double dtau, double tau_n, double mass, const double qE[3],
+                 const double qB[3], double p[3]) {
+    if (integrator == 0) {
+        const double pt = sqrt(mass * mass + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+        const double ipt = pt > 0 ? 1.0 / pt : 0.0;
+        double f[3] = {qE[0] + (p[1] * qB[2] - p[2] * qB[1]) * ipt, qE[1] + (p[2] * qB[0] - p[0] * qB[2]) * ipt,
+                       qE[2] + (p[0] * qB[1] - p[1] * qB[0]) * ipt};
+        if (expanding) f[2] -= p[2] / tau_n;
+        for (int i = 0; i < 3; i++) p[i] += dtau * f[i];
+        return;
+    }
+    const double tau_h = tau_n + 0.5 * dtau, tau_1 = tau_n + dtau;
+    if (expanding) p[2] *= tau_n / tau_h;
+    for (int i = 0; i < 3; i++) p[i] += 0.5 * dtau * qE[i];
+    const double g = sqrt(mass * mass + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    const double ig = g > 0 ? 1.0 / g : 0.0;
+    const double t[3] = {0.5 * dtau * qB[0] * ig, 0.5 * dtau * qB[1] * ig, 0.5 * dtau * qB[2] * ig};
+    const double pp[3] = {p[0] + (p[1] * t[2] - p[2] * t[1]), p[1] + (p[2] * t[0] - p[0] * t[2]),
+                          p[2] + (p[0] * t[1] - p[1] * t[0])};
+    const double sf = 2.0 / (1.0 + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    p[0] += sf * (pp[1] * t[2] - pp[2] * t[1]);
+    p[1] += sf * (pp[2] * t[0] - pp[0] * t[2]);
+    p[2] += sf * (pp[0] * t[1] - pp[1] * t[0]);
+    for (int i = 0; i < 3; i++) p[i] += 0.5 * dtau * qE[i];
+    if (expanding) p[2] *= tau_h / tau_1;
+}
+
+void o_push_int(int np, int n, int expanding, double dtau, int step, double mass, const cplx *U,
+                const double *Eo, const double *En, const double *phi, const double *pio,
+                const double *pin, double *x, double *y, double *eta, double *px, double *py,
+                double *peta, double *Q, const double *p0, double acc[4], int integrator) {
     double tau_n = step * dtau, tau_h = (step + 0.5) * dtau;
     double te_h = expanding ? tau_h : 1.0;
     double sx = 0, sy = 0, sz = 0;
@@ -207,14 +250,9 @@ void o_push(int np, int n, int expanding, double dtau, int step, double mass, co
         double *q = Q + 8 * j;
         double qE[3] = {dot8(q, F[0]), dot8(q, F[1]), dot8(q, F[2])};
         double qB[3] = {dot8(q, F[3]), dot8(q, F[4]), dot8(q, F[5])};
-        double pxo = px[j], pyo = py[j], pzo = peta[j];
-        double pt = sqrt(mass * mass + pxo * pxo + pyo * pyo + pzo * pzo);
-        double ipt = pt > 0 ? 1.0 / pt : 0.0;
-        double fx = qE[0] + (pyo * qB[2] - pzo * qB[1]) * ipt;
-        double fy = qE[1] + (pzo * qB[0] - pxo * qB[2]) * ipt;
-        double fz = qE[2] + (pxo * qB[1] - pyo * qB[0]) * ipt;
-        if (expanding) fz -= pzo / tau_n;
-        double pxn = pxo + dtau * fx, pyn = pyo + dtau * fy, pzn = pzo + dtau * fz;
+        double pk[3] = {px[j], py[j], peta[j]};
+        kick(integrator, expanding, dtau, tau_n, mass, qE, qB, pk);
+        double pxn = pk[0], pyn = pk[1], pzn = pk[2];
         double ptn = sqrt(mass * mass + pxn * pxn + pyn * pyn + pzn * pzn);
         double iptn = ptn > 0 ? 1.0 / ptn : 0.0;
         double xn = x[j] + dtau * pxn * iptn;

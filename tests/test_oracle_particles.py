@@ -291,3 +291,97 @@ def test_particle_init_distributions():
     pt = np.hypot(P.px, P.py)
     assert pt.max() <= 2.0 and abs(pt.mean() - 1.0) < 5 * 2 / np.sqrt(12 * N)
     assert np.all(P.eta == 0) and np.all(P.peta == 0)
+
+
+# ---------------------------------------------------------------- Boris integrator
+def run_int(P, st, dtau, mass, m, expanding, integrator):
+    for _ in range(m):
+        nx = O.field_step(st, dtau, expanding)
+        O.push(P, st, nx, dtau, mass, expanding, integrator)
+        st = nx
+    return st
+
+
+def test_boris_uniform_bz_norm_exact_and_cyclotron_second_order():
+    """Pure magnetic field: the Boris rotation keeps |p| to rounding at any step, and
+    the orbit converges at second order (the explicit kick: first order, |p| grows)."""
+    n = 24
+    bz = -2 * np.sin(uniform_bz_state(n)[1] / 2)
+    mass, p0, T = 0.4, 0.3, 6.0
+    Q0 = O.q0_cartan()
+    w = Q0[2] * bz / np.sqrt(mass ** 2 + p0 ** 2)
+    errs = []
+    for dtau in (0.04, 0.02):
+        P = O.Particles(1)
+        P.x[:], P.y[:], P.px[:] = 12.3, 11.7, p0
+        P.Q[0] = Q0
+        P.set_p0(mass, expanding=0)
+        run_int(P, uniform_bz_state(n)[0], dtau, mass, int(round(T / dtau)), 0, 1)
+        assert abs(np.hypot(P.px[0], P.py[0]) - p0) < 1e-14
+        want = p0 * np.array([np.cos(w * T), -np.sin(w * T)])
+        errs.append(np.hypot(P.px[0] - want[0], P.py[0] - want[1]) / p0)
+    assert errs[0] < 0.01 and 3.5 < errs[0] / errs[1] < 4.5, errs
+    P = O.Particles(1)
+    P.x[:], P.y[:], P.px[:] = 12.3, 11.7, p0
+    P.Q[0] = Q0
+    P.set_p0(mass, expanding=0)
+    run_int(P, uniform_bz_state(n)[0], 0.04, mass, 150, 0, 0)
+    assert np.hypot(P.px[0], P.py[0]) > p0 * (1 + 1e-4)
+
+
+def test_boris_equals_explicit_without_magnetic_field():
+    """Uniform Cartan E_x, no B: both integrators give p_x = p_0 + Q^3 e t exactly and
+    the same positions."""
+    e, mass, dtau, m = 0.3, 0.5, 0.02, 120
+    st = vac_state(8, 0)
+    st.E[:, 0, 2] = e
+    rng = np.random.default_rng(5)
+    P = make_particles(20, 8, rng, pscale=0.2, mass=mass)
+    Pb = P.copy()
+    run_int(P, st, dtau, mass, m, 0, 0)
+    run_int(Pb, st, dtau, mass, m, 0, 1)
+    for k in ("px", "py", "peta", "x", "y"):
+        assert np.abs(getattr(P, k) - getattr(Pb, k)).max() < 1e-12, k
+
+
+def test_boris_milne_free_particle_peta_exact():
+    """Zero field in Milne coordinates: p_eta^ = tau p^eta falls as 1/tau exactly (the
+    covariant p_eta = tau^2 p^eta is conserved); the Boris step applies that decay
+    exactly, the explicit kick to first order."""
+    dtau, mass, tau0, T = 0.02, 1.0, 0.5, 1.0
+    res = {}
+    for integrator in (0, 1):
+        P = O.Particles(1)
+        P.px[:] = 0.3
+        P.peta[:] = 0.8
+        P.set_p0(mass)
+        st = vac_state(4, step=int(round(tau0 / dtau)))
+        run_int(P, st, dtau, mass, int(round(T / dtau)), 1, integrator)
+        res[integrator] = P.peta[0]
+    want = 0.8 * tau0 / (tau0 + T)
+    assert abs(res[1] - want) < 1e-14
+    assert abs(res[0] - want) > 1e-4
+
+
+@pytest.mark.parametrize("expanding", [0, 1])
+def test_boris_is_gauge_invariant(expanding):
+    rng = np.random.default_rng(13)
+    n, dtau, mass, m = 6, 0.1, 0.6, 30
+    st = rand_fields(n, rng)
+    P = make_particles(60, n, rng, mass=mass, peta=True)
+    Om = [O.exp_i(2 * rng.standard_normal(8)) for _ in range(n * n)]
+    stg = st.copy()
+    for s in range(n * n):
+        x, y = s % n, s // n
+        for d, sp in ((0, (x + 1) % n + n * y), (1, x + n * ((y + 1) % n))):
+            stg.U[s, d] = Om[s] @ st.U[s, d] @ Om[sp].conj().T
+            stg.E[s, d] = O.conj_by(Om[s], st.E[s, d])
+        stg.phi[s] = O.conj_by(Om[s], st.phi[s])
+        stg.pi[s] = O.conj_by(Om[s], st.pi[s])
+    Pg = P.copy()
+    for j in range(P.np):
+        Pg.Q[j] = O.conj_by(Om[int(P.x[j]) + n * int(P.y[j])], P.Q[j])
+    run_int(P, st, dtau, mass, m, expanding, 1)
+    run_int(Pg, stg, dtau, mass, m, expanding, 1)
+    for k in ("px", "py", "peta", "x", "y", "eta"):
+        assert np.abs(getattr(P, k) - getattr(Pg, k)).max() < 1e-11
