@@ -81,6 +81,10 @@ typedef struct {
     double p_min_GeV, p_max_GeV;
     double q2, q3;           /* Casimirs of Q (4 and 10/3 for <QQ> = 1/2, <QQQ> = d/4) */
     int32_t bin_every;       /* counting sort of the particles by cell every k steps (0: never) */
+    int32_t integrator;      /* momentum kick of Eq. 2: 0 explicit first order (magnetic term with the
+                                pre-step momentum); 1 Boris (half electric kick, norm-preserving
+                                rotation about Q.B, half electric kick; the Christoffel decay of
+                                p_eta^ applied exactly over each half step): second order */
     uint64_t seed;           /* Philox key of positions, momenta and Haar rotations */
 } cpic_params;
 

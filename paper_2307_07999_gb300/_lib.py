@@ -64,6 +64,7 @@ class CpicParams(C.Structure):
         ("q2", C.c_double),
         ("q3", C.c_double),
         ("bin_every", C.c_int32),
+        ("integrator", C.c_int32),
         ("seed", C.c_uint64),
     ]
 

@@ -278,6 +278,7 @@ static glasma_status check_cpic(const cpic_params* p) {
     if (p->mass_GeV < 0 || p->tau_form_fm < 0 || p->p_min_GeV < 0 || p->p_max_GeV < p->p_min_GeV)
         return fail(GLASMA_ERR_INVALID, "bad mass, tau_form or momentum range");
     if (p->init_kind != 0 && p->init_kind != 1) return fail(GLASMA_ERR_INVALID, "bad init_kind");
+    if (p->integrator != 0 && p->integrator != 1) return fail(GLASMA_ERR_INVALID, "bad integrator");
     return GLASMA_OK;
 }
 static int total_steps(const glasma_params* gp) {
@@ -393,18 +394,13 @@ extern "C" glasma_status cpic_push(cpic_ctx* c, int32_t n_steps) {
         glasma_status s = one_field_step(g);
         if (s != GLASMA_OK) return s;
         if (n >= c->first_step && c->np > 0) {
-            const double tn = n * g->dtau, th = (n + 0.5) * g->dtau;
             PushHost a;
             a.fo = fo;
             a.fn = g->buf[g->cur];
             a.n = g->n;
             a.np = c->np;
-            a.dtau = g->dtau;
-            a.te = g->p.expanding ? tn : 1.0;
-            a.ichr = g->p.expanding ? 1.0 / tn : 0.0;
-            a.teh = g->p.expanding ? th : 1.0;
+            push_coeffs(a, n, g->dtau, g->p.expanding, c->p.integrator);
             a.mass = c->mass;
-            a.expanding = g->p.expanding;
             a.acc = c->acc + 4 * (size_t)(n + 1);
             CK(launch_push(g->prec, a, c->P[c->pcur], g->st));
             if (c->p.bin_every > 0 && ++c->since_sort >= c->p.bin_every) {

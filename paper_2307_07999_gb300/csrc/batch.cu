@@ -94,7 +94,7 @@ static glasma_status check_batch(const glasma_params* ev, const cpic_params* pp,
             ev[e].n_sheets < 1 || !(ev[e].tau_end_fm > 0))
             return bfail(GLASMA_ERR_INVALID, "bad event parameters");
         if (pp[e].n_particles < 0 || pp[e].mass_GeV < 0 || pp[e].tau_form_fm < 0 || pp[e].p_max_GeV < pp[e].p_min_GeV ||
-            (pp[e].init_kind != 0 && pp[e].init_kind != 1))
+            (pp[e].init_kind != 0 && pp[e].init_kind != 1) || (pp[e].integrator != 0 && pp[e].integrator != 1))
             return bfail(GLASMA_ERR_INVALID, "bad particle parameters");
     }
     return GLASMA_OK;
@@ -290,9 +290,9 @@ static glasma_status build_tables(glasma_batch* b) {
             const StepHost st = step_coeffs(src, dst, x.n, s, x.dtau, 1, reunit);
             pack_step_args(b->prec, st, hs.data() + ((size_t)k * E + i) * sa);
             PushHost ph;
-            ph.fo = src; ph.fn = dst; ph.n = x.n; ph.np = x.np; ph.dtau = x.dtau;
-            ph.te = s * x.dtau; ph.ichr = 1.0 / (s * x.dtau); ph.teh = (s + 0.5) * x.dtau; ph.mass = x.mass;
-            ph.expanding = 1;
+            ph.fo = src; ph.fn = dst; ph.n = x.n; ph.np = x.np;
+            push_coeffs(ph, s, x.dtau, 1, x.pp.integrator);
+            ph.mass = x.mass;
             ph.acc = (on && s >= x.n_form) ? x.acc + 4 * (size_t)(s + 1) : nullptr;
             pack_push_args(b->prec, ph, x.P, hp.data() + ((size_t)k * E + i) * pa);
         }
@@ -417,9 +417,9 @@ static cudaError_t enqueue_per_event(glasma_batch* b) {
             if (e != cudaSuccess) return e;
             if (s >= x.n_form && x.np > 0) {
                 PushHost ph;
-                ph.fo = x.buf[k % 3]; ph.fn = x.buf[(k + 1) % 3]; ph.n = x.n; ph.np = x.np; ph.dtau = x.dtau;
-                ph.te = s * x.dtau; ph.ichr = 1.0 / (s * x.dtau); ph.teh = (s + 0.5) * x.dtau; ph.mass = x.mass;
-                ph.expanding = 1;
+                ph.fo = x.buf[k % 3]; ph.fn = x.buf[(k + 1) % 3]; ph.n = x.n; ph.np = x.np;
+                push_coeffs(ph, s, x.dtau, 1, x.pp.integrator);
+                ph.mass = x.mass;
                 ph.acc = x.acc + 4 * (size_t)(s + 1);
                 e = launch_push(b->prec, ph, x.P, b->st);
                 if (e != cudaSuccess) return e;

@@ -60,8 +60,22 @@ struct PushHost {
     int n, np;
     double dtau, te, ichr, teh, mass;
     int expanding;
+    int boris;           // momentum kick: 0 explicit, 1 Boris
+    double dec0, dec1;   // Boris: p_eta^ decay factors tau_n/tau_{n+1/2}, tau_{n+1/2}/tau_{n+1} (1: static box)
     double* acc;
 };
+// the step-dependent coefficients of the push from tau_n = step * dtau to tau_{n+1}
+inline void push_coeffs(PushHost& a, int step, double dtau, int expanding, int integrator) {
+    const double tn = step * dtau, th = (step + 0.5) * dtau, t1 = (step + 1.0) * dtau;
+    a.dtau = dtau;
+    a.expanding = expanding;
+    a.te = expanding ? tn : 1.0;
+    a.ichr = expanding ? 1.0 / tn : 0.0;
+    a.teh = expanding ? th : 1.0;
+    a.boris = integrator == 1;
+    a.dec0 = expanding ? tn / th : 1.0;
+    a.dec1 = expanding ? th / t1 : 1.0;
+}
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st);
 // batched push: args[n_ev] (acc == nullptr: event idle this step), items {ev, j0} of 256 particles
 size_t push_args_size(int prec);

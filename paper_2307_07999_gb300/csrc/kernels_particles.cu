@@ -39,6 +39,7 @@ template <class T> static PushArgs<T> push_args(const PushHost& a, const PartHos
     A.P = soa<T>(h); A.np = a.np;
     A.dtau = (T)a.dtau; A.te = (T)a.te; A.ichr = (T)a.ichr; A.teh = (T)a.teh; A.mass = (T)a.mass;
     A.expanding = a.expanding; A.acc = a.acc;
+    A.boris = a.boris; A.dec0 = (T)a.dec0; A.dec1 = (T)a.dec1;
     return A;
 }
 size_t push_args_size(int prec) { return prec ? sizeof(PushArgs<float>) : sizeof(PushArgs<double>); }

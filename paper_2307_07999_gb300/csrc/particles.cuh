@@ -31,6 +31,8 @@ template <class T> struct PushArgs {
     T teh;         // tau_{n+1/2} (expanding) or 1: eta drift
     T mass;
     int expanding;
+    int boris;     // momentum kick: 0 explicit (first order), 1 Boris (second order)
+    T dec0, dec1;  // Boris: p_eta^ decay tau_n/tau_{n+1/2}, tau_{n+1/2}/tau_{n+1} (1 in a static box)
     double* acc;   // this step's row: {sum dpx^2, sum dpy^2, sum dpz^2, count}
 };
 
@@ -269,14 +271,34 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
     T pz = CG ? __ldcg(P.peta + j) : P.peta[j];
     const T m2 = A.mass * A.mass;
     T px = p0x + dpx, py = p0y + dpy;
-    const T pt = sqrt(m2 + px * px + py * py + pz * pz);
-    const T ipt = pt > T(0) ? T(1) / pt : T(0);
-    const T fx = qE[0] + (py * qB[2] - pz * qB[1]) * ipt;
-    const T fy = qE[1] + (pz * qB[0] - px * qB[2]) * ipt;
-    const T fz = qE[2] + (px * qB[1] - py * qB[0]) * ipt - pz * A.ichr;
-    dpx += A.dtau * fx;
-    dpy += A.dtau * fy;
-    pz += A.dtau * fz;
+    if (!A.boris) {
+        // explicit: p += dtau [Q.E + (p / p^tau) x Q.B] - dtau p_eta^ / tau_n e_eta
+        const T pt = sqrt(m2 + px * px + py * py + pz * pz);
+        const T ipt = pt > T(0) ? T(1) / pt : T(0);
+        const T fx = qE[0] + (py * qB[2] - pz * qB[1]) * ipt;
+        const T fy = qE[1] + (pz * qB[0] - px * qB[2]) * ipt;
+        const T fz = qE[2] + (px * qB[1] - py * qB[0]) * ipt - pz * A.ichr;
+        dpx += A.dtau * fx;
+        dpy += A.dtau * fy;
+        pz += A.dtau * fz;
+    } else {
+        // Boris (1970): the Christoffel decay of p_eta^ over the first half step (exact for
+        // a free particle), half electric kick, rotation about Q.B by the angle of
+        // t = (dtau/2) Q.B / p^tau (|p| unchanged), half electric kick, decay over the
+        // second half step.  The transverse change is accumulated into dp, so FP32
+        // round-off stays relative to the change.
+        const T h = T(0.5) * A.dtau;
+        pz *= A.dec0;
+        const T mx = px + h * qE[0], my = py + h * qE[1], mz = pz + h * qE[2];
+        const T g = sqrt(m2 + mx * mx + my * my + mz * mz);
+        const T ig = g > T(0) ? h / g : T(0);
+        const T tx = qB[0] * ig, ty = qB[1] * ig, tz = qB[2] * ig;
+        const T ux = mx + (my * tz - mz * ty), uy = my + (mz * tx - mx * tz), uz = mz + (mx * ty - my * tx);
+        const T sf = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
+        dpx += A.dtau * qE[0] + sf * (uy * tz - uz * ty);
+        dpy += A.dtau * qE[1] + sf * (uz * tx - ux * tz);
+        pz = (mz + sf * (ux * ty - uy * tx) + h * qE[2]) * A.dec1;
+    }
     px = p0x + dpx;
     py = p0y + dpy;
     const T ptn = sqrt(m2 + px * px + py * py + pz * pz);

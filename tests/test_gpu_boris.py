@@ -1,0 +1,170 @@
+"""The Boris momentum kick on the GPU (cpic_params.integrator = 1) against the oracle's
+Boris push, through the C ABI.
+
+Boris (1970): half electric kick, rotation of p about Q.B by the angle of
+t = (dtau/2) Q.B / p^tau, which keeps |p| exactly, half electric kick; in Milne
+coordinates the Christoffel decay of p_eta^ is applied exactly over each half step.
+FP64: 1e-10 relative, as the explicit push.  FP32: 1e-4 on <dp^2>(tau) and kappa of
+the 32^2 configuration, as the explicit push.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import HBARC, lattice_units, random_particles, random_state, rel_err
+
+pytestmark = pytest.mark.gpu
+
+G = pytest.importorskip("paper_2307_07999_gb300")
+W = pytest.importorskip("paper_2307_07999_gb300.workloads")
+
+
+def run_pair(n, np_, steps, prec, seed, expanding=1, mass=0.5, bin_every=0):
+    st = random_state(n, seed=seed, step=4)
+    P = random_particles(np_, n, seed + 1, mass=mass)
+    g = G.Glasma(n, 6.0, precision=prec, expanding=expanding, tau_end_fm=100.0)
+    g.set_state(st.U, st.E, st.phi, st.pi, st.step)
+    a_gev = (6.0 / n) / HBARC
+    c = G.CPIC(g, np_, mass / a_gev, 0.0, bin_every=bin_every, integrator=1)
+    c.set_particles(P.x, P.y, P.eta, P.px, P.py, P.peta, P.Q, P.p0)
+    accs = []
+    for _ in range(steps):
+        nx = O.field_step(st, 0.125, expanding)
+        accs.append(O.push(P, st, nx, 0.125, mass, expanding, integrator=1))
+        st = nx
+    c.push(steps)
+    return c, P, np.array(accs), a_gev
+
+
+def check_particles(got, P, n, tol):
+    dx = np.abs(got["x"] - P.x)
+    dy = np.abs(got["y"] - P.y)
+    assert np.minimum(dx, n - dx).max() < tol and np.minimum(dy, n - dy).max() < tol
+    for k in ("px", "py", "peta", "eta"):
+        assert rel_err(got[k], getattr(P, k)) < tol, k
+    assert rel_err(got["Q"], P.Q) < tol
+
+
+@pytest.mark.parametrize("n,np_,mass", [(12, 300, 0.5), (37, 700, 0.5), (10, 64, 0.0)])
+@pytest.mark.parametrize("expanding", [1, 0])
+def test_boris_push_fp64(n, np_, mass, expanding):
+    """Lattices of 12^2, 37^2 (ragged against every block) and 10^2 with massless
+    particles; 12 coupled steps; particle states and broadening table at 1e-10."""
+    c, P, accs, a_gev = run_pair(n, np_, 12, 0, 61 + n, expanding, mass=mass)
+    check_particles(c.get_particles(), P, n, 1e-10)
+    tab = c.broadening()
+    want = accs[:, :3] / accs[:, 3:4] / a_gev ** 2
+    assert rel_err(tab[1:, 1:4], want) < 1e-10
+    assert np.all(tab[1:, 4] == np_)
+
+
+def test_boris_differs_from_explicit():
+    """The integrator switch reaches the kernel: on the same inputs the first-order
+    explicit kick and the second-order Boris kick part at O(dtau) over a few steps."""
+    n, np_ = 12, 200
+    c1, _, _, _ = run_pair(n, np_, 8, 0, 71)
+    st = random_state(n, seed=71, step=4)
+    P = random_particles(np_, n, 72, mass=0.5)
+    g = G.Glasma(n, 6.0, precision=0, tau_end_fm=100.0)
+    g.set_state(st.U, st.E, st.phi, st.pi, st.step)
+    c0 = G.CPIC(g, np_, 0.5 / ((6.0 / n) / HBARC), 0.0, integrator=0)
+    c0.set_particles(P.x, P.y, P.eta, P.px, P.py, P.peta, P.Q, P.p0)
+    c0.push(8)
+    d = rel_err(c1.get_particles()["px"], c0.get_particles()["px"])
+    assert d > 1e-4
+
+
+def test_boris_sorting_is_invisible():
+    c1, P1, _, _ = run_pair(16, 500, 10, 0, 81, bin_every=0)
+    c2, P2, _, _ = run_pair(16, 500, 10, 0, 81, bin_every=3)
+    a, b = c1.get_particles(), c2.get_particles()
+    for k in a:
+        assert np.abs(a[k] - b[k]).max() < 1e-13, k
+
+
+def config1_boris_oracle(n=32, L=6.0, np_=1000, mass_gev=1.5, tau_form=0.1, seed=12345, pseed=777):
+    a_fm, a, g2mua, mira = lattice_units(n, L)
+    st, iters, fails = O.glasma_init(n, 10, g2mua, mira, seed, 0.125)
+    st0 = st.copy()
+    P = O.particles_init(np_, n, mass_gev * a, 0, 0.0, 0.0, pseed)
+    nform = int(round(tau_form / (0.125 * a_fm)))
+    nsteps = int(np.ceil(1.0 / (0.125 * a_fm) - 1e-9))
+    while st.step < nform:
+        st = O.field_step(st, 0.125)
+    rows = [(nform * 0.125 * a_fm, 0.0, 0.0, 0.0, np_)]
+    while st.step < nsteps:
+        nx = O.field_step(st, 0.125)
+        acc = O.push(P, st, nx, 0.125, mass_gev * a, integrator=1)
+        rows.append((nx.step * 0.125 * a_fm, *(acc[:3] / acc[3] / a ** 2), acc[3]))
+        st = nx
+    return np.array(rows), st0
+
+
+@pytest.fixture(scope="module")
+def config1():
+    return config1_boris_oracle()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_config1_boris(config1, prec, tol):
+    """32^2, L = 6 fm, 1000 charm at rest formed at 0.1 fm/c, to 1 fm/c with the Boris
+    kick: <dp_i^2>(tau) and kappa at 1e-10 (FP64) and 1e-4 (FP32, Gauss law 1e-5)."""
+    want, st0 = config1
+    g = G.Glasma(32, 6.0, precision=prec, tau_end_fm=1.0, seed=12345, reunit_every=(8 if prec else 0))
+    g.set_state(st0.U, st0.E, st0.phi, st0.pi, 1)
+    c = G.CPIC(g, 1000, 1.5, 0.1, seed=777, integrator=1)
+    c.init()
+    n_form = int(round(0.1 / (0.125 * 6.0 / 32)))
+    g.step(n_form - 1)
+    c.push(int(np.ceil(1.0 / (0.125 * 6.0 / 32) - 1e-9)) - n_form)
+    tab = c.broadening()
+    assert tab.shape == want.shape
+    e_dp = rel_err(tab[:, 1:4], want[:, 1:4])
+    e_k = rel_err(G.kappa_qhat(tab)[:, 1:], G.kappa_qhat(want)[:, 1:])
+    print(f"boris prec {prec}: dp2 {e_dp:.2e} kappa {e_k:.2e}")
+    assert e_dp < tol and e_k < tol
+    if prec:
+        assert g.diagnostics()[0] < 1e-5
+    else:
+        drift = c.casimir_drift()
+        assert drift[0] < 1e-11 and drift[1] < 1e-11
+
+
+def test_boris_batch_modes_agree():
+    """A two-event FP64 batch with the Boris kick: every batch mode gives the graph
+    mode's broadening to 1e-13, and the graph mode the oracle's to 1e-10."""
+    spec = [(24, 2.4, 1.8), (32, 2.6, 2.0)]
+    evs, pps = [], []
+    for e, (n, L, g2mu) in enumerate(spec):
+        s = W.event_seed(9, 10 + e)
+        gp = W.glasma_params(n, L, g2mu, s, 0, tau_end_fm=0.3, reunit_every=0)
+        gp.newton_tol = 1e-14
+        evs.append(gp)
+        pps.append(W.charm_params(300, s, mass=1.5, p_max=3.0, tau_form=0.08, integrator=1))
+    B = G.Batch(evs, pps)
+    assert B.init() == 0
+    tabs = {}
+    for mode in ("graph", "eager", "per_event", "fused", "persistent"):
+        B.run(mode)
+        tabs[mode] = [B.broadening(e) for e in range(len(evs))]
+    for m in ("eager", "per_event", "fused", "persistent"):
+        for e in range(len(evs)):
+            assert rel_err(tabs[m][e][:, 1:4], tabs["graph"][e][:, 1:4]) < 1e-13, (m, e)
+    for e, (gp, pp) in enumerate(zip(evs, pps)):
+        n = gp.n
+        a_fm = gp.L_fm / n
+        a = a_fm / HBARC
+        st, _, _ = O.glasma_init(n, gp.n_sheets, gp.g2mu_GeV * a, gp.m_ir_GeV * a, gp.seed, 0.125, tol=1e-14)
+        P = O.particles_init(pp.n_particles, n, pp.mass_GeV * a, 0, 0.0, pp.p_max_GeV * a, pp.seed)
+        n_form = max(1, int(round(pp.tau_form_fm / (0.125 * a_fm))))
+        n_steps = int(np.ceil(gp.tau_end_fm / (0.125 * a_fm) - 1e-9))
+        while st.step < n_form:
+            st = O.field_step(st, 0.125)
+        rows = []
+        while st.step < n_steps:
+            nx = O.field_step(st, 0.125)
+            acc = O.push(P, st, nx, 0.125, pp.mass_GeV * a, integrator=1)
+            rows.append(acc[:3] / acc[3] / a ** 2)
+            st = nx
+        got = tabs["graph"][e]
+        assert rel_err(got[1:, 1:4], np.array(rows)) < 1e-10, e
