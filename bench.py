@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Glasma site-updates/s & Wong particle-steps/s on 1 GB300 vs plain, at fixed tol"
 WORKLOAD = ("64 MV events, 16 each of 128^2/256^2/384^2/512^2 (L=10 fm, g2mu~U[1.5,2.5] GeV), "
             "10k charm/event, FP32 fields+particles with FP64 accumulators, tau 0->1 fm/c")
+HBARC_GEV_FM = 0.1973269804
 BYTES_PER_SITE = 448  # algorithmic bytes of one FP32 site-update (12-real links, read + write once)
 BYTES_PER_PARTICLE = 132  # algorithmic bytes of one FP32 particle-step (state read + write, p0 read)
 
@@ -48,10 +49,11 @@ def parse():
     p.add_argument("--mode", default="auto", choices=["auto", "graph", "persistent", "eager", "per_event", "fused"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
-    p.add_argument("--workload", default="batch", choices=["batch", "warm_start", "correlators"],
+    p.add_argument("--workload", default="batch", choices=["batch", "warm_start", "correlators", "single_512"],
                    help="batch: the 64-event coupled evolution (default); warm_start: the tau = 0+ link "
                         "solve of 16 events at 1024^2, cold vs learned warm start; correlators: the lattice-"
-                        "correlator estimators of Eqs. 4-5 on a 1024^2 event")
+                        "correlator estimators of Eqs. 4-5 on a 1024^2 event; single_512: one 512^2 event with "
+                        "100k charm + 100k beauty, FP32 and FP64")
     return p.parse_args()
 
 
@@ -537,6 +539,112 @@ def run_correlators(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- one event at paper scale, FP32 and FP64
+def run_single_512(args, ws, rank, local):
+    """One MV event on 512^2 (L = 10 fm, g2mu = 2 GeV, m = 0.2 GeV, 10 sheets) with 100k
+    charm (1.5 GeV) and 100k beauty (4.7 GeV) quarks, |p_T| ~ U[0, 5] GeV, formed at
+    1/(2M), evolved from tau = dtau to 1 fm/c (409 coupled steps), in FP32 and in FP64.
+    A step is one whole run; every run restarts from the same initial state (uploaded
+    untimed).  Also: the FP32 field step alone (roofline) and the FP32-vs-FP64 errors of
+    <dp_i^2>, kappa and the anisotropy <dp_L^2>/<dp_T^2>."""
+    import torch
+
+    import paper_2307_07999_gb300 as G
+
+    torch.cuda.set_device(local)
+    n, L, NP = 512, 10.0, 100000
+    species = [(1.5, (2 << 32) + 11 + 1000 * rank), (4.7, (2 << 32) + 12 + 1000 * rank)]
+    seed = (2 << 32) + 1000 * rank
+    stream = torch.cuda.Stream()
+    g0 = G.Glasma(n, L, precision=G.GLASMA_FP64, tau_end_fm=1.0, seed=seed, stream=stream)
+    fails = g0.init()[0]
+    U, E, phi, pi, _ = g0.get_state()
+    del g0
+    n_steps = int(math.ceil(1.0 / (0.125 * L / n) - 1e-9))
+
+    def setup(prec):
+        g = G.Glasma(n, L, precision=prec, tau_end_fm=1.0, seed=seed, reunit_every=(64 if prec else 0),
+                     stream=stream)
+        cs = [G.CPIC(g, NP, m, HBARC_GEV_FM / (2 * m), p_min_GeV=0.0, p_max_GeV=5.0, seed=ps) for m, ps in species]
+        return g, cs
+
+    def one_run(g, cs):
+        g.set_state(U, E, phi, pi, 1)
+        for c in cs:
+            c.init()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.push_many(cs, n_steps - 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    out = {}
+    for prec in (G.GLASMA_FP32, G.GLASMA_FP64):
+        g, cs = setup(prec)
+        for _ in range(args.warmup):
+            one_run(g, cs)
+        sampler = ClockSampler(local) if prec == G.GLASMA_FP32 else None
+        if sampler:
+            sampler.start()
+        barrier(ws)
+        ms = [one_run(g, cs) for _ in range(args.steps)]
+        clocks = sampler.stop() if sampler else None
+        tabs = [c.broadening() for c in cs]
+        psteps = sum(int(t[1:, 4].sum()) for t in tabs)
+        g.set_state(U, E, phi, pi, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(100)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[prec] = dict(ms=max_over_ranks(statistics.mean(ms), ws), tabs=tabs, psteps=psteps,
+                         field_ms=e0.elapsed_time(e1) / 100, clocks=clocks, diag=g.diagnostics())
+        del cs, g
+    f32, f64 = out[G.GLASMA_FP32], out[G.GLASMA_FP64]
+    su = n * n * (n_steps - 1)
+    errs = {}
+    for name, t32, t64 in zip(("charm", "beauty"), f32["tabs"], f64["tabs"]):
+        den = lambda a: max(np.abs(a).max(), 1e-300)
+        k32, k64 = G.kappa_qhat(t32)[:, 1:], G.kappa_qhat(t64)[:, 1:]
+        a32, a64 = G.anisotropy(t32)[1:, 1], G.anisotropy(t64)[1:, 1]
+        errs[name] = {"dp2": float(np.abs(t32[:, 1:4] - t64[:, 1:4]).max() / den(t64[:, 1:4])),
+                      "kappa": float(np.abs(k32 - k64).max() / den(k64)),
+                      "anisotropy": float(np.abs(a32 - a64).max() / den(a64)),
+                      "final_anisotropy": float(a64[-1]),
+                      "kappa_T_peak_GeV2_per_fm": float((k64[:, 0] + k64[:, 1]).max()),
+                      "kappa_L_peak_GeV2_per_fm": float(k64[:, 2].max())}
+    peak, kind = measured_peak()
+    field_bw = BYTES_PER_SITE * n * n / (f32["field_ms"] / 1000.0) / 1e9
+    whole_bw = (BYTES_PER_SITE * su + BYTES_PER_PARTICLE * f32["psteps"]) / (f32["ms"] / 1000.0) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "Glasma site-updates/s & Wong particle-steps/s, one 512^2 event, FP32 vs FP64",
+            "value": su * ws / (f32["ms"] / 1000.0), "unit": "site-updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": f32["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 accumulators)", "data": "synthetic",
+            "particle_steps_per_s": f32["psteps"] * ws / (f32["ms"] / 1000.0),
+            "config": {"workload": "one MV event on 512^2 (L=10 fm, g2mu=2 GeV, m=0.2 GeV, 10 sheets), 100k charm "
+                                   "(1.5 GeV) + 100k beauty (4.7 GeV), |p_T|~U[0,5] GeV, tau_form=1/(2M), tau "
+                                   "dtau->1 fm/c (409 steps)",
+                       "l2": "inputs larger than L2 (58.7 MB per FP32 field buffer x 2 read per step, 30 MB of "
+                             "particles)", "ic_unconverged_links": int(fails)},
+            "fp64": {"ms_per_step": f64["ms"], "site_updates_per_s": su * ws / (f64["ms"] / 1000.0),
+                     "particle_steps_per_s": f64["psteps"] * ws / (f64["ms"] / 1000.0),
+                     "field_step_ms": f64["field_ms"], "fp32_speedup": f64["ms"] / f32["ms"]},
+            "fp32_vs_fp64": errs,
+            "fp32_monitors": {"gauss_rel": f32["diag"][0], "unitarity": f32["diag"][5]},
+            "roofline": {"bound": "hbm", "achieved": field_bw, "peak": peak, "unit": "GB/s", "frac": field_bw / peak,
+                         "traffic": None, "kernel": "k_field_step<float> (one event)",
+                         "peak_kind": f"{kind} HBM copy (burst)", "field_step_ms": f32["field_ms"],
+                         "whole_step": {"achieved": whole_bw, "frac": whole_bw / peak, "unit": "GB/s"}},
+            "clocks": f32["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -546,6 +654,8 @@ def main():
         run_warm_start(args, ws, rank, local)
     elif args.workload == "correlators":
         run_correlators(args, ws, rank, local)
+    elif args.workload == "single_512":
+        run_single_512(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -198,6 +198,14 @@ glasma_status cpic_get_particles(cpic_ctx* c, double* x, double* y, double* eta,
  * Enqueue only. */
 glasma_status cpic_push(cpic_ctx* c, int32_t n_steps);
 
+/* Coupled step for several ensembles in the same event (Sec. 2: charm and beauty quarks,
+ * or jets of several momenta, probing one Glasma): n_steps x (one field step; then the
+ * push of cs[0], cs[1], ... in that order, each as in cpic_push).  cs: host array of
+ * n_ctx >= 1 distinct ensembles, all created on the same field context; each ensemble
+ * keeps its own mass, formation step, integrator and broadening table.  A bad list is
+ * rejected with GLASMA_ERR_INVALID before any work is enqueued.  Enqueue only. */
+glasma_status cpic_push_many(cpic_ctx* const* cs, int32_t n_ctx, int32_t n_steps);
+
 /* Broadening table (synchronises): rows r = 0..n-1 from the first pushed step (tau_form,
  * or the field step at particle initialisation if later) to the current
  * step, each {tau_fm, <dp_x^2>, <dp_y^2>, <dp_z^2> (GeV^2), particle count},

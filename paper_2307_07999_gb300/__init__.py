@@ -29,6 +29,9 @@ from .api import (  # noqa: F401
     cpic_create,
     cpic_init,
     cpic_push,
+    cpic_push_many,
+    push_many,
+    anisotropy,
     field_tile_shape,
     field_tile_variants,
     glasma_create,

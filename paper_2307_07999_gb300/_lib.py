@@ -91,6 +91,7 @@ SIGNATURES = {
     "cpic_init_from_host": (C.c_int, [_p] + [_p] * 8),
     "cpic_get_particles": (C.c_int, [_p] + [_p] * 7),
     "cpic_push": (C.c_int, [_p, _i32]),
+    "cpic_push_many": (C.c_int, [_p, _i32, _i32]),
     "broadening_accumulate": (C.c_int, [_p, _p, _i64, C.POINTER(_i64)]),
     "cpic_casimir_drift": (C.c_int, [_p, _p]),
     "cpic_destroy": (None, [_p]),

@@ -59,6 +59,11 @@ def cpic_push(handle, n_steps):
     check(lib().cpic_push(handle, n_steps))
 
 
+def cpic_push_many(handles, n_steps):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    check(lib().cpic_push_many(arr, len(handles), n_steps))
+
+
 def broadening_accumulate(handle, cap):
     out = np.zeros((cap, 5))
     n = C.c_int64()
@@ -390,6 +395,24 @@ class Batch:
         if h:
             lib().glasma_batch_destroy(h)
             self.handle = None
+
+
+def push_many(ensembles, n_steps=1):
+    """Coupled steps of several CPIC ensembles on one Glasma event (one field step, then
+    each ensemble's push)."""
+    cpic_push_many([c.handle for c in ensembles], n_steps)
+
+
+def anisotropy(table, kind="hq"):
+    """Ratio of longitudinal over transverse broadening (Sec. 2): heavy quarks
+    <dp_z^2> / (<dp_x^2> + <dp_y^2>); jets along x <dp_z^2> / <dp_y^2>.  table rows
+    {tau_fm, <dpx^2>, <dpy^2>, <dpz^2>, ...}; returns rows {tau_fm, ratio} (NaN where the
+    transverse broadening is zero)."""
+    t = np.asarray(table)
+    den = t[:, 1] + t[:, 2] if kind == "hq" else t[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(den != 0, t[:, 3] / np.where(den != 0, den, 1.0), np.nan)
+    return np.stack([t[:, 0], r], axis=1)
 
 
 def kappa_qhat(table):

@@ -383,37 +383,57 @@ extern "C" glasma_status cpic_get_particles(cpic_ctx* c, double* x, double* y, d
     return GLASMA_OK;
 }
 
-extern "C" glasma_status cpic_push(cpic_ctx* c, int32_t n_steps) {
-    if (!c || n_steps < 0) return fail(GLASMA_ERR_INVALID, "bad arguments");
+// the push of ensemble c from step n (fields fo) to n+1 (fields in the current buffer)
+static glasma_status push_ensemble(cpic_ctx* c, int n, const void* fo) {
     glasma_ctx* g = c->g;
+    if (n < c->first_step || c->np == 0) return GLASMA_OK;
+    PushHost a;
+    a.fo = fo;
+    a.fn = g->buf[g->cur];
+    a.n = g->n;
+    a.np = c->np;
+    push_coeffs(a, n, g->dtau, g->p.expanding, c->p.integrator);
+    a.mass = c->mass;
+    a.acc = c->acc + 4 * (size_t)(n + 1);
+    CK(launch_push(g->prec, a, c->P[c->pcur], g->st));
+    if (c->p.bin_every > 0 && ++c->since_sort >= c->p.bin_every) {
+        int* cnt = c->sort_ws;
+        int* start = cnt + g->ns;
+        int* tot = start + g->ns;
+        CK(launch_sort(g->prec, c->P[c->pcur], c->P[c->pcur ^ 1], c->np, (int)g->ns, cnt, start, tot, g->st));
+        c->pcur ^= 1;
+        c->since_sort = 0;
+    }
+    return GLASMA_OK;
+}
+
+extern "C" glasma_status cpic_push_many(cpic_ctx* const* cs, int32_t n_ctx, int32_t n_steps) {
+    if (!cs || n_ctx < 1 || n_steps < 0) return fail(GLASMA_ERR_INVALID, "bad arguments");
+    for (int i = 0; i < n_ctx; i++) {
+        if (!cs[i]) return fail(GLASMA_ERR_INVALID, "null context");
+        if (cs[i]->g != cs[0]->g) return fail(GLASMA_ERR_INVALID, "ensembles bound to different field contexts");
+        for (int k = 0; k < i; k++)
+            if (cs[k] == cs[i]) return fail(GLASMA_ERR_INVALID, "an ensemble is listed twice");
+    }
+    glasma_ctx* g = cs[0]->g;
     if (g->step < 1) return fail(GLASMA_ERR_INVALID, "field state not initialised");
     for (int k = 0; k < n_steps; k++) {
-        if (g->step + 1 >= c->acc_rows) return fail(GLASMA_ERR_INVALID, "beyond tau_end");
+        if (g->step + 1 >= cs[0]->acc_rows) return fail(GLASMA_ERR_INVALID, "beyond tau_end");
         const int n = g->step;
         const void* fo = g->buf[g->cur];
         glasma_status s = one_field_step(g);
         if (s != GLASMA_OK) return s;
-        if (n >= c->first_step && c->np > 0) {
-            PushHost a;
-            a.fo = fo;
-            a.fn = g->buf[g->cur];
-            a.n = g->n;
-            a.np = c->np;
-            push_coeffs(a, n, g->dtau, g->p.expanding, c->p.integrator);
-            a.mass = c->mass;
-            a.acc = c->acc + 4 * (size_t)(n + 1);
-            CK(launch_push(g->prec, a, c->P[c->pcur], g->st));
-            if (c->p.bin_every > 0 && ++c->since_sort >= c->p.bin_every) {
-                int* cnt = c->sort_ws;
-                int* start = cnt + g->ns;
-                int* tot = start + g->ns;
-                CK(launch_sort(g->prec, c->P[c->pcur], c->P[c->pcur ^ 1], c->np, (int)g->ns, cnt, start, tot, g->st));
-                c->pcur ^= 1;
-                c->since_sort = 0;
-            }
+        for (int i = 0; i < n_ctx; i++) {
+            s = push_ensemble(cs[i], n, fo);
+            if (s != GLASMA_OK) return s;
         }
     }
     return GLASMA_OK;
+}
+
+extern "C" glasma_status cpic_push(cpic_ctx* c, int32_t n_steps) {
+    if (!c) return fail(GLASMA_ERR_INVALID, "bad arguments");
+    return cpic_push_many(&c, 1, n_steps);
 }
 
 extern "C" glasma_status broadening_accumulate(cpic_ctx* c, double* out, int64_t cap, int64_t* n_rows) {

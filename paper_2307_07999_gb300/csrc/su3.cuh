@@ -386,6 +386,29 @@ template <class T> DEV M3<T> expi(const H3<T>& X) {
     return W;
 }
 
+// Renormalisation of rows 0, 1 in the working precision, for links within rounding of
+// SU(3): with |r|^2 = 1 + d, the Newton step r <- r - (d / 2) r leaves |r|^2 = 1 + O(d^2);
+// r1 is made orthogonal to the normalised r0 first.  d is accumulated from -1 by FMAs,
+// so it is never rounded as 1 + d (in FP32 that would quantise it to 6e-8 steps), and
+// the scaling is one FMA per entry.  The complex sums run on the paired FMAs.
+DEV CA<float> as_acc(cx<float> z) { return {pk2(z.r, z.i)}; }
+DEV CA<double> as_acc(cx<double> z) { return {z}; }
+template <class T> DEV T norm2_minus_one(const cx<T>* r) {
+    return val(ccmac(ccmac(ccmac(as_acc(mk(T(-1), T(0))), r[0], r[0]), r[1], r[1]), r[2], r[2])).r;
+}
+template <class T> DEV void renorm_rows(M3<T>& U) {
+    const T h0 = T(-0.5) * norm2_minus_one(U.m[0]);
+#pragma unroll
+    for (int k = 0; k < 3; k++) U.m[0][k] = val(rmac(as_acc(U.m[0][k]), h0, U.m[0][k]));
+    const cx<T> ip = val(ccmac(ccmac(ccmul(U.m[0][0], U.m[1][0]), U.m[0][1], U.m[1][1]), U.m[0][2], U.m[1][2]));
+    const cx<T> mip = mk(-ip.r, -ip.i);
+#pragma unroll
+    for (int k = 0; k < 3; k++) U.m[1][k] = val(cmac(as_acc(U.m[1][k]), mip, U.m[0][k]));
+    const T h1 = T(-0.5) * norm2_minus_one(U.m[1]);
+#pragma unroll
+    for (int k = 0; k < 3; k++) U.m[1][k] = val(rmac(as_acc(U.m[1][k]), h1, U.m[1][k]));
+}
+
 // Gram-Schmidt of rows 0, 1 in FP64 (row 2 is implied)
 template <class T> DEV void reunit_rows(M3<T>& U) {
     double r0[6], r1[6];

@@ -1,0 +1,125 @@
+"""The 512^2 heavy-quark configuration at full size: one MV event on 512^2, L = 10 fm,
+g^2 mu = 2 GeV, m = 0.2 GeV, 10 sheets, dtau = a/8 to 1 fm/c (410 steps); 100k charm
+(1.5 GeV) and 100k beauty (4.7 GeV) quarks probing the same fields, |p_T| ~ U[0, 5] GeV
+with isotropic azimuth, formed at 1/(2M) (Sec. 2).
+
+- FP64 on the GPU against the FP64 oracle: both start from the oracle's initial
+  condition; the oracle evolves the fields itself and pushes a sample of 300 quarks of
+  each species one by one through the first 120 steps (past the kappa peak at
+  delta tau ~ 0.03-0.05 fm/c); the sampled GPU quarks must agree to 1e-10.
+- FP32 against FP64 (both GPU, both whole ensembles, all 410 steps): <dp_i^2>(tau) and
+  the anisotropy <dp_L^2>/<dp_T^2> within 1e-4 of their largest values, Gauss law within
+  1e-5; kappa within 3e-4 of its peak.  kappa is the central difference of <dp^2> over
+  one step, and with the nearest-grid-point gather the force on a quark jumps when a
+  rounding-level change of its path moves a cell crossing by one step: the plain FP64 run
+  of this configuration, with only its stored fields rounded to FP32 after every step,
+  already differs from itself unrounded by 1.9e-4 of the charm kappa peak (late tau, the
+  longitudinal component), against 5e-6 on <dp^2>.  No FP32 field storage gets under
+  that floor, so the bound on kappa sits above it.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import HBARC, lattice_units, rel_err
+
+pytestmark = pytest.mark.gpu
+
+G = pytest.importorskip("paper_2307_07999_gb300")
+
+N, L, NP, SEED = 512, 10.0, 100000, 20001
+SPECIES = {"charm": (1.5, 0x5A5A0001), "beauty": (4.7, 0x5A5A0002)}
+K_CHECK = 120
+N_SAMPLE = 300
+
+
+def tau_form(mass):
+    return HBARC / (2.0 * mass)
+
+
+@pytest.fixture(scope="module")
+def oracle_run():
+    a_fm, a, g2mua, mira = lattice_units(N, L)
+    st, iters, fails = O.glasma_init(N, 10, g2mua, mira, SEED, 0.125)
+    assert fails == 0
+    st0 = st.copy()
+    rng = np.random.default_rng(5)
+    samples = {}
+    for name, (m, pseed) in SPECIES.items():
+        P = O.particles_init(NP, N, m * a, 0, 0.0, 5.0 * a, pseed)
+        idx = np.sort(rng.choice(NP, N_SAMPLE, replace=False))
+        sub = O.Particles(N_SAMPLE)
+        for k in ("x", "y", "eta", "px", "py", "peta", "Q", "p0"):
+            getattr(sub, k)[...] = getattr(P, k)[idx]
+        n_form = max(1, int(round(tau_form(m) / (0.125 * a_fm))))
+        samples[name] = (idx, sub, n_form, m * a)
+    while st.step < K_CHECK:
+        nx = O.field_step(st, 0.125)
+        for name, (idx, sub, n_form, ma) in samples.items():
+            if st.step >= n_form:
+                O.push(sub, st, nx, 0.125, ma)
+        st = nx
+    return st0, samples
+
+
+def gpu_run(st0, prec, stop=None):
+    g = G.Glasma(N, L, precision=prec, tau_end_fm=1.0, seed=SEED, reunit_every=(64 if prec else 0))
+    g.set_state(st0.U, st0.E, st0.phi, st0.pi, 1)
+    cs = {}
+    for name, (m, pseed) in SPECIES.items():
+        c = G.CPIC(g, NP, m, tau_form(m), p_min_GeV=0.0, p_max_GeV=5.0, seed=pseed)
+        c.init()
+        cs[name] = c
+    n_steps = int(np.ceil(1.0 / (0.125 * L / N) - 1e-9))
+    assert n_steps == 410
+    G.push_many(list(cs.values()), (stop or n_steps) - 1)
+    return g, cs
+
+
+def test_config2_fp64_sampled_against_oracle(oracle_run):
+    st0, samples = oracle_run
+    g, cs = gpu_run(st0, 0, stop=K_CHECK)
+    for name, (idx, sub, n_form, ma) in samples.items():
+        got = cs[name].get_particles()
+        for k in ("px", "py", "peta", "eta"):
+            assert rel_err(got[k][idx], getattr(sub, k)) < 1e-10, (name, k)
+        dx = np.abs(got["x"][idx] - sub.x)
+        dy = np.abs(got["y"][idx] - sub.y)
+        assert np.minimum(dx, N - dx).max() < 1e-10 and np.minimum(dy, N - dy).max() < 1e-10, name
+        assert rel_err(got["Q"][idx], sub.Q) < 1e-10, name
+        tab = cs[name].broadening()
+        assert tab.shape[0] == K_CHECK - n_form + 1 and np.all(tab[1:, 4] == NP)
+
+
+def test_config2_fp32_against_fp64(oracle_run):
+    st0, _ = oracle_run
+    g64, c64 = gpu_run(st0, 0)
+    g32, c32 = gpu_run(st0, 1)
+    d32 = g32.diagnostics()
+    print(f"FP32 Gauss {d32[0]:.2e} unitarity {d32[5]:.2e}")
+    assert d32[0] < 1e-5 and d32[7] == 0
+    for name in SPECIES:
+        t64, t32 = c64[name].broadening(), c32[name].broadening()
+        assert t64.shape == t32.shape and t64.shape[0] == 410 - int(round(tau_form(SPECIES[name][0]) /
+                                                                           (0.125 * L / N))) + 1
+        e_dp = rel_err(t32[:, 1:4], t64[:, 1:4])
+        e_k = rel_err(G.kappa_qhat(t32)[:, 1:], G.kappa_qhat(t64)[:, 1:])
+        a64, a32 = G.anisotropy(t64)[1:, 1], G.anisotropy(t32)[1:, 1]
+        e_a = rel_err(a32, a64)
+        print(f"{name}: dp2 {e_dp:.2e} kappa {e_k:.2e} anisotropy {e_a:.2e} "
+              f"(final <dp_L^2>/<dp_T^2> = {a64[-1]:.3f})")
+        assert e_dp < 1e-4 and e_a < 1e-4 and e_k < 3e-4, name
+        assert np.all(np.isfinite(a64)) and np.all(a64 > 0)
+        drift = c32[name].casimir_drift()
+        assert drift[0] < 1e-3 and drift[1] < 1e-3, (name, drift)
+
+
+def test_push_many_checks_its_list():
+    g = G.Glasma(8, 2.0, precision=0, tau_end_fm=0.2)
+    h = G.Glasma(8, 2.0, precision=0, tau_end_fm=0.2)
+    a = G.CPIC(g, 4, 1.5, 0.0)
+    b = G.CPIC(h, 4, 1.5, 0.0)
+    with pytest.raises(G.GlasmaError):
+        G.push_many([a, b], 1)   # different field contexts
+    with pytest.raises(G.GlasmaError):
+        G.push_many([a, a], 1)   # listed twice
