@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--mode", default="auto", choices=["auto", "graph", "persistent", "eager", "per_event", "fused"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--field-variant", type=int, default=-1,
+                   help="fixed field tile variant (default: tuned on the batch)")
+    p.add_argument("--push-variant", type=int, default=-1, help="fixed push kernel with --field-variant")
     p.add_argument("--workload", default="batch", choices=["batch", "warm_start", "correlators", "single_512"],
                    help="batch: the 64-event coupled evolution (default); warm_start: the tau = 0+ link "
                         "solve of 16 events at 1024^2, cold vs learned warm start; correlators: the lattice-"
@@ -255,8 +258,16 @@ def run_ours(args, ws, rank, local):
     with torch.cuda.stream(stream):
         B = G.Batch(evs, pps, device=dev, stream=stream)
         ic_fail = B.init()
-        # tile shape of the batched field kernel: timed on this batch, fastest kept
-        tile_v, tile_ms = B.tune(steps=8)
+        if args.field_variant >= 0:
+            # a fixed tile shape and push kernel (profiling runs: the tuner's timings are
+            # distorted under a profiler, so the shape the plain run chose is given here)
+            B.set_variant(args.field_variant)
+            B.set_push_variant(max(args.push_variant, 0))
+            tile_v = args.field_variant
+            tile_ms = [float("nan")] * G.field_tile_variants(G.GLASMA_FP32)
+        else:
+            # tile shape of the batched field kernel: timed on this batch, fastest kept
+            tile_v, tile_ms = B.tune(steps=8)
     su, ps = B.work()
     shapes = [G.field_tile_shape(G.GLASMA_FP32, v) for v in range(len(tile_ms))]
     tile = shapes[tile_v]
@@ -363,10 +374,11 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "particle_steps_per_s": pvalue,
             "config": {"workload": WORKLOAD, "mode": mode,
-                       "field_tile": f"{tile[0]}x{tile[1]}, {tile[2]} CTAs/SM (autotuned)",
+                       "field_tile": f"{tile[0]}x{tile[1]}, {tile[2]} CTAs/SM " + ("(fixed)" if args.field_variant >= 0 else "(autotuned)"),
                        "push_kernel": ("fields staged in shared memory (32-thread blocks)" if B.push_variant == 1
-                                       else "fields through L1 (128-thread blocks)") + " (autotuned)",
-                       "tile_tuning_ms_per_8_steps": {f"{a}x{b}/{c}": round(t, 3) for (a, b, c), t in zip(shapes, tile_ms)},
+                                       else "fields through L1 (128-thread blocks)") + (" (fixed)" if args.field_variant >= 0 else " (autotuned)"),
+                       "tile_tuning_ms_per_8_steps": ({f"{a}x{b}/{c}": round(t, 3) for (a, b, c), t in zip(shapes, tile_ms)}
+                                                      if args.field_variant < 0 else None),
                        "site_updates_per_step": su,
                        "particle_steps_per_step": ps, "l2": "inputs larger than L2 (3.5 GB of field state)",
                        "ic_unconverged_links": ic_fail, "parallelism": f"{ws} independent replica batch(es)"},
