@@ -52,11 +52,11 @@ def parse():
     p.add_argument("--field-variant", type=int, default=-1,
                    help="fixed field tile variant (default: tuned on the batch)")
     p.add_argument("--push-variant", type=int, default=-1, help="fixed push kernel with --field-variant")
-    p.add_argument("--workload", default="batch", choices=["batch", "warm_start", "correlators", "single_512"],
+    p.add_argument("--workload", default="batch", choices=["batch", "warm_start", "correlators", "single_512", "scans"],
                    help="batch: the 64-event coupled evolution (default); warm_start: the tau = 0+ link "
                         "solve of 16 events at 1024^2, cold vs learned warm start; correlators: the lattice-"
                         "correlator estimators of Eqs. 4-5 on a 1024^2 event; single_512: one 512^2 event with "
-                        "100k charm + 100k beauty, FP32 and FP64")
+                        "100k charm + 100k beauty, FP32 and FP64; scans: the p_T and p_x scans of Figs. 1-2")
     return p.parse_args()
 
 
@@ -657,6 +657,92 @@ def run_single_512(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- parameter scans of Figs. 1 and 2
+def run_scans(args, ws, rank, local):
+    """The heavy-quark and jet scans of Figs. 1-2 as multi-ensemble jobs: on each of 4 MV
+    events (512^2, L = 10 fm, g2mu = 2 GeV), 4 beauty ensembles (m = 4.2 GeV as in Fig. 1,
+    |p_T| = 0, 2, 5, 10 GeV with isotropic azimuth, tau_form = 1/(2m)) and 4 quark-jet
+    ensembles (m = 1.5 GeV, p_x = 1, 2, 5, 10 GeV along x, tau_form = 0: pushed from the
+    first step after tau = 0+), 25k particles each, pushed together (cpic_push_many) in
+    FP32 to 1 fm/c.  Reports, pooled over the events: peak of the total kappa = kappa_T +
+    kappa_L (heavy quarks) or qhat = qhat_y + qhat_z (jets) and its delta tau, and the
+    anisotropy at delta tau = 0.3 fm/c.  The paper's printed values are quoted as context
+    only: its lattice parameters are not given."""
+    import torch
+
+    import paper_2307_07999_gb300 as G
+
+    torch.cuda.set_device(local)
+    n, L, NP, n_ev = 512, 10.0, 25000, 4
+    hq = [(4.2, p, HBARC_GEV_FM / (2 * 4.2)) for p in (0.0, 2.0, 5.0, 10.0)]
+    jets = [(1.5, p, 0.0) for p in (1.0, 2.0, 5.0, 10.0)]
+    stream = torch.cuda.Stream()
+    tabs = [[] for _ in range(len(hq) + len(jets))]
+    n_steps = int(math.ceil(1.0 / (0.125 * L / n) - 1e-9))
+    ms_total, psteps = 0.0, 0
+    for e in range(n_ev):
+        g = G.Glasma(n, L, precision=G.GLASMA_FP32, tau_end_fm=1.0, seed=(6 << 32) + e + 1000 * rank,
+                     reunit_every=64, stream=stream)
+        assert g.init()[0] == 0
+        cs = []
+        for k, (m, p, tf) in enumerate(hq + jets):
+            jet = k >= len(hq)
+            c = G.CPIC(g, NP, m, tf, p_min_GeV=p, p_max_GeV=p, init_kind=1 if jet else 0,
+                       seed=((6 << 32) + 100 * e + k + 1000 * rank) ^ 0x5A5A5A5A5A5A5A5A)
+            c.init()
+            cs.append(c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.push_many(cs, n_steps - 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_total += e0.elapsed_time(e1)
+        for k, c in enumerate(cs):
+            t = c.broadening()
+            tabs[k].append(t)
+            psteps += int(t[1:, 4].sum())
+        del cs, g
+
+    def pooled(ts):
+        out = ts[0].copy()
+        cnt = sum(t[:, 4] for t in ts)
+        out[:, 1:4] = sum(t[:, 1:4] * t[:, 4:5] for t in ts) / np.where(cnt > 0, cnt, 1.0)[:, None]
+        out[:, 4] = cnt
+        return out
+
+    res = {"heavy_quarks": [], "jets": []}
+    for k, (m, p, tf) in enumerate(hq + jets):
+        jet = k >= len(hq)
+        t = pooled(tabs[k])
+        kq = G.kappa_qhat(t)
+        dtau = t[:, 0] - t[0, 0]
+        tot = kq[:, 2] + kq[:, 3] if jet else kq[:, 1] + kq[:, 2] + kq[:, 3]
+        i = int(np.argmax(tot))
+        a = G.anisotropy(t, "jet" if jet else "hq")
+        j = int(np.argmin(np.abs(dtau - 0.3)))
+        entry = {"mass_GeV": m, ("p_x_GeV" if jet else "p_T_GeV"): p, "tau_form_fm": round(tf, 4),
+                 "peak_GeV2_per_fm": float(tot[i]), "peak_delta_tau_fm": float(dtau[i]),
+                 "anisotropy_at_0.3fm": float(a[j, 1]), "anisotropy_at_end": float(a[-1, 1]),
+                 "dp2_at_end_GeV2": t[-1, 1:4].tolist()}
+        res["jets" if jet else "heavy_quarks"].append(entry)
+    if rank == 0:
+        line = {
+            "metric": "parameter scans of Figs. 1-2: particle-steps/s (8 ensembles x 25k on 4 events of 512^2)",
+            "value": psteps * ws / (ms_total / 1000.0), "unit": "particle-steps/s", "n_gpus": ws, "steps": 1,
+            "warmup": 0, "ms_per_step": ms_total, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (FP64 accumulators)", "data": "synthetic",
+            "config": {"workload": "4 MV events of 512^2 (L=10 fm, g2mu=2 GeV); beauty m=4.2 GeV p_T in {0,2,5,10} "
+                                   "GeV (tau_form=1/2m), quarks m=1.5 GeV p_x in {1,2,5,10} GeV (tau_form=0); 25k "
+                                   "each, FP32 to 1 fm/c"},
+            "results": res,
+            "paper_context": {"kappa_total_peak_GeV2_per_fm": "19-22 at delta tau 0.03-0.05 fm/c (beauty, m=4.2 GeV)",
+                              "qhat_total_peak_GeV2_per_fm": "24-30 at tau 0.04 fm/c",
+                              "note": "Q_s = 2 GeV there, lattice parameters not given: qualitative only"},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -668,6 +754,8 @@ def main():
         run_correlators(args, ws, rank, local)
     elif args.workload == "single_512":
         run_single_512(args, ws, rank, local)
+    elif args.workload == "scans":
+        run_scans(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

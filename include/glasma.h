@@ -213,6 +213,27 @@ glasma_status cpic_push_many(cpic_ctx* const* cs, int32_t n_ctx, int32_t n_steps
 glasma_status broadening_accumulate(cpic_ctx* c, double* host_out, int64_t cap_rows,
                                     int64_t* n_rows);
 
+/* Checkpoint and resume of a coupled run (the paper has no counterpart: a long evolution,
+ * e.g. 820 steps of 1024^2 with millions of partons, can be stopped and continued with
+ * identical results).  A blob is a small header followed by the raw device image:
+ *   field context: the current field buffer and its step (attached correlator
+ *     estimators are not included);
+ *   particle ensemble: the particle planes (original order kept), the FP64 broadening
+ *     sums of every row, the formation step and the sorting counter.
+ * *_state_bytes: the blob size for this context (negative glasma_status on a null
+ * context).  export: host must hold that many bytes; synchronises.  import: into a
+ * context created with the same parameters (precision, lattice, dtau, tau_end,
+ * expanding; for particles also count, mass and integrator), otherwise
+ * GLASMA_ERR_INVALID and nothing is changed; synchronises.  A run continued from the
+ * blobs repeats the original bit for bit (the broadening sums to the order of their
+ * FP64 atomic additions). */
+int64_t glasma_state_bytes(const glasma_ctx* g);
+glasma_status glasma_export_state(glasma_ctx* g, void* host, int64_t bytes);
+glasma_status glasma_import_state(glasma_ctx* g, const void* host, int64_t bytes);
+int64_t cpic_state_bytes(const cpic_ctx* c);
+glasma_status cpic_export_state(cpic_ctx* c, void* host, int64_t bytes);
+glasma_status cpic_import_state(cpic_ctx* c, const void* host, int64_t bytes);
+
 /* Maximum drift of the Casimirs q2, q3 over all particles (synchronises). */
 glasma_status cpic_casimir_drift(cpic_ctx* c, double out[2]);
 

@@ -32,6 +32,7 @@ from .api import (  # noqa: F401
     cpic_push_many,
     push_many,
     anisotropy,
+    pool_broadening,
     field_tile_shape,
     field_tile_variants,
     glasma_create,

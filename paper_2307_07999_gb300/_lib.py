@@ -92,6 +92,12 @@ SIGNATURES = {
     "cpic_get_particles": (C.c_int, [_p] + [_p] * 7),
     "cpic_push": (C.c_int, [_p, _i32]),
     "cpic_push_many": (C.c_int, [_p, _i32, _i32]),
+    "glasma_state_bytes": (_i64, [_p]),
+    "glasma_export_state": (C.c_int, [_p, _p, _i64]),
+    "glasma_import_state": (C.c_int, [_p, _p, _i64]),
+    "cpic_state_bytes": (_i64, [_p]),
+    "cpic_export_state": (C.c_int, [_p, _p, _i64]),
+    "cpic_import_state": (C.c_int, [_p, _p, _i64]),
     "broadening_accumulate": (C.c_int, [_p, _p, _i64, C.POINTER(_i64)]),
     "cpic_casimir_drift": (C.c_int, [_p, _p]),
     "cpic_destroy": (None, [_p]),

@@ -105,6 +105,18 @@ class Glasma:
         E, phi, pi = (np.ascontiguousarray(a, dtype=np.float64) for a in (E, phi, pi))
         check(lib().glasma_init_from_host(self.handle, _dp(U), _dp(E), _dp(phi), _dp(pi), step))
 
+    def export_state(self):
+        """Checkpoint blob of the current fields (numpy uint8)."""
+        nb = lib().glasma_state_bytes(self.handle)
+        check(0 if nb >= 0 else nb)
+        blob = np.empty(nb, dtype=np.uint8)
+        check(lib().glasma_export_state(self.handle, blob.ctypes.data_as(C.c_void_p), nb))
+        return blob
+
+    def import_state(self, blob):
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        check(lib().glasma_import_state(self.handle, blob.ctypes.data_as(C.c_void_p), blob.size))
+
     def get_state(self):
         ns = self.n * self.n
         U = np.zeros((ns, 2, 3, 3), dtype=np.complex128)
@@ -280,6 +292,18 @@ class CPIC:
     def broadening(self):
         return broadening_accumulate(self.handle, 1 << 16)
 
+    def export_state(self):
+        """Checkpoint blob of the particles and their broadening sums (numpy uint8)."""
+        nb = lib().cpic_state_bytes(self.handle)
+        check(0 if nb >= 0 else nb)
+        blob = np.empty(nb, dtype=np.uint8)
+        check(lib().cpic_export_state(self.handle, blob.ctypes.data_as(C.c_void_p), nb))
+        return blob
+
+    def import_state(self, blob):
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        check(lib().cpic_import_state(self.handle, blob.ctypes.data_as(C.c_void_p), blob.size))
+
     def casimir_drift(self):
         out = np.zeros(2)
         check(lib().cpic_casimir_drift(self.handle, _dp(out)))
@@ -401,6 +425,32 @@ def push_many(ensembles, n_steps=1):
     """Coupled steps of several CPIC ensembles on one Glasma event (one field step, then
     each ensemble's push)."""
     cpic_push_many([c.handle for c in ensembles], n_steps)
+
+
+def pool_broadening(table, group=None):
+    """Pools the broadening tables of independent event replicas, one per rank of a
+    torch.distributed group (Sec. 2: <dp_i^2> is an average over particles and events):
+    every rank passes its table (rows {tau_fm, <dpx^2>, <dpy^2>, <dpz^2>, count} on the
+    same tau grid) and gets the count-weighted average over all ranks, with the summed
+    counts.  A host-side FP64 all-reduce of sums; the replicas exchange nothing else."""
+    import torch
+    import torch.distributed as dist
+
+    t = np.asarray(table, dtype=np.float64)
+    grid = torch.tensor([t.shape[0], t[:, 0].sum() if t.size else 0.0], dtype=torch.float64)
+    lo, hi = grid.clone(), grid.clone()
+    dist.all_reduce(lo, op=dist.ReduceOp.MIN, group=group)
+    dist.all_reduce(hi, op=dist.ReduceOp.MAX, group=group)
+    if not (torch.equal(lo, hi)):
+        raise ValueError("broadening tables of the replicas are on different tau grids")
+    w = torch.from_numpy(np.concatenate([t[:, 1:4] * t[:, 4:5], t[:, 4:5]], axis=1).copy())
+    dist.all_reduce(w, group=group)
+    w = w.numpy()
+    out = t.copy()
+    cnt = w[:, 3]
+    out[:, 1:4] = np.where(cnt[:, None] > 0, w[:, :3] / np.where(cnt > 0, cnt, 1.0)[:, None], 0.0)
+    out[:, 4] = cnt
+    return out
 
 
 def anisotropy(table, kind="hq"):

@@ -457,6 +457,119 @@ extern "C" glasma_status broadening_accumulate(cpic_ctx* c, double* out, int64_t
     return GLASMA_OK;
 }
 
+// ---------------------------------------------------------------- checkpoints
+// A checkpoint blob: this header, then the raw device image of the state (field buffer,
+// or particle planes followed by the broadening sums).  The header pins what the image
+// depends on, so a blob only loads into a context of the same shape.
+struct CkptHeader {
+    char magic[8];
+    int32_t version, prec, n, np;
+    int32_t step, first_step, since_sort, acc_rows;
+    double dtau, a_fm, mass;
+    int32_t expanding, integrator;
+    int64_t body_bytes;
+};
+static void ckpt_header(CkptHeader& h, const char* magic, const glasma_ctx* g) {
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, magic, 8);
+    h.version = 1;
+    h.prec = g->prec;
+    h.n = g->n;
+    h.dtau = g->dtau;
+    h.a_fm = g->a_fm;
+    h.expanding = g->p.expanding;
+}
+static bool ckpt_same_shape(const CkptHeader& a, const CkptHeader& b) {
+    return !memcmp(a.magic, b.magic, 8) && a.version == b.version && a.prec == b.prec && a.n == b.n && a.np == b.np &&
+           a.acc_rows == b.acc_rows && a.dtau == b.dtau && a.a_fm == b.a_fm && a.mass == b.mass &&
+           a.expanding == b.expanding && a.integrator == b.integrator && a.body_bytes == b.body_bytes;
+}
+
+extern "C" int64_t glasma_state_bytes(const glasma_ctx* g) {
+    if (!g) return GLASMA_ERR_INVALID;
+    return (int64_t)(sizeof(CkptHeader) + field_buf_bytes(&g->p));
+}
+extern "C" glasma_status glasma_export_state(glasma_ctx* g, void* host, int64_t bytes) {
+    if (!g || !host) return fail(GLASMA_ERR_INVALID, "null argument");
+    if (g->step < 0) return fail(GLASMA_ERR_INVALID, "state not initialised");
+    if (bytes < glasma_state_bytes(g)) return fail(GLASMA_ERR_NOSPACE, "host buffer smaller than glasma_state_bytes");
+    CkptHeader h;
+    ckpt_header(h, "GLSMFLD1", g);
+    h.step = g->step;
+    h.body_bytes = (int64_t)field_buf_bytes(&g->p);
+    memcpy(host, &h, sizeof(h));
+    CK(cudaMemcpyAsync((char*)host + sizeof(h), g->buf[g->cur], (size_t)h.body_bytes, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return GLASMA_OK;
+}
+extern "C" glasma_status glasma_import_state(glasma_ctx* g, const void* host, int64_t bytes) {
+    if (!g || !host) return fail(GLASMA_ERR_INVALID, "null argument");
+    if (bytes < glasma_state_bytes(g)) return fail(GLASMA_ERR_INVALID, "blob smaller than glasma_state_bytes");
+    CkptHeader want, got;
+    ckpt_header(want, "GLSMFLD1", g);
+    want.body_bytes = (int64_t)field_buf_bytes(&g->p);
+    memcpy(&got, host, sizeof(got));
+    want.step = got.step;
+    if (!ckpt_same_shape(want, got) || got.step < 0 || got.step > g->n_steps)
+        return fail(GLASMA_ERR_INVALID, "checkpoint does not match this field context");
+    CK(cudaMemcpyAsync(g->buf[0], (const char*)host + sizeof(got), (size_t)got.body_bytes, cudaMemcpyHostToDevice,
+                       g->st));
+    CK(cudaStreamSynchronize(g->st));
+    g->cur = 0;
+    g->step = got.step;
+    return GLASMA_OK;
+}
+
+static CkptHeader cpic_header(const cpic_ctx* c) {
+    CkptHeader h;
+    ckpt_header(h, "GLSMCPC1", c->g);
+    h.np = c->np;
+    h.acc_rows = c->acc_rows;
+    h.mass = c->mass;
+    h.integrator = c->p.integrator;
+    h.body_bytes = (int64_t)(part_bytes(c->np, c->g->prec) + (size_t)c->acc_rows * 4 * 8);
+    return h;
+}
+extern "C" int64_t cpic_state_bytes(const cpic_ctx* c) {
+    if (!c) return GLASMA_ERR_INVALID;
+    return (int64_t)sizeof(CkptHeader) + cpic_header(c).body_bytes;
+}
+extern "C" glasma_status cpic_export_state(cpic_ctx* c, void* host, int64_t bytes) {
+    if (!c || !host) return fail(GLASMA_ERR_INVALID, "null argument");
+    if (bytes < cpic_state_bytes(c)) return fail(GLASMA_ERR_NOSPACE, "host buffer smaller than cpic_state_bytes");
+    glasma_ctx* g = c->g;
+    CkptHeader h = cpic_header(c);
+    h.first_step = c->first_step;
+    h.since_sort = c->since_sort;
+    memcpy(host, &h, sizeof(h));
+    char* body = (char*)host + sizeof(h);
+    const size_t pb = part_bytes(c->np, g->prec);
+    if (c->np > 0) CK(cudaMemcpyAsync(body, c->P[c->pcur].cell, pb, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(body + pb, c->acc, (size_t)c->acc_rows * 4 * 8, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return GLASMA_OK;
+}
+extern "C" glasma_status cpic_import_state(cpic_ctx* c, const void* host, int64_t bytes) {
+    if (!c || !host) return fail(GLASMA_ERR_INVALID, "null argument");
+    if (bytes < cpic_state_bytes(c)) return fail(GLASMA_ERR_INVALID, "blob smaller than cpic_state_bytes");
+    glasma_ctx* g = c->g;
+    CkptHeader want = cpic_header(c), got;
+    memcpy(&got, host, sizeof(got));
+    want.first_step = got.first_step;
+    want.since_sort = got.since_sort;
+    if (!ckpt_same_shape(want, got) || got.first_step < 1 || got.first_step >= c->acc_rows || got.since_sort < 0)
+        return fail(GLASMA_ERR_INVALID, "checkpoint does not match this particle ensemble");
+    const char* body = (const char*)host + sizeof(got);
+    const size_t pb = part_bytes(c->np, g->prec);
+    if (c->np > 0) CK(cudaMemcpyAsync(c->P[0].cell, body, pb, cudaMemcpyHostToDevice, g->st));
+    CK(cudaMemcpyAsync(c->acc, body + pb, (size_t)c->acc_rows * 4 * 8, cudaMemcpyHostToDevice, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    c->pcur = 0;
+    c->first_step = got.first_step;
+    c->since_sort = got.since_sort;
+    return GLASMA_OK;
+}
+
 extern "C" glasma_status cpic_casimir_drift(cpic_ctx* c, double out[2]) {
     if (!c || !out) return fail(GLASMA_ERR_INVALID, "null argument");
     glasma_ctx* g = c->g;

@@ -123,3 +123,30 @@ def test_push_many_checks_its_list():
         G.push_many([a, b], 1)   # different field contexts
     with pytest.raises(G.GlasmaError):
         G.push_many([a, a], 1)   # listed twice
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_push_many_ensembles_do_not_interact(prec):
+    """Ensembles pushed together on one event give what each gives alone on a copy of the
+    same event: the same particles bit for bit, the same broadening tables."""
+    def run(which):
+        g = G.Glasma(40, 4.0, precision=prec, tau_end_fm=1.0, seed=31, reunit_every=(16 if prec else 0))
+        assert g.init()[0] == 0
+        spec = [(1.5, 0.02, 0, 11), (4.7, 0.01, 1, 12), (0.0, 0.0, 0, 13)]
+        cs = []
+        for k in which:
+            m, tf, integ, seed = spec[k]
+            c = G.CPIC(g, 500, m, tf, p_min_GeV=(2.0 if m == 0 else 0.0), p_max_GeV=5.0, init_kind=(1 if m == 0 else 0),
+                       seed=seed, integrator=integ)
+            c.init()
+            cs.append(c)
+        G.push_many(cs, 60)
+        return [(c.get_particles(), c.broadening()) for c in cs]
+
+    together = run([0, 1, 2])
+    for k in range(3):
+        alone = run([k])[0]
+        for key in alone[0]:
+            assert np.array_equal(alone[0][key], together[k][0][key]), (k, key)
+        assert alone[1].shape == together[k][1].shape
+        assert rel_err(alone[1][:, 1:4], together[k][1][:, 1:4]) < 1e-13
