@@ -70,6 +70,7 @@ def _declare(L):
         "o_corr_step": (None, [_i, _i, _d, _i] + [_p] * 9 + [_i, _i, _p]),
         "o_push": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p]),
         "o_push_int": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p, _i]),
+        "o_push_sub": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p, _i, _i]),
         "o_casimirs": (None, [_p, _p, _p]),
         "o_pz_lab": (_d, [_d, _d, _d, _d, _d]),
         "o_mlp_forward": (None, [_i] + [_p] * 10),
@@ -418,14 +419,14 @@ class Correlators:
         return out
 
 
-def push(P, old, new, dtau, mass, expanding=1, integrator=0):
+def push(P, old, new, dtau, mass, expanding=1, integrator=0, substeps=1):
     """One push of step old.step -> old.step+1 (old: fields before, new: after the field step);
-    integrator 0 explicit, 1 Boris."""
+    integrator 0 explicit, 1 Boris; substeps particle steps of dtau / substeps."""
     acc = rz(4)
-    lib().o_push_int(P.np, old.n, expanding, dtau, old.step, mass, _ptr(old.U), _ptr(old.E),
+    lib().o_push_sub(P.np, old.n, expanding, dtau, old.step, mass, _ptr(old.U), _ptr(old.E),
                      _ptr(new.E), _ptr(old.phi), _ptr(old.pi), _ptr(new.pi), _ptr(P.x), _ptr(P.y),
                      _ptr(P.eta), _ptr(P.px), _ptr(P.py), _ptr(P.peta), _ptr(P.Q), _ptr(P.p0),
-                     _ptr(acc), integrator)
+                     _ptr(acc), integrator, substeps)
     return acc
 
 

@@ -109,6 +109,12 @@ void o_push_int(int np, int n, int expanding, double dtau, int step, double mass
                 const double *pio, const double *pin,
                 double *x, double *y, double *eta, double *px, double *py, double *peta,
                 double *Q, const double *p0, double acc[4], int integrator);
+/* o_push_int taken as `substeps` particle steps of dtau / substeps with the fields of the step */
+void o_push_sub(int np, int n, int expanding, double dtau, int step, double mass,
+                const cplx *U, const double *Eo, const double *En, const double *phi,
+                const double *pio, const double *pin,
+                double *x, double *y, double *eta, double *px, double *py, double *peta,
+                double *Q, const double *p0, double acc[4], int integrator, int substeps);
 void o_casimirs(const double Q[8], double *q2, double *q3);
 double o_pz_lab(double mass, double px, double py, double peta, double eta);
 

@@ -235,58 +235,80 @@ static void kick(int integrator, int expanding, double dtau, double tau_n, doubl
     if (expanding) p[2] *= tau_h / tau_1;
 }
 
+void o_push_sub(int np, int n, int expanding, double dtau, int step, double mass, const cplx *U,
+                const double *Eo, const double *En, const double *phi, const double *pio,
+                const double *pin, double *x, double *y, double *eta, double *px, double *py,
+                double *peta, double *Q, const double *p0, double acc[4], int integrator, int substeps);
+
 void o_push_int(int np, int n, int expanding, double dtau, int step, double mass, const cplx *U,
                 const double *Eo, const double *En, const double *phi, const double *pio,
                 const double *pin, double *x, double *y, double *eta, double *px, double *py,
                 double *peta, double *Q, const double *p0, double acc[4], int integrator) {
-    double tau_n = step * dtau, tau_h = (step + 0.5) * dtau;
-    double te_h = expanding ? tau_h : 1.0;
+    o_push_sub(np, n, expanding, dtau, step, mass, U, Eo, En, phi, pio, pin, x, y, eta, px, py, peta, Q, p0, acc,
+               integrator, 1);
+}
+
+/* The push of one field step taken as `substeps` particle steps of h = dtau / substeps.
+ * The fields stay those of the step (gathered at the particle's current cell in every
+ * sub-step, E and D phi divided by tau_n); the sub-step k from tau_k = tau_n + k h kicks
+ * with h at tau_k, drifts with h (eta with tau_k + h/2) and rotates the colour as one
+ * step does.  The broadening terms are taken after the last sub-step. */
+void o_push_sub(int np, int n, int expanding, double dtau, int step, double mass, const cplx *U,
+                const double *Eo, const double *En, const double *phi, const double *pio,
+                const double *pin, double *x, double *y, double *eta, double *px, double *py,
+                double *peta, double *Q, const double *p0, double acc[4], int integrator, int substeps) {
+    const double tau_n = step * dtau, h = dtau / substeps;
     double sx = 0, sy = 0, sz = 0;
 #pragma omp parallel for reduction(+ : sx, sy, sz)
     for (int j = 0; j < np; j++) {
-        int cx = (int)floor(x[j]), cy = (int)floor(y[j]);
-        double F[6][8];
-        o_gather(n, tau_n, expanding, U, Eo, En, phi, pio, pin, cx, cy, F);
         double *q = Q + 8 * j;
-        double qE[3] = {dot8(q, F[0]), dot8(q, F[1]), dot8(q, F[2])};
-        double qB[3] = {dot8(q, F[3]), dot8(q, F[4]), dot8(q, F[5])};
+        double xj = x[j], yj = y[j];
         double pk[3] = {px[j], py[j], peta[j]};
-        kick(integrator, expanding, dtau, tau_n, mass, qE, qB, pk);
-        double pxn = pk[0], pyn = pk[1], pzn = pk[2];
-        double ptn = sqrt(mass * mass + pxn * pxn + pyn * pyn + pzn * pzn);
-        double iptn = ptn > 0 ? 1.0 / ptn : 0.0;
-        double xn = x[j] + dtau * pxn * iptn;
-        double yn = y[j] + dtau * pyn * iptn;
-        double deta = dtau * pzn * iptn / te_h;
-        /* color: rotation along eta at the old cell */
-        {
-            double a[8];
-            cplx W[9];
-            for (int k = 0; k < 8; k++) a[k] = -phi[8 * site(n, cx, cy) + k] * deta;
-            o_exp_i(a, W);
+        for (int k = 0; k < substeps; k++) {
+            const double tau_k = tau_n + k * h;
+            const double te_h = expanding ? tau_k + 0.5 * h : 1.0;
+            int cx = (int)floor(xj), cy = (int)floor(yj);
+            double F[6][8];
+            o_gather(n, tau_n, expanding, U, Eo, En, phi, pio, pin, cx, cy, F);
+            double qE[3] = {dot8(q, F[0]), dot8(q, F[1]), dot8(q, F[2])};
+            double qB[3] = {dot8(q, F[3]), dot8(q, F[4]), dot8(q, F[5])};
+            kick(integrator, expanding, h, tau_k, mass, qE, qB, pk);
+            double ptn = sqrt(mass * mass + pk[0] * pk[0] + pk[1] * pk[1] + pk[2] * pk[2]);
+            double iptn = ptn > 0 ? 1.0 / ptn : 0.0;
+            double xn = xj + h * pk[0] * iptn;
+            double yn = yj + h * pk[1] * iptn;
+            double deta = h * pk[2] * iptn / te_h;
+            /* color: rotation along eta at the old cell */
+            {
+                double a[8];
+                cplx W[9];
+                for (int c = 0; c < 8; c++) a[c] = -phi[8 * site(n, cx, cy) + c] * deta;
+                o_exp_i(a, W);
+                double qn[8];
+                o_conj_by(W, q, qn);
+                memcpy(q, qn, sizeof(qn));
+            }
+            int nx = (int)floor(xn), ny = (int)floor(yn);
             double qn[8];
-            o_conj_by(W, q, qn);
-            memcpy(q, qn, sizeof(qn));
+            if (nx == cx + 1) { o_transport(U + 18 * site(n, cx, cy) + 0, q, qn); memcpy(q, qn, sizeof(qn)); }
+            else if (nx == cx - 1) { o_conj_by(U + 18 * site(n, cx - 1, cy) + 0, q, qn); memcpy(q, qn, sizeof(qn)); }
+            if (ny == cy + 1) { o_transport(U + 18 * site(n, nx, cy) + 9, q, qn); memcpy(q, qn, sizeof(qn)); }
+            else if (ny == cy - 1) { o_conj_by(U + 18 * site(n, nx, cy - 1) + 9, q, qn); memcpy(q, qn, sizeof(qn)); }
+            /* periodic wrap, keeping x inside its cell */
+            if (nx < 0) { xn += n; nx += n; } else if (nx >= n) { xn -= n; nx -= n; }
+            if (ny < 0) { yn += n; ny += n; } else if (ny >= n) { yn -= n; ny -= n; }
+            if (xn < nx) xn = nx;
+            if (xn >= nx + 1) xn = nextafter((double)(nx + 1), 0.0);
+            if (yn < ny) yn = ny;
+            if (yn >= ny + 1) yn = nextafter((double)(ny + 1), 0.0);
+            xj = xn; yj = yn;
+            eta[j] += deta;
         }
-        int nx = (int)floor(xn), ny = (int)floor(yn);
-        double qn[8];
-        if (nx == cx + 1) { o_transport(U + 18 * site(n, cx, cy) + 0, q, qn); memcpy(q, qn, sizeof(qn)); }
-        else if (nx == cx - 1) { o_conj_by(U + 18 * site(n, cx - 1, cy) + 0, q, qn); memcpy(q, qn, sizeof(qn)); }
-        if (ny == cy + 1) { o_transport(U + 18 * site(n, nx, cy) + 9, q, qn); memcpy(q, qn, sizeof(qn)); }
-        else if (ny == cy - 1) { o_conj_by(U + 18 * site(n, nx, cy - 1) + 9, q, qn); memcpy(q, qn, sizeof(qn)); }
-        /* periodic wrap, keeping x inside its cell */
-        if (nx < 0) { xn += n; nx += n; } else if (nx >= n) { xn -= n; nx -= n; }
-        if (ny < 0) { yn += n; ny += n; } else if (ny >= n) { yn -= n; ny -= n; }
-        if (xn < nx) xn = nx;
-        if (xn >= nx + 1) xn = nextafter((double)(nx + 1), 0.0);
-        if (yn < ny) yn = ny;
-        if (yn >= ny + 1) yn = nextafter((double)(ny + 1), 0.0);
-        x[j] = xn; y[j] = yn;
-        eta[j] += deta;
-        px[j] = pxn; py[j] = pyn; peta[j] = pzn;
-        double pz = expanding ? o_pz_lab(mass, pxn, pyn, pzn, eta[j]) : pzn;
-        sx += pxn * pxn - p0[3 * j + 0] * p0[3 * j + 0];
-        sy += pyn * pyn - p0[3 * j + 1] * p0[3 * j + 1];
+        x[j] = xj; y[j] = yj;
+        px[j] = pk[0]; py[j] = pk[1]; peta[j] = pk[2];
+        double pz = expanding ? o_pz_lab(mass, pk[0], pk[1], pk[2], eta[j]) : pk[2];
+        sx += pk[0] * pk[0] - p0[3 * j + 0] * p0[3 * j + 0];
+        sy += pk[1] * pk[1] - p0[3 * j + 1] * p0[3 * j + 1];
         sz += pz * pz - p0[3 * j + 2] * p0[3 * j + 2];
     }
     acc[0] += sx;

@@ -385,3 +385,99 @@ def test_boris_is_gauge_invariant(expanding):
     run_int(Pg, stg, dtau, mass, m, expanding, 1)
     for k in ("px", "py", "peta", "x", "y", "eta"):
         assert np.abs(getattr(P, k) - getattr(Pg, k)).max() < 1e-11
+
+
+# ---------------------------------------------------------------- sub-cycled particle steps
+def run_sub(P, st, dtau, mass, m, expanding, integrator, substeps):
+    for _ in range(m):
+        nx = O.field_step(st, dtau, expanding)
+        O.push(P, st, nx, dtau, mass, expanding, integrator, substeps)
+        st = nx
+    return st
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_substeps_equal_finer_steps_in_static_fields(integrator):
+    """In the static box with fields that do not evolve (a uniform Cartan B_z: every
+    plaquette equal, no staple force, E = 0 so the links stay put), s sub-steps of dtau/s
+    within one field step are the same particle steps as s field steps of dtau/s
+    (cyclotron orbits crossing cells, colour carried by the links): identical to
+    rounding, for either kick."""
+    n, mass, dtau, s, m = 16, 0.5, 0.08, 4, 25
+    st = uniform_bz_state(n, k=3)[0]
+    rng = np.random.default_rng(21)
+    P = make_particles(40, n, rng, pscale=0.3, mass=mass)
+    P.set_p0(mass, expanding=0)
+    Pf = P.copy()
+    run_sub(P, st, dtau, mass, m, 0, integrator, s)
+    run_sub(Pf, st, dtau / s, mass, m * s, 0, integrator, 1)
+    for k in ("px", "py", "peta", "x", "y", "eta", "Q"):
+        assert np.abs(getattr(P, k) - getattr(Pf, k)).max() < 1e-12, k
+
+
+def test_substeps_cyclotron_error_falls_as_one_over_s():
+    """Uniform B_z, explicit kick (first order): at a fixed field step the orbit error
+    falls as 1/s with the sub-steps."""
+    n = 24
+    bz = -2 * np.sin(uniform_bz_state(n)[1] / 2)
+    mass, p0, T, dtau = 0.4, 0.3, 6.0, 0.04
+    Q0 = O.q0_cartan()
+    w = Q0[2] * bz / np.sqrt(mass ** 2 + p0 ** 2)
+    want = p0 * np.array([np.cos(w * T), -np.sin(w * T)])
+    errs = []
+    for s in (1, 4):
+        P = O.Particles(1)
+        P.x[:], P.y[:], P.px[:] = 12.3, 11.7, p0
+        P.Q[0] = Q0
+        P.set_p0(mass, expanding=0)
+        run_sub(P, uniform_bz_state(n)[0], dtau, mass, int(round(T / dtau)), 0, 0, s)
+        errs.append(np.hypot(P.px[0] - want[0], P.py[0] - want[1]) / p0)
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+@pytest.mark.parametrize("s", [1, 3, 8])
+def test_substeps_milne_free_particle(s):
+    """Zero field in Milne coordinates: with the Boris kick p_eta^ = p_eta^(tau0) tau0/tau
+    exactly for any number of sub-steps (the half-step decays telescope only if every
+    sub-step starts at its own tau_k); the explicit kick's error falls as 1/s; the
+    transverse motion is a straight line at constant speed."""
+    dtau, mass, tau0, T = 0.02, 1.0, 0.5, 1.0
+    m = int(round(T / dtau))
+    want = 0.8 * tau0 / (tau0 + T)
+    errs = {}
+    for integrator in (0, 1):
+        P = O.Particles(1)
+        P.x[:], P.px[:], P.peta[:] = 1.25, 0.3, 0.8
+        P.set_p0(mass)
+        run_sub(P, vac_state(4, step=int(round(tau0 / dtau))), dtau, mass, m, 1, integrator, s)
+        errs[integrator] = abs(P.peta[0] - want)
+        assert abs(P.px[0] - 0.3) < 1e-15 and P.py[0] == 0.0
+    assert errs[1] < 1e-14
+    P1 = O.Particles(1)
+    P1.px[:], P1.peta[:] = 0.3, 0.8
+    P1.set_p0(mass)
+    run_sub(P1, vac_state(4, step=int(round(tau0 / dtau))), dtau, mass, m, 1, 0, 1)
+    assert abs(errs[0] * s / abs(P1.peta[0] - want) - 1.0) < 0.05
+
+
+def test_substeps_are_gauge_invariant():
+    rng = np.random.default_rng(17)
+    n, dtau, mass, m = 6, 0.1, 0.6, 20
+    st = rand_fields(n, rng)
+    P = make_particles(60, n, rng, mass=mass, peta=True)
+    Om = [O.exp_i(2 * rng.standard_normal(8)) for _ in range(n * n)]
+    stg = st.copy()
+    for s in range(n * n):
+        x, y = s % n, s // n
+        for d, sp in ((0, (x + 1) % n + n * y), (1, x + n * ((y + 1) % n))):
+            stg.U[s, d] = Om[s] @ st.U[s, d] @ Om[sp].conj().T
+            stg.E[s, d] = O.conj_by(Om[s], st.E[s, d])
+        stg.phi[s] = O.conj_by(Om[s], st.phi[s])
+        stg.pi[s] = O.conj_by(Om[s], st.pi[s])
+    Pg = P.copy()
+    for j in range(P.np):
+        Pg.Q[j] = O.conj_by(Om[int(P.x[j]) + n * int(P.y[j])], P.Q[j])
+    run_sub(P, st, dtau, mass, m, 1, 1, 3)
+    run_sub(Pg, stg, dtau, mass, m, 1, 1, 3)
+    for k in ("px", "py", "peta", "x", "y", "eta"):
+        assert np.abs(getattr(P, k) - getattr(Pg, k)).max() < 1e-11
