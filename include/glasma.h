@@ -85,6 +85,11 @@ typedef struct {
                                 pre-step momentum); 1 Boris (half electric kick, norm-preserving
                                 rotation about Q.B, half electric kick; the Christoffel decay of
                                 p_eta^ applied exactly over each half step): second order */
+    int32_t substeps;        /* particle steps per field step (0 or 1: one).  s > 1: s steps of dtau/s,
+                                each gathering the fields of the field step at the particle's
+                                current cell (at most 64; a batch with such events pushes them
+                                with a kernel of its own, not the tuned variants, and rejects
+                                GLASMA_BATCH_FUSED and GLASMA_BATCH_PERSISTENT) */
     uint64_t seed;           /* Philox key of positions, momenta and Haar rotations */
 } cpic_params;
 

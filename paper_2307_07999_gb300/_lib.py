@@ -65,6 +65,7 @@ class CpicParams(C.Structure):
         ("q3", C.c_double),
         ("bin_every", C.c_int32),
         ("integrator", C.c_int32),
+        ("substeps", C.c_int32),
         ("seed", C.c_uint64),
     ]
 

@@ -40,6 +40,7 @@ template <class T> static PushArgs<T> push_args(const PushHost& a, const PartHos
     A.dtau = (T)a.dtau; A.te = (T)a.te; A.ichr = (T)a.ichr; A.teh = (T)a.teh; A.mass = (T)a.mass;
     A.expanding = a.expanding; A.acc = a.acc;
     A.boris = a.boris; A.dec0 = (T)a.dec0; A.dec1 = (T)a.dec1;
+    A.nsub = a.nsub; A.hsub = (T)a.hsub; A.tau0 = (T)a.tau0;
     return A;
 }
 size_t push_args_size(int prec) { return prec ? sizeof(PushArgs<float>) : sizeof(PushArgs<double>); }
@@ -69,21 +70,28 @@ static cudaError_t push_batched_impl(int v, const void* args, const void* items,
     const PushItem* it = (const PushItem*)items;
     if (v == 1)
         k_push_staged<T><<<(unsigned)n_items * (256 / PUSH_PPB), PUSH_PPB, push_staged_smem<T>(), st>>>(a, it);
+    else if (v == PUSH_VARIANT_SUB)
+        k_push_batched<T, 128, 3, true><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
     else
         k_push_batched<T, 128, 3><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
     return cudaGetLastError();
 }
 cudaError_t launch_push_batched(int prec, int v, const void* args, const void* items, int n_items, cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
-    if (v < 0 || v >= push_variants()) return cudaErrorInvalidValue;
+    if (v < 0 || (v >= push_variants() && v != PUSH_VARIANT_SUB)) return cudaErrorInvalidValue;
     return prec ? push_batched_impl<float>(v, args, items, n_items, st)
                 : push_batched_impl<double>(v, args, items, n_items, st);
 }
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st) {
     if (a.np <= 0) return cudaSuccess;
     const int nb = (a.np + 255) / 256;
-    if (prec) k_push<float><<<nb, 256, 0, st>>>(push_args<float>(a, P));
-    else k_push<double><<<nb, 256, 0, st>>>(push_args<double>(a, P));
+    if (a.nsub > 1) {
+        if (prec) k_push<float, true><<<nb, 256, 0, st>>>(push_args<float>(a, P));
+        else k_push<double, true><<<nb, 256, 0, st>>>(push_args<double>(a, P));
+    } else {
+        if (prec) k_push<float><<<nb, 256, 0, st>>>(push_args<float>(a, P));
+        else k_push<double><<<nb, 256, 0, st>>>(push_args<double>(a, P));
+    }
     return cudaGetLastError();
 }
 

@@ -29,6 +29,8 @@ template <class T> struct PushArgs {
     T te;          // tau_n (expanding) or 1: divides E_i and D_i phi
     T ichr;        // 1/tau_n (expanding, Christoffel term) or 0
     T teh;         // tau_{n+1/2} (expanding) or 1: eta drift
+    int nsub;      // particle steps per field step (1: one step with the coefficients above)
+    T hsub, tau0;  // nsub > 1: steps of hsub from tau0 = tau_n, coefficients per step
     T mass;
     int expanding;
     int boris;     // momentum kick: 0 explicit (first order), 1 Boris (second order)
@@ -253,8 +255,12 @@ template <class T, class V> DEV void site_fields(const V& C, T te, Al<T> E[3], A
     for (int k = 0; k < 8; k++) B[2].a[k] = -T(0.25) * (acc.a[k] + t2.a[k] + t3.a[k] + t4.a[k]);
 }
 
-// one particle: gather, kick, drift, color transport; returns its broadening terms
-template <class T, class S, bool CG = false>
+// one particle: gather, kick, drift, color transport; returns its broadening terms.
+// SUB: the step is taken as A.nsub particle steps of A.hsub, each gathering the step's
+// fields at the particle's current cell (the source must serve any cell: GlobalSrc).
+// Without SUB the loop runs once with the host's coefficients (the kernels of the
+// default path are compiled without it: the loop's carried state costs registers).
+template <class T, class S, bool CG = false, bool SUB = false>
 DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, double& sy, double& sz, double& sc) {
     const PartSoA<T>& P = A.P;
     const int n = A.n;
@@ -263,80 +269,104 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
     Al<T> q;
 #pragma unroll
     for (int a = 0; a < 8; a++) q.a[a] = CG ? __ldcg(P.Q + (size_t)a * P.qs + j) : P.Q[(size_t)a * P.qs + j];
-    T qE[3], qB[3];
-    const auto C = F.view(cx, cy);
-    gather_qf_view(C, A.te, q, qE, qB);
     const T p0x = P.p0x[j], p0y = P.p0y[j];  // constant during a run
     T dpx = CG ? __ldcg(P.dpx + j) : P.dpx[j], dpy = CG ? __ldcg(P.dpy + j) : P.dpy[j];
     T pz = CG ? __ldcg(P.peta + j) : P.peta[j];
+    T ox, oy, eta;
     const T m2 = A.mass * A.mass;
-    T px = p0x + dpx, py = p0y + dpy;
-    if (!A.boris) {
-        // explicit: p += dtau [Q.E + (p / p^tau) x Q.B] - dtau p_eta^ / tau_n e_eta
-        const T pt = sqrt(m2 + px * px + py * py + pz * pz);
-        const T ipt = pt > T(0) ? T(1) / pt : T(0);
-        const T fx = qE[0] + (py * qB[2] - pz * qB[1]) * ipt;
-        const T fy = qE[1] + (pz * qB[0] - px * qB[2]) * ipt;
-        const T fz = qE[2] + (px * qB[1] - py * qB[0]) * ipt - pz * A.ichr;
-        dpx += A.dtau * fx;
-        dpy += A.dtau * fy;
-        pz += A.dtau * fz;
-    } else {
-        // Boris (1970): the Christoffel decay of p_eta^ over the first half step (exact for
-        // a free particle), half electric kick, rotation about Q.B by the angle of
-        // t = (dtau/2) Q.B / p^tau (|p| unchanged), half electric kick, decay over the
-        // second half step.  The transverse change is accumulated into dp, so FP32
-        // round-off stays relative to the change.
-        const T h = T(0.5) * A.dtau;
-        pz *= A.dec0;
-        const T mx = px + h * qE[0], my = py + h * qE[1], mz = pz + h * qE[2];
-        const T g = sqrt(m2 + mx * mx + my * my + mz * mz);
-        const T ig = g > T(0) ? h / g : T(0);
-        const T tx = qB[0] * ig, ty = qB[1] * ig, tz = qB[2] * ig;
-        const T ux = mx + (my * tz - mz * ty), uy = my + (mz * tx - mx * tz), uz = mz + (mx * ty - my * tx);
-        const T sf = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
-        dpx += A.dtau * qE[0] + sf * (uy * tz - uz * ty);
-        dpy += A.dtau * qE[1] + sf * (uz * tx - ux * tz);
-        pz = (mz + sf * (ux * ty - uy * tx) + h * qE[2]) * A.dec1;
-    }
-    px = p0x + dpx;
-    py = p0y + dpy;
-    const T ptn = sqrt(m2 + px * px + py * py + pz * pz);
-    const T iptn = ptn > T(0) ? T(1) / ptn : T(0);
-    T ox = (CG ? __ldcg(P.ox + j) : P.ox[j]) + A.dtau * px * iptn;
-    T oy = (CG ? __ldcg(P.oy + j) : P.oy[j]) + A.dtau * py * iptn;
-    const T deta = A.dtau * pz * iptn / A.teh;
-    // color: rotation along eta at the old cell, then across the x face, then the y face
-    {
-        Al<T> e;
-        const Al<T> ph = C.phi(0, 0);
+    T px, py, ptn;
+    const int nsub = SUB ? A.nsub : 1;
+    for (int k = 0; k < nsub; k++) {
+        T h = A.dtau, ichr = A.ichr, teh = A.teh, dec0 = A.dec0, dec1 = A.dec1;
+        if (SUB && nsub > 1) {
+            h = A.hsub;
+            if (A.expanding) {
+                const T tk = A.tau0 + T(k) * h, tm = tk + T(0.5) * h;
+                ichr = T(1) / tk;
+                teh = tm;
+                dec0 = tk / tm;
+                dec1 = tm / (tk + h);
+            }
+        }
+        T qE[3], qB[3];
+        const auto C = F.view(cx, cy);
+        gather_qf_view(C, A.te, q, qE, qB);
+        px = p0x + dpx;
+        py = p0y + dpy;
+        if (!A.boris) {
+            // explicit: p += h [Q.E + (p / p^tau) x Q.B] - h p_eta^ / tau e_eta
+            const T pt = sqrt(m2 + px * px + py * py + pz * pz);
+            const T ipt = pt > T(0) ? T(1) / pt : T(0);
+            const T fx = qE[0] + (py * qB[2] - pz * qB[1]) * ipt;
+            const T fy = qE[1] + (pz * qB[0] - px * qB[2]) * ipt;
+            const T fz = qE[2] + (px * qB[1] - py * qB[0]) * ipt - pz * ichr;
+            dpx += h * fx;
+            dpy += h * fy;
+            pz += h * fz;
+        } else {
+            // Boris (1970): the Christoffel decay of p_eta^ over the first half step (exact for
+            // a free particle), half electric kick, rotation about Q.B by the angle of
+            // t = (h/2) Q.B / p^tau (|p| unchanged), half electric kick, decay over the second
+            // half step.  The transverse change is accumulated into dp, so FP32 round-off
+            // stays relative to the change.
+            const T hh = T(0.5) * h;
+            pz *= dec0;
+            const T mx = px + hh * qE[0], my = py + hh * qE[1], mz = pz + hh * qE[2];
+            const T g = sqrt(m2 + mx * mx + my * my + mz * mz);
+            const T ig = g > T(0) ? hh / g : T(0);
+            const T tx = qB[0] * ig, ty = qB[1] * ig, tz = qB[2] * ig;
+            const T ux = mx + (my * tz - mz * ty), uy = my + (mz * tx - mx * tz), uz = mz + (mx * ty - my * tx);
+            const T sf = T(2) / (T(1) + tx * tx + ty * ty + tz * tz);
+            dpx += h * qE[0] + sf * (uy * tz - uz * ty);
+            dpy += h * qE[1] + sf * (uz * tx - ux * tz);
+            pz = (mz + sf * (ux * ty - uy * tx) + hh * qE[2]) * dec1;
+        }
+        px = p0x + dpx;
+        py = p0y + dpy;
+        ptn = sqrt(m2 + px * px + py * py + pz * pz);
+        const T iptn = ptn > T(0) ? T(1) / ptn : T(0);
+        if (k == 0) {  // loaded here, after the gather, to keep them out of its live range
+            ox = CG ? __ldcg(P.ox + j) : P.ox[j];
+            oy = CG ? __ldcg(P.oy + j) : P.oy[j];
+            eta = CG ? __ldcg(P.eta + j) : P.eta[j];
+        }
+        ox += h * px * iptn;
+        oy += h * py * iptn;
+        const T deta = h * pz * iptn / teh;
+        // color: rotation along eta at the old cell, then across the x face, then the y face
+        {
+            Al<T> e;
+            const Al<T> ph = C.phi(0, 0);
 #pragma unroll
-        for (int a = 0; a < 8; a++) e.a[a] = -deta * ph.a[a];
-        q = alg(conj_by(expi(herm(e)), herm(q)));
+            for (int a = 0; a < 8; a++) e.a[a] = -deta * ph.a[a];
+            q = alg(conj_by(expi(herm(e)), herm(q)));
+        }
+        int nx = cx, ny = cy, ddx = 0;
+        if (ox >= T(1)) {
+            q = transport_alg(C.link(0, 0, 0), q);
+            ox -= T(1);
+            nx = cx == n - 1 ? 0 : cx + 1;
+            ddx = 1;
+        } else if (ox < T(0)) {
+            nx = cx == 0 ? n - 1 : cx - 1;
+            ddx = -1;
+            q = conj_alg(C.link(0, -1, 0), q);
+            ox = clamp_below_one(ox + T(1));
+        }
+        if (oy >= T(1)) {
+            q = transport_alg(C.link(1, ddx, 0), q);
+            oy -= T(1);
+            ny = cy == n - 1 ? 0 : cy + 1;
+        } else if (oy < T(0)) {
+            ny = cy == 0 ? n - 1 : cy - 1;
+            q = conj_alg(C.link(1, ddx, -1), q);
+            oy = clamp_below_one(oy + T(1));
+        }
+        cx = nx;
+        cy = ny;
+        eta += deta;
     }
-    int nx = cx, ny = cy, ddx = 0;
-    if (ox >= T(1)) {
-        q = transport_alg(C.link(0, 0, 0), q);
-        ox -= T(1);
-        nx = cx == n - 1 ? 0 : cx + 1;
-        ddx = 1;
-    } else if (ox < T(0)) {
-        nx = cx == 0 ? n - 1 : cx - 1;
-        ddx = -1;
-        q = conj_alg(C.link(0, -1, 0), q);
-        ox = clamp_below_one(ox + T(1));
-    }
-    if (oy >= T(1)) {
-        q = transport_alg(C.link(1, ddx, 0), q);
-        oy -= T(1);
-        ny = cy == n - 1 ? 0 : cy + 1;
-    } else if (oy < T(0)) {
-        ny = cy == 0 ? n - 1 : cy - 1;
-        q = conj_alg(C.link(1, ddx, -1), q);
-        oy = clamp_below_one(oy + T(1));
-    }
-    const T eta = (CG ? __ldcg(P.eta + j) : P.eta[j]) + deta;
-    P.cell[j] = nx + n * ny;
+    P.cell[j] = cx + n * cy;
     P.ox[j] = ox;
     P.oy[j] = oy;
     P.eta[j] = eta;
@@ -355,10 +385,10 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
     sc = 1.0;
 }
 
-template <class T, bool CG = false>
+template <class T, bool CG = false, bool SUB = false>
 DEV void push_one(const PushArgs<T>& A, int j, double& sx, double& sy, double& sz, double& sc) {
     GlobalSrc<T, CG> F{A.fo, A.fn, A.n, (size_t)A.n * A.n};
-    push_one_src<T, GlobalSrc<T, CG>, CG>(A, F, j, sx, sy, sz, sc);
+    push_one_src<T, GlobalSrc<T, CG>, CG, SUB>(A, F, j, sx, sy, sz, sc);
 }
 
 // warp -> block -> one FP64 atomic per block and term (any block shape, at most 256
@@ -384,11 +414,11 @@ DEV void block_acc4(double sx, double sy, double sz, double sc, double* acc) {
     }
 }
 
-template <class T>
+template <class T, bool SUB = false>
 __global__ void __launch_bounds__(256) k_push(PushArgs<T> A) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
-    if (j < A.np) push_one(A, j, sx, sy, sz, sc);
+    if (j < A.np) push_one<T, false, SUB>(A, j, sx, sy, sz, sc);
     block_acc4(sx, sy, sz, sc, A.acc);
 }
 
@@ -396,7 +426,7 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<T> A) {
 // of NT threads; args[ev] of this step (acc == nullptr marks an event whose particles
 // are not pushed at this step)
 struct PushItem { int ev, j0; };
-template <class T, int NT, int MINB>
+template <class T, int NT, int MINB, bool MULTI = false>
 __global__ void __launch_bounds__(NT, MINB) k_push_batched(const PushArgs<T>* __restrict__ args,
                                                            const PushItem* __restrict__ items) {
     static_assert(256 % NT == 0 && NT % 32 == 0, "push block");
@@ -406,7 +436,7 @@ __global__ void __launch_bounds__(NT, MINB) k_push_batched(const PushArgs<T>* __
     if (A.acc == nullptr) return;
     const int j = it.j0 + (int)(blockIdx.x % SUB) * NT + threadIdx.x;
     double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
-    if (j < A.np) push_one(A, j, sx, sy, sz, sc);
+    if (j < A.np) push_one<T, false, MULTI>(A, j, sx, sy, sz, sc);
     block_acc4(sx, sy, sz, sc, A.acc);
 }
 
