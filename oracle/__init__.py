@@ -71,6 +71,8 @@ def _declare(L):
         "o_push": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p]),
         "o_push_int": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p, _i]),
         "o_push_sub": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p, _i, _i]),
+        "o_push_ext": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p, _i, _i, _i]),
+        "o_gather_cic": (None, [_i, _d, _i] + [_p] * 6 + [_i, _i, _d, _d, _p]),
         "o_casimirs": (None, [_p, _p, _p]),
         "o_pz_lab": (_d, [_d, _d, _d, _d, _d]),
         "o_mlp_forward": (None, [_i] + [_p] * 10),
@@ -419,15 +421,26 @@ class Correlators:
         return out
 
 
-def push(P, old, new, dtau, mass, expanding=1, integrator=0, substeps=1):
+def push(P, old, new, dtau, mass, expanding=1, integrator=0, substeps=1, interp=0):
     """One push of step old.step -> old.step+1 (old: fields before, new: after the field step);
-    integrator 0 explicit, 1 Boris; substeps particle steps of dtau / substeps."""
+    integrator 0 explicit, 1 Boris; substeps particle steps of dtau / substeps; interp 0
+    nearest grid point, 1 cloud in cell."""
     acc = rz(4)
-    lib().o_push_sub(P.np, old.n, expanding, dtau, old.step, mass, _ptr(old.U), _ptr(old.E),
+    lib().o_push_ext(P.np, old.n, expanding, dtau, old.step, mass, _ptr(old.U), _ptr(old.E),
                      _ptr(new.E), _ptr(old.phi), _ptr(old.pi), _ptr(new.pi), _ptr(P.x), _ptr(P.y),
                      _ptr(P.eta), _ptr(P.px), _ptr(P.py), _ptr(P.peta), _ptr(P.Q), _ptr(P.p0),
-                     _ptr(acc), integrator, substeps)
+                     _ptr(acc), integrator, substeps, interp)
     return acc
+
+
+def gather_cic(old, new, cx, cy, ox, oy, dtau, expanding=1):
+    """Cloud-in-cell (Ex, Ey, Ez, Bx, By, Bz) for offsets (ox, oy) in cell (cx, cy), in the
+    frame of site (cx, cy), for the push of step old.step."""
+    F = rz(6, 8)
+    tau = old.step * dtau
+    lib().o_gather_cic(old.n, tau, expanding, _ptr(old.U), _ptr(old.E), _ptr(new.E), _ptr(old.phi),
+                       _ptr(old.pi), _ptr(new.pi), cx, cy, ox, oy, _ptr(F))
+    return F
 
 
 def casimirs(Q):

@@ -109,6 +109,16 @@ void o_push_int(int np, int n, int expanding, double dtau, int step, double mass
                 const double *pio, const double *pin,
                 double *x, double *y, double *eta, double *px, double *py, double *peta,
                 double *Q, const double *p0, double acc[4], int integrator);
+/* cloud-in-cell gather: site-centred fields of c, c+x, c+y, c+x+y transported to c, bilinear weights */
+void o_gather_cic(int n, double tau, int expanding, const cplx *U, const double *Eo, const double *En,
+                  const double *phi, const double *pio, const double *pin, int cx, int cy, double ox,
+                  double oy, double F[6][8]);
+/* o_push_sub with interp: 0 nearest grid point, 1 cloud in cell */
+void o_push_ext(int np, int n, int expanding, double dtau, int step, double mass,
+                const cplx *U, const double *Eo, const double *En, const double *phi,
+                const double *pio, const double *pin,
+                double *x, double *y, double *eta, double *px, double *py, double *peta,
+                double *Q, const double *p0, double acc[4], int integrator, int substeps, int interp);
 /* o_push_int taken as `substeps` particle steps of dtau / substeps with the fields of the step */
 void o_push_sub(int np, int n, int expanding, double dtau, int step, double mass,
                 const cplx *U, const double *Eo, const double *En, const double *phi,

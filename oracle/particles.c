@@ -187,6 +187,38 @@ void o_gather(int n, double tau, int expanding, const cplx *U, const double *Eo,
     for (int a = 0; a < 8; a++) F[5][a] = -0.25 * fxy[a];  /* B_z = -F_xy */
 }
 
+/* Cloud-in-cell gather (reading; the paper does not give the interpolation): the
+ * site-centred fields of the four sites around the particle, c, c+x, c+y, c+x+y, each
+ * parallel transported into the frame of c where Q lives (c+x by U_x(c), c+y by U_y(c),
+ * c+x+y by U_y(c+x) and then U_x(c): x before y, as the colour crossings), weighted
+ * bilinearly with the particle's offsets (ox, oy) in the cell. */
+void o_gather_cic(int n, double tau, int expanding, const cplx *U, const double *Eo, const double *En,
+                  const double *phi, const double *pio, const double *pin, int cx, int cy, double ox,
+                  double oy, double F[6][8]) {
+    const double w[4] = {(1 - ox) * (1 - oy), ox * (1 - oy), (1 - ox) * oy, ox * oy};
+    const int sx[4] = {cx, cx + 1, cx, cx + 1}, sy[4] = {cy, cy, cy + 1, cy + 1};
+    for (int i = 0; i < 6; i++)
+        for (int a = 0; a < 8; a++) F[i][a] = 0.0;
+    for (int k = 0; k < 4; k++) {
+        double Fk[6][8];
+        o_gather(n, tau, expanding, U, Eo, En, phi, pio, pin, sx[k], sy[k], Fk);
+        for (int i = 0; i < 6; i++) {
+            double t[8];
+            if (k == 3) { /* c+x+y -> c+x -> c */
+                o_conj_by(U + 18 * site(n, cx + 1, cy) + 9, Fk[i], t);
+                o_conj_by(U + 18 * site(n, cx, cy) + 0, t, Fk[i]);
+            } else if (k == 1) {
+                o_conj_by(U + 18 * site(n, cx, cy) + 0, Fk[i], t);
+                memcpy(Fk[i], t, sizeof(t));
+            } else if (k == 2) {
+                o_conj_by(U + 18 * site(n, cx, cy) + 9, Fk[i], t);
+                memcpy(Fk[i], t, sizeof(t));
+            }
+            for (int a = 0; a < 8; a++) F[i][a] += w[k] * Fk[i][a];
+        }
+    }
+}
+
 double o_pz_lab(double mass, double px, double py, double peta, double eta) {
     double pt = sqrt(mass * mass + px * px + py * py + peta * peta);
     return pt * sinh(eta) + peta * cosh(eta);
@@ -235,17 +267,18 @@ static void kick(int integrator, int expanding, double dtau, double tau_n, doubl
     if (expanding) p[2] *= tau_h / tau_1;
 }
 
-void o_push_sub(int np, int n, int expanding, double dtau, int step, double mass, const cplx *U,
+void o_push_ext(int np, int n, int expanding, double dtau, int step, double mass, const cplx *U,
                 const double *Eo, const double *En, const double *phi, const double *pio,
                 const double *pin, double *x, double *y, double *eta, double *px, double *py,
-                double *peta, double *Q, const double *p0, double acc[4], int integrator, int substeps);
+                double *peta, double *Q, const double *p0, double acc[4], int integrator, int substeps,
+                int interp);
 
 void o_push_int(int np, int n, int expanding, double dtau, int step, double mass, const cplx *U,
                 const double *Eo, const double *En, const double *phi, const double *pio,
                 const double *pin, double *x, double *y, double *eta, double *px, double *py,
                 double *peta, double *Q, const double *p0, double acc[4], int integrator) {
-    o_push_sub(np, n, expanding, dtau, step, mass, U, Eo, En, phi, pio, pin, x, y, eta, px, py, peta, Q, p0, acc,
-               integrator, 1);
+    o_push_ext(np, n, expanding, dtau, step, mass, U, Eo, En, phi, pio, pin, x, y, eta, px, py, peta, Q, p0, acc,
+               integrator, 1, 0);
 }
 
 /* The push of one field step taken as `substeps` particle steps of h = dtau / substeps.
@@ -257,6 +290,17 @@ void o_push_sub(int np, int n, int expanding, double dtau, int step, double mass
                 const double *Eo, const double *En, const double *phi, const double *pio,
                 const double *pin, double *x, double *y, double *eta, double *px, double *py,
                 double *peta, double *Q, const double *p0, double acc[4], int integrator, int substeps) {
+    o_push_ext(np, n, expanding, dtau, step, mass, U, Eo, En, phi, pio, pin, x, y, eta, px, py, peta, Q, p0, acc,
+               integrator, substeps, 0);
+}
+
+/* o_push_sub with the gather chosen by interp: 0 nearest grid point (the site at the
+ * lower-left corner of the particle's cell), 1 cloud in cell (o_gather_cic). */
+void o_push_ext(int np, int n, int expanding, double dtau, int step, double mass, const cplx *U,
+                const double *Eo, const double *En, const double *phi, const double *pio,
+                const double *pin, double *x, double *y, double *eta, double *px, double *py,
+                double *peta, double *Q, const double *p0, double acc[4], int integrator, int substeps,
+                int interp) {
     const double tau_n = step * dtau, h = dtau / substeps;
     double sx = 0, sy = 0, sz = 0;
 #pragma omp parallel for reduction(+ : sx, sy, sz)
@@ -269,7 +313,10 @@ void o_push_sub(int np, int n, int expanding, double dtau, int step, double mass
             const double te_h = expanding ? tau_k + 0.5 * h : 1.0;
             int cx = (int)floor(xj), cy = (int)floor(yj);
             double F[6][8];
-            o_gather(n, tau_n, expanding, U, Eo, En, phi, pio, pin, cx, cy, F);
+            if (interp)
+                o_gather_cic(n, tau_n, expanding, U, Eo, En, phi, pio, pin, cx, cy, xj - cx, yj - cy, F);
+            else
+                o_gather(n, tau_n, expanding, U, Eo, En, phi, pio, pin, cx, cy, F);
             double qE[3] = {dot8(q, F[0]), dot8(q, F[1]), dot8(q, F[2])};
             double qB[3] = {dot8(q, F[3]), dot8(q, F[4]), dot8(q, F[5])};
             kick(integrator, expanding, h, tau_k, mass, qE, qB, pk);

@@ -481,3 +481,125 @@ def test_substeps_are_gauge_invariant():
     run_sub(Pg, stg, dtau, mass, m, 1, 1, 3)
     for k in ("px", "py", "peta", "x", "y", "eta"):
         assert np.abs(getattr(P, k) - getattr(Pg, k)).max() < 1e-11
+
+
+# ---------------------------------------------------------------- cloud-in-cell gather
+def test_cic_exact_for_affine_abelian_fields():
+    """Links at unity, E_x, E_y, pi affine in (x, y) away from the periodic seam: the site
+    average of the link fields is affine again (E_x(X, Y) = e0 + g_x (X - 1/2) + g_y Y, E_y
+    with Y - 1/2), and bilinear weights reproduce an affine function exactly, so the
+    cloud-in-cell field at the particle equals the closed form at its position; the
+    nearest-grid-point field is the value at the cell's corner site."""
+    n = 16
+    rng = np.random.default_rng(31)
+    st = vac_state(n, step=3)
+    e0, gx, gy = rng.standard_normal((3, 3, 8))
+    for s in range(n * n):
+        X, Y = s % n, s // n
+        st.E[s, 0] = e0[0] + gx[0] * X + gy[0] * Y
+        st.E[s, 1] = e0[1] + gx[1] * X + gy[1] * Y
+        st.pi[s] = e0[2] + gx[2] * X + gy[2] * Y
+    for _ in range(20):
+        x, y = rng.uniform(3, n - 4, 2)
+        cx, cy = int(x), int(y)
+        F = O.gather_cic(st, st, cx, cy, x - cx, y - cy, 0.1, expanding=0)
+        assert np.abs(F[0] - (e0[0] + gx[0] * (x - 0.5) + gy[0] * y)).max() < 1e-12
+        assert np.abs(F[1] - (e0[1] + gx[1] * x + gy[1] * (y - 0.5))).max() < 1e-12
+        assert np.abs(F[2] - (e0[2] + gx[2] * x + gy[2] * y)).max() < 1e-12
+        assert np.abs(F[3:]).max() < 1e-14
+        G0 = O.gather(st, st, cx, cy, 0.1, expanding=0)
+        assert np.abs(G0[0] - (e0[0] + gx[0] * (cx - 0.5) + gy[0] * cy)).max() < 1e-12
+
+
+def test_cic_pure_gauge_of_uniform_fields_is_uniform():
+    """A gauge transform of uniform fields (U_i(x) = W(x) W(x+i)^dag, every field
+    W(x) F0 W(x)^dag): every site's fields carried to the cell's site are W(c) F0 W(c)^dag,
+    so the cloud-in-cell gather equals the nearest-grid-point one at any offset.  This fixes
+    the direction of every transport, the diagonal site's path included."""
+    n = 8
+    rng = np.random.default_rng(41)
+    Wg = [O.exp_i(1.5 * rng.standard_normal(8)) for _ in range(n * n)]
+    Ex, Ey, Pz, Ph = rng.standard_normal((4, 8))
+    st = vac_state(n, step=3)
+    for s in range(n * n):
+        X, Y = s % n, s // n
+        for d, sp in ((0, (X + 1) % n + n * Y), (1, X + n * ((Y + 1) % n))):
+            st.U[s, d] = Wg[s] @ Wg[sp].conj().T
+        st.E[s, 0] = O.conj_by(Wg[s], Ex)
+        st.E[s, 1] = O.conj_by(Wg[s], Ey)
+        st.pi[s] = O.conj_by(Wg[s], Pz)
+        st.phi[s] = O.conj_by(Wg[s], Ph)
+    for _ in range(10):
+        cx, cy = rng.integers(0, n, 2)
+        ox, oy = rng.uniform(0, 1, 2)
+        F = O.gather_cic(st, st, cx, cy, ox, oy, 0.1, expanding=0)
+        G0 = O.gather(st, st, cx, cy, 0.1, expanding=0)
+        assert np.abs(F - G0).max() < 1e-12
+        c = cx + n * cy
+        assert np.abs(F[0] - O.conj_by(Wg[c], Ex)).max() < 1e-12
+
+
+def test_cic_force_continuous_across_faces():
+    """Random non-abelian fields: crossing an x face the contracted force is continuous
+    (the charge is carried across by the same link that carries the fields), while the
+    nearest-grid-point force jumps; crossing a y face the force jumps only by the
+    plaquette holonomy of the diagonal site's two paths, a second-order amount that falls
+    fourfold when the fields are halved."""
+    n = 8
+    rng = np.random.default_rng(51)
+
+    def fields(scale):
+        r = np.random.default_rng(52)
+        st = O.State(n, step=3)
+        for s in range(n * n):
+            for d in range(2):
+                st.U[s, d] = O.exp_i(scale * r.standard_normal(8))
+        st.E[...] = scale * r.standard_normal((n * n, 2, 8))
+        st.phi[...] = scale * r.standard_normal((n * n, 8))
+        st.pi[...] = scale * r.standard_normal((n * n, 8))
+        return st
+
+    Q = O.conj_by(O.haar(rng.standard_normal(18)), O.q0_cartan())
+    st = fields(0.3)
+    cx, cy, oy, eps = 3, 4, 0.37, 1e-9
+    before = O.gather_cic(st, st, cx, cy, 1 - eps, oy, 0.1, expanding=0) @ Q
+    Qn = O.transport(st.U[cx + n * cy, 0], Q)
+    after = O.gather_cic(st, st, cx + 1, cy, 0.0, oy, 0.1, expanding=0) @ Qn
+    assert np.abs(before - after).max() < 1e-7
+    ngp_jump = np.abs(O.gather(st, st, cx, cy, 0.1, 0) @ Q - O.gather(st, st, cx + 1, cy, 0.1, 0) @ Qn).max()
+    assert ngp_jump > 1e-2
+    jumps = []
+    for scale in (0.2, 0.1):
+        st = fields(scale)
+        ox = 0.6
+        b = O.gather_cic(st, st, cx, cy, ox, 1 - eps, 0.1, expanding=0) @ Q
+        Qn = O.transport(st.U[cx + n * cy, 1], Q)
+        a = O.gather_cic(st, st, cx, cy + 1, ox, 0.0, 0.1, expanding=0) @ Qn
+        jumps.append(np.abs(b - a).max())
+    assert 3.0 < jumps[0] / jumps[1] < 5.5, jumps
+
+
+def test_cic_push_is_gauge_invariant():
+    rng = np.random.default_rng(61)
+    n, dtau, mass, m = 6, 0.1, 0.6, 20
+    st = rand_fields(n, rng)
+    P = make_particles(60, n, rng, mass=mass, peta=True)
+    Om = [O.exp_i(2 * rng.standard_normal(8)) for _ in range(n * n)]
+    stg = st.copy()
+    for s in range(n * n):
+        x, y = s % n, s // n
+        for d, sp in ((0, (x + 1) % n + n * y), (1, x + n * ((y + 1) % n))):
+            stg.U[s, d] = Om[s] @ st.U[s, d] @ Om[sp].conj().T
+            stg.E[s, d] = O.conj_by(Om[s], st.E[s, d])
+        stg.phi[s] = O.conj_by(Om[s], st.phi[s])
+        stg.pi[s] = O.conj_by(Om[s], st.pi[s])
+    Pg = P.copy()
+    for j in range(P.np):
+        Pg.Q[j] = O.conj_by(Om[int(P.x[j]) + n * int(P.y[j])], P.Q[j])
+    for _ in range(m):
+        nx, nxg = O.field_step(st, dtau, 1), O.field_step(stg, dtau, 1)
+        O.push(P, st, nx, dtau, mass, 1, 1, 2, 1)
+        O.push(Pg, stg, nxg, dtau, mass, 1, 1, 2, 1)
+        st, stg = nx, nxg
+    for k in ("px", "py", "peta", "x", "y", "eta"):
+        assert np.abs(getattr(P, k) - getattr(Pg, k)).max() < 1e-11
