@@ -90,6 +90,10 @@ typedef struct {
                                 current cell (at most 64; a batch with such events pushes them
                                 with a kernel of its own, not the tuned variants, and rejects
                                 GLASMA_BATCH_FUSED and GLASMA_BATCH_PERSISTENT) */
+    int32_t interp;          /* field gather: 0 nearest grid point (the site at the lower-left corner of
+                                the particle's cell); 1 cloud in cell (the four sites around the
+                                particle, their fields carried to that site by the links, x before
+                                y, bilinear weights; batches as for substeps > 1) */
     uint64_t seed;           /* Philox key of positions, momenta and Haar rotations */
 } cpic_params;
 

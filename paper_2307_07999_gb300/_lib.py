@@ -66,6 +66,7 @@ class CpicParams(C.Structure):
         ("bin_every", C.c_int32),
         ("integrator", C.c_int32),
         ("substeps", C.c_int32),
+        ("interp", C.c_int32),
         ("seed", C.c_uint64),
     ]
 

@@ -263,10 +263,10 @@ class CPIC:
     """A particle ensemble bound to a Glasma context."""
 
     def __init__(self, glasma, n_particles, mass_GeV, tau_form_fm, p_min_GeV=0.0, p_max_GeV=0.0, init_kind=0,
-                 q2=4.0, q3=10.0 / 3.0, bin_every=0, seed=2, device="cuda", integrator=0, substeps=1):
+                 q2=4.0, q3=10.0 / 3.0, bin_every=0, seed=2, device="cuda", integrator=0, substeps=1, interp=0):
         self.glasma = glasma
         self.params = CpicParams(n_particles, init_kind, mass_GeV, tau_form_fm, p_min_GeV, p_max_GeV, q2, q3,
-                                 bin_every, integrator, substeps, seed)
+                                 bin_every, integrator, substeps, interp, seed)
         nb = lib().cpic_workspace_bytes(C.byref(glasma.params), C.byref(self.params))
         check(0 if nb >= 0 else nb)
         self._ws, ptr = _workspace(nb, device)

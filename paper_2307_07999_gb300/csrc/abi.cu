@@ -280,6 +280,7 @@ static glasma_status check_cpic(const cpic_params* p) {
     if (p->init_kind != 0 && p->init_kind != 1) return fail(GLASMA_ERR_INVALID, "bad init_kind");
     if (p->integrator != 0 && p->integrator != 1) return fail(GLASMA_ERR_INVALID, "bad integrator");
     if (p->substeps < 0 || p->substeps > 64) return fail(GLASMA_ERR_INVALID, "substeps must be in [0, 64]");
+    if (p->interp != 0 && p->interp != 1) return fail(GLASMA_ERR_INVALID, "bad interp");
     return GLASMA_OK;
 }
 static int total_steps(const glasma_params* gp) {
@@ -393,7 +394,7 @@ static glasma_status push_ensemble(cpic_ctx* c, int n, const void* fo) {
     a.fn = g->buf[g->cur];
     a.n = g->n;
     a.np = c->np;
-    push_coeffs(a, n, g->dtau, g->p.expanding, c->p.integrator, c->p.substeps);
+    push_coeffs(a, n, g->dtau, g->p.expanding, c->p.integrator, c->p.substeps, c->p.interp);
     a.mass = c->mass;
     a.acc = c->acc + 4 * (size_t)(n + 1);
     CK(launch_push(g->prec, a, c->P[c->pcur], g->st));
@@ -467,7 +468,7 @@ struct CkptHeader {
     int32_t version, prec, n, np;
     int32_t step, first_step, since_sort, acc_rows;
     double dtau, a_fm, mass;
-    int32_t expanding, integrator, substeps, pad;
+    int32_t expanding, integrator, substeps, interp;
     int64_t body_bytes;
 };
 static void ckpt_header(CkptHeader& h, const char* magic, const glasma_ctx* g) {
@@ -483,7 +484,7 @@ static void ckpt_header(CkptHeader& h, const char* magic, const glasma_ctx* g) {
 static bool ckpt_same_shape(const CkptHeader& a, const CkptHeader& b) {
     return !memcmp(a.magic, b.magic, 8) && a.version == b.version && a.prec == b.prec && a.n == b.n && a.np == b.np &&
            a.acc_rows == b.acc_rows && a.dtau == b.dtau && a.a_fm == b.a_fm && a.mass == b.mass &&
-           a.expanding == b.expanding && a.integrator == b.integrator && a.substeps == b.substeps &&
+           a.expanding == b.expanding && a.integrator == b.integrator && a.substeps == b.substeps && a.interp == b.interp &&
            a.body_bytes == b.body_bytes;
 }
 
@@ -530,6 +531,7 @@ static CkptHeader cpic_header(const cpic_ctx* c) {
     h.mass = c->mass;
     h.integrator = c->p.integrator;
     h.substeps = c->p.substeps > 1 ? c->p.substeps : 1;
+    h.interp = c->p.interp;
     h.body_bytes = (int64_t)(part_bytes(c->np, c->g->prec) + (size_t)c->acc_rows * 4 * 8);
     return h;
 }

@@ -95,7 +95,7 @@ static glasma_status check_batch(const glasma_params* ev, const cpic_params* pp,
             return bfail(GLASMA_ERR_INVALID, "bad event parameters");
         if (pp[e].n_particles < 0 || pp[e].mass_GeV < 0 || pp[e].tau_form_fm < 0 || pp[e].p_max_GeV < pp[e].p_min_GeV ||
             (pp[e].init_kind != 0 && pp[e].init_kind != 1) || (pp[e].integrator != 0 && pp[e].integrator != 1) ||
-            pp[e].substeps < 0 || pp[e].substeps > 64)
+            pp[e].substeps < 0 || pp[e].substeps > 64 || (pp[e].interp != 0 && pp[e].interp != 1))
             return bfail(GLASMA_ERR_INVALID, "bad particle parameters");
     }
     return GLASMA_OK;
@@ -165,7 +165,7 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
         x.np = pp[e].n_particles;
         x.n_form = std::max(1, (int)lround(pp[e].tau_form_fm / (x.dtau * x.a_fm)));
         x.mass = pp[e].mass_GeV * x.a_gev;
-        if (pp[e].substeps > 1) b->any_sub = true;
+        if (pp[e].substeps > 1 || pp[e].interp) b->any_sub = true;
         x.buf[0] = A.take(fbytes(ev[e]));
         x.buf[1] = A.take(fbytes(ev[e]));
         x.buf[2] = A.take(fbytes(ev[e]));
@@ -293,7 +293,7 @@ static glasma_status build_tables(glasma_batch* b) {
             pack_step_args(b->prec, st, hs.data() + ((size_t)k * E + i) * sa);
             PushHost ph;
             ph.fo = src; ph.fn = dst; ph.n = x.n; ph.np = x.np;
-            push_coeffs(ph, s, x.dtau, 1, x.pp.integrator, x.pp.substeps);
+            push_coeffs(ph, s, x.dtau, 1, x.pp.integrator, x.pp.substeps, x.pp.interp);
             ph.mass = x.mass;
             ph.acc = (on && s >= x.n_form) ? x.acc + 4 * (size_t)(s + 1) : nullptr;
             pack_push_args(b->prec, ph, x.P, hp.data() + ((size_t)k * E + i) * pa);
@@ -420,7 +420,7 @@ static cudaError_t enqueue_per_event(glasma_batch* b) {
             if (s >= x.n_form && x.np > 0) {
                 PushHost ph;
                 ph.fo = x.buf[k % 3]; ph.fn = x.buf[(k + 1) % 3]; ph.n = x.n; ph.np = x.np;
-                push_coeffs(ph, s, x.dtau, 1, x.pp.integrator, x.pp.substeps);
+                push_coeffs(ph, s, x.dtau, 1, x.pp.integrator, x.pp.substeps, x.pp.interp);
                 ph.mass = x.mass;
                 ph.acc = x.acc + 4 * (size_t)(s + 1);
                 e = launch_push(b->prec, ph, x.P, b->st);
@@ -461,12 +461,12 @@ extern "C" glasma_status glasma_batch_run(glasma_batch* b, int32_t mode) {
         case GLASMA_BATCH_PER_EVENT: BCK(enqueue_per_event(b)); return GLASMA_OK;
         case GLASMA_BATCH_EAGER: BCK(enqueue_batched(b)); return GLASMA_OK;
         case GLASMA_BATCH_PERSISTENT:
-            if (b->any_sub) return bfail(GLASMA_ERR_INVALID, "the persistent mode does not take sub-stepped particles");
+            if (b->any_sub) return bfail(GLASMA_ERR_INVALID, "the persistent mode does not take sub-stepped or cloud-in-cell particles");
             return batch_run_persistent(b);
         case GLASMA_BATCH_GRAPH: return run_graph(b, false);
         case GLASMA_BATCH_FUSED:
             // a fused tile holds the fields of its own cells only; sub-steps may leave them
-            if (b->any_sub) return bfail(GLASMA_ERR_INVALID, "the fused mode does not take sub-stepped particles");
+            if (b->any_sub) return bfail(GLASMA_ERR_INVALID, "the fused mode does not take sub-stepped or cloud-in-cell particles");
             return run_graph(b, true);
         default: return bfail(GLASMA_ERR_INVALID, "unknown mode");
     }
@@ -567,7 +567,7 @@ extern "C" glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, dou
                                               int64_t* main_sites, int64_t* main_particle_steps, double* other_ms) {
     if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
     const bool fused = mode == GLASMA_BATCH_FUSED;
-    if (fused && b->any_sub) return bfail(GLASMA_ERR_INVALID, "the fused mode does not take sub-stepped particles");
+    if (fused && b->any_sub) return bfail(GLASMA_ERR_INVALID, "the fused mode does not take sub-stepped or cloud-in-cell particles");
     BCK(enqueue_restore(b));
     const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
     const int K = b->max_iter;

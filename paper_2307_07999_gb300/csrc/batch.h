@@ -40,7 +40,7 @@ struct glasma_batch {
     void* gtiles_dev = nullptr;   // TileItem list of the chosen field variant (graph and eager paths)
     int fvar = 0;                 // FP32 field tile variant of the graph and eager paths
     int pvar = 0;                 // batched push kernel of the graph and eager paths
-    bool any_sub = false;         // some event takes several particle steps per field step
+    bool any_sub = false;         // some event takes several particle steps per field step or the CIC gather
     void* pitems_dev = nullptr;   // PushItem list, grouped by event
     void* scratch = nullptr;      // initial-condition / sort scratch
     std::vector<int> tiles_upto, gtiles_upto, pitems_upto, active;

@@ -63,11 +63,13 @@ struct PushHost {
     int boris;           // momentum kick: 0 explicit, 1 Boris
     int nsub;            // particle steps per field step
     double hsub, tau0;   // their length dtau / nsub, and tau_n
+    int interp;          // gather: 0 nearest grid point, 1 cloud in cell
     double dec0, dec1;   // Boris: p_eta^ decay factors tau_n/tau_{n+1/2}, tau_{n+1/2}/tau_{n+1} (1: static box)
     double* acc;
 };
 // the step-dependent coefficients of the push from tau_n = step * dtau to tau_{n+1}
-inline void push_coeffs(PushHost& a, int step, double dtau, int expanding, int integrator, int substeps) {
+inline void push_coeffs(PushHost& a, int step, double dtau, int expanding, int integrator, int substeps,
+                        int interp) {
     const double tn = step * dtau, th = (step + 0.5) * dtau, t1 = (step + 1.0) * dtau;
     a.dtau = dtau;
     a.expanding = expanding;
@@ -80,13 +82,15 @@ inline void push_coeffs(PushHost& a, int step, double dtau, int expanding, int i
     a.nsub = substeps > 1 ? substeps : 1;
     a.hsub = dtau / a.nsub;
     a.tau0 = tn;
+    a.interp = interp;
 }
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st);
 // batched push: args[n_ev] (acc == nullptr: event idle this step), items {ev, j0} of 256 particles
 size_t push_args_size(int prec);
 void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out);
 int push_variants();
-// the batched push of batches with sub-stepped events (global source, any cell; not tuned)
+// the batched push of batches with sub-stepped or cloud-in-cell events (global source, any
+// cell; not tuned)
 constexpr int PUSH_VARIANT_SUB = 2;
 // lattice-correlator estimators (kernels_corr.cu): state = I [24][ns], J [24][ns], W [18][ns]
 size_t corr_state_bytes(int prec, int n);

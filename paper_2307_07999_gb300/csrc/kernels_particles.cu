@@ -40,7 +40,7 @@ template <class T> static PushArgs<T> push_args(const PushHost& a, const PartHos
     A.dtau = (T)a.dtau; A.te = (T)a.te; A.ichr = (T)a.ichr; A.teh = (T)a.teh; A.mass = (T)a.mass;
     A.expanding = a.expanding; A.acc = a.acc;
     A.boris = a.boris; A.dec0 = (T)a.dec0; A.dec1 = (T)a.dec1;
-    A.nsub = a.nsub; A.hsub = (T)a.hsub; A.tau0 = (T)a.tau0;
+    A.nsub = a.nsub; A.hsub = (T)a.hsub; A.tau0 = (T)a.tau0; A.interp = a.interp;
     return A;
 }
 size_t push_args_size(int prec) { return prec ? sizeof(PushArgs<float>) : sizeof(PushArgs<double>); }
@@ -85,7 +85,7 @@ cudaError_t launch_push_batched(int prec, int v, const void* args, const void* i
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st) {
     if (a.np <= 0) return cudaSuccess;
     const int nb = (a.np + 255) / 256;
-    if (a.nsub > 1) {
+    if (a.nsub > 1 || a.interp) {
         if (prec) k_push<float, true><<<nb, 256, 0, st>>>(push_args<float>(a, P));
         else k_push<double, true><<<nb, 256, 0, st>>>(push_args<double>(a, P));
     } else {

@@ -31,6 +31,7 @@ template <class T> struct PushArgs {
     T teh;         // tau_{n+1/2} (expanding) or 1: eta drift
     int nsub;      // particle steps per field step (1: one step with the coefficients above)
     T hsub, tau0;  // nsub > 1: steps of hsub from tau0 = tau_n, coefficients per step
+    int interp;    // gather: 0 nearest grid point, 1 cloud in cell (SUB kernels only)
     T mass;
     int expanding;
     int boris;     // momentum kick: 0 explicit (first order), 1 Boris (second order)
@@ -216,6 +217,35 @@ DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
     qB[2] = -T(0.25) * bz;
 }
 
+// Cloud-in-cell gather: the Q-contracted fields of the four sites around the particle
+// (c, c+x, c+y, c+x+y) carried to c, with bilinear weights in the offsets (ox, oy).
+// Carrying the field F(s) to c is W F(s) W^dag with W the links from c to s (x before y
+// for the diagonal site); Q.(W F W^dag) = (W^dag Q W).F, so Q is carried to each site
+// instead (three transports of one 8-vector rather than eighteen).  The source must
+// serve views at any cell (GlobalSrc).
+template <class T, class S>
+DEV void gather_qf_cic(const S& F, int n, int cx, int cy, T ox, T oy, T te, const Al<T>& q, T qE[3], T qB[3]) {
+    const int xp = cx == n - 1 ? 0 : cx + 1, yp = cy == n - 1 ? 0 : cy + 1;
+    const auto C = F.view(cx, cy);
+    const Al<T> q10 = transport_alg(C.link(0, 0, 0), q);
+    const Al<T> q01 = transport_alg(C.link(1, 0, 0), q);
+    const Al<T> q11 = transport_alg(C.link(1, 1, 0), q10);
+    const T w00 = (T(1) - ox) * (T(1) - oy), w10 = ox * (T(1) - oy), w01 = (T(1) - ox) * oy, w11 = ox * oy;
+    T e[3], b[3];
+    gather_qf_view(C, te, q, qE, qB);
+#pragma unroll
+    for (int i = 0; i < 3; i++) { qE[i] *= w00; qB[i] *= w00; }
+    gather_qf_view(F.view(xp, cy), te, q10, e, b);
+#pragma unroll
+    for (int i = 0; i < 3; i++) { qE[i] = fma(w10, e[i], qE[i]); qB[i] = fma(w10, b[i], qB[i]); }
+    gather_qf_view(F.view(cx, yp), te, q01, e, b);
+#pragma unroll
+    for (int i = 0; i < 3; i++) { qE[i] = fma(w01, e[i], qE[i]); qB[i] = fma(w01, b[i], qB[i]); }
+    gather_qf_view(F.view(xp, yp), te, q11, e, b);
+#pragma unroll
+    for (int i = 0; i < 3; i++) { qE[i] = fma(w11, e[i], qE[i]); qB[i] = fma(w11, b[i], qB[i]); }
+}
+
 // The site-centred fields at the view's cell, as 8-vectors (the same formulas as
 // gather_qf_view, which contracts each with Q as soon as it is read):
 // E = (E_x, E_y, E_z), B = (B_x, B_y, B_z)
@@ -257,7 +287,8 @@ template <class T, class V> DEV void site_fields(const V& C, T te, Al<T> E[3], A
 
 // one particle: gather, kick, drift, color transport; returns its broadening terms.
 // SUB: the step is taken as A.nsub particle steps of A.hsub, each gathering the step's
-// fields at the particle's current cell (the source must serve any cell: GlobalSrc).
+// fields at the particle's current cell, by nearest grid point or cloud in cell
+// (A.interp); the source must serve any cell (GlobalSrc).
 // Without SUB the loop runs once with the host's coefficients (the kernels of the
 // default path are compiled without it: the loop's carried state costs registers).
 template <class T, class S, bool CG = false, bool SUB = false>
@@ -273,6 +304,11 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
     T dpx = CG ? __ldcg(P.dpx + j) : P.dpx[j], dpy = CG ? __ldcg(P.dpy + j) : P.dpy[j];
     T pz = CG ? __ldcg(P.peta + j) : P.peta[j];
     T ox, oy, eta;
+    if (SUB) {  // the cloud-in-cell gather needs the offsets first
+        ox = CG ? __ldcg(P.ox + j) : P.ox[j];
+        oy = CG ? __ldcg(P.oy + j) : P.oy[j];
+        eta = CG ? __ldcg(P.eta + j) : P.eta[j];
+    }
     const T m2 = A.mass * A.mass;
     T px, py, ptn;
     const int nsub = SUB ? A.nsub : 1;
@@ -290,7 +326,10 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
         }
         T qE[3], qB[3];
         const auto C = F.view(cx, cy);
-        gather_qf_view(C, A.te, q, qE, qB);
+        if (SUB && A.interp)
+            gather_qf_cic(F, n, cx, cy, ox, oy, A.te, q, qE, qB);
+        else
+            gather_qf_view(C, A.te, q, qE, qB);
         px = p0x + dpx;
         py = p0y + dpy;
         if (!A.boris) {
@@ -325,7 +364,7 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
         py = p0y + dpy;
         ptn = sqrt(m2 + px * px + py * py + pz * pz);
         const T iptn = ptn > T(0) ? T(1) / ptn : T(0);
-        if (k == 0) {  // loaded here, after the gather, to keep them out of its live range
+        if (!SUB && k == 0) {  // loaded here, after the gather, to keep them out of its live range
             ox = CG ? __ldcg(P.ox + j) : P.ox[j];
             oy = CG ? __ldcg(P.oy + j) : P.oy[j];
             eta = CG ? __ldcg(P.eta + j) : P.eta[j];

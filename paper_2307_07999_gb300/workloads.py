@@ -26,7 +26,7 @@ def glasma_params(n, L_fm, g2mu, seed, precision, tau_end_fm=1.0, m_ir=0.2, n_sh
 def charm_params(n_particles, seed, mass=1.5, p_max=5.0, tau_form=None, integrator=0):
     # tau_form = 1/(2M) (Sec. 2: formation time proportional to the inverse mass)
     tf = HBARC / (2.0 * mass) if tau_form is None else tau_form
-    return CpicParams(n_particles, 0, mass, tf, 0.0, p_max, 4.0, 10.0 / 3.0, 0, integrator, 1, seed ^ PARTICLE_KEY_XOR)
+    return CpicParams(n_particles, 0, mass, tf, 0.0, p_max, 4.0, 10.0 / 3.0, 0, integrator, 1, 0, seed ^ PARTICLE_KEY_XOR)
 
 
 def batched_uneven(rank=0, precision=GLASMA_FP32, n_events=64, sizes=(128, 256, 384, 512), n_particles=10000):
@@ -50,7 +50,7 @@ def single_32(precision=GLASMA_FP64):
     """32^2, L = 6 fm, g^2 mu = 2 GeV, 1000 charm at rest formed at 0.1 fm/c."""
     s = event_seed(1, 0)
     return ([glasma_params(32, 6.0, 2.0, s, precision, reunit_every=0)],
-            [CpicParams(1000, 0, 1.5, 0.1, 0.0, 0.0, 4.0, 10.0 / 3.0, 0, 0, 1, s ^ PARTICLE_KEY_XOR)])
+            [CpicParams(1000, 0, 1.5, 0.1, 0.0, 0.0, 4.0, 10.0 / 3.0, 0, 0, 1, 0, s ^ PARTICLE_KEY_XOR)])
 
 
 WORKLOADS = {"batched_uneven": batched_uneven, "single_32": single_32}

@@ -36,7 +36,7 @@ def test_field_parameters_are_checked(lib, bad):
 def test_particle_parameters_are_checked(lib):
     gp = params()
     for bad in (dict(n_particles=-1), dict(mass_GeV=-1.0), dict(init_kind=5), dict(p_min_GeV=3.0, p_max_GeV=1.0),
-                dict(integrator=2), dict(integrator=-1), dict(substeps=-1), dict(substeps=65)):
+                dict(integrator=2), dict(integrator=-1), dict(substeps=-1), dict(substeps=65), dict(interp=2)):
         pp = W.charm_params(10, 1)
         for k, v in bad.items():
             setattr(pp, k, v)
