@@ -574,10 +574,11 @@ def run_single_512(args, ws, rank, local):
     del g0
     n_steps = int(math.ceil(1.0 / (0.125 * L / n) - 1e-9))
 
-    def setup(prec):
+    def setup(prec, interp=0):
         g = G.Glasma(n, L, precision=prec, tau_end_fm=1.0, seed=seed, reunit_every=(64 if prec else 0),
                      stream=stream)
-        cs = [G.CPIC(g, NP, m, HBARC_GEV_FM / (2 * m), p_min_GeV=0.0, p_max_GeV=5.0, seed=ps) for m, ps in species]
+        cs = [G.CPIC(g, NP, m, HBARC_GEV_FM / (2 * m), p_min_GeV=0.0, p_max_GeV=5.0, seed=ps, interp=interp)
+              for m, ps in species]
         return g, cs
 
     def one_run(g, cs):
@@ -615,9 +616,22 @@ def run_single_512(args, ws, rank, local):
         out[prec] = dict(ms=max_over_ranks(statistics.mean(ms), ws), tabs=tabs, psteps=psteps,
                          field_ms=e0.elapsed_time(e1) / 100, clocks=clocks, diag=g.diagnostics())
         del cs, g
+    # the same run with the cloud-in-cell gather: one timed run per precision, and its errors
+    cic = {}
+    for prec in (G.GLASMA_FP32, G.GLASMA_FP64):
+        g, cs = setup(prec, interp=1)
+        one_run(g, cs)
+        cic[prec] = dict(ms=max_over_ranks(one_run(g, cs), ws), tabs=[c.broadening() for c in cs])
+        del cs, g
     f32, f64 = out[G.GLASMA_FP32], out[G.GLASMA_FP64]
     su = n * n * (n_steps - 1)
     errs = {}
+    cic_errs = {}
+    for name, t32, t64 in zip(("charm", "beauty"), cic[G.GLASMA_FP32]["tabs"], cic[G.GLASMA_FP64]["tabs"]):
+        den = lambda a: max(np.abs(a).max(), 1e-300)
+        k32, k64 = G.kappa_qhat(t32)[:, 1:], G.kappa_qhat(t64)[:, 1:]
+        cic_errs[name] = {"dp2": float(np.abs(t32[:, 1:4] - t64[:, 1:4]).max() / den(t64[:, 1:4])),
+                          "kappa": float(np.abs(k32 - k64).max() / den(k64))}
     for name, t32, t64 in zip(("charm", "beauty"), f32["tabs"], f64["tabs"]):
         den = lambda a: max(np.abs(a).max(), 1e-300)
         k32, k64 = G.kappa_qhat(t32)[:, 1:], G.kappa_qhat(t64)[:, 1:]
@@ -647,6 +661,8 @@ def run_single_512(args, ws, rank, local):
                      "particle_steps_per_s": f64["psteps"] * ws / (f64["ms"] / 1000.0),
                      "field_step_ms": f64["field_ms"], "fp32_speedup": f64["ms"] / f32["ms"]},
             "fp32_vs_fp64": errs,
+            "cloud_in_cell": {"fp32_ms_per_run": cic[G.GLASMA_FP32]["ms"], "fp64_ms_per_run": cic[G.GLASMA_FP64]["ms"],
+                              "fp32_vs_fp64": cic_errs},
             "fp32_monitors": {"gauss_rel": f32["diag"][0], "unitarity": f32["diag"][5]},
             "roofline": {"bound": "hbm", "achieved": field_bw, "peak": peak, "unit": "GB/s", "frac": field_bw / peak,
                          "traffic": None, "kernel": "k_field_step<float> (one event)",

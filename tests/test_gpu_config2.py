@@ -15,7 +15,8 @@ with isotropic azimuth, formed at 1/(2M) (Sec. 2).
   of this configuration, with only its stored fields rounded to FP32 after every step,
   already differs from itself unrounded by 1.9e-4 of the charm kappa peak (late tau, the
   longitudinal component), against 5e-6 on <dp^2>.  No FP32 field storage gets under
-  that floor, so the bound on kappa sits above it.
+  that floor, so the bound on kappa sits above it.  With the cloud-in-cell gather the
+  force is continuous across cell faces (to second order) and kappa is held to 1e-4.
 """
 import numpy as np
 import pytest
@@ -62,12 +63,12 @@ def oracle_run():
     return st0, samples
 
 
-def gpu_run(st0, prec, stop=None):
+def gpu_run(st0, prec, stop=None, interp=0):
     g = G.Glasma(N, L, precision=prec, tau_end_fm=1.0, seed=SEED, reunit_every=(64 if prec else 0))
     g.set_state(st0.U, st0.E, st0.phi, st0.pi, 1)
     cs = {}
     for name, (m, pseed) in SPECIES.items():
-        c = G.CPIC(g, NP, m, tau_form(m), p_min_GeV=0.0, p_max_GeV=5.0, seed=pseed)
+        c = G.CPIC(g, NP, m, tau_form(m), p_min_GeV=0.0, p_max_GeV=5.0, seed=pseed, interp=interp)
         c.init()
         cs[name] = c
     n_steps = int(np.ceil(1.0 / (0.125 * L / N) - 1e-9))
@@ -91,10 +92,11 @@ def test_config2_fp64_sampled_against_oracle(oracle_run):
         assert tab.shape[0] == K_CHECK - n_form + 1 and np.all(tab[1:, 4] == NP)
 
 
-def test_config2_fp32_against_fp64(oracle_run):
+@pytest.mark.parametrize("interp,kappa_tol", [(0, 3e-4), (1, 1e-4)])
+def test_config2_fp32_against_fp64(oracle_run, interp, kappa_tol):
     st0, _ = oracle_run
-    g64, c64 = gpu_run(st0, 0)
-    g32, c32 = gpu_run(st0, 1)
+    g64, c64 = gpu_run(st0, 0, interp=interp)
+    g32, c32 = gpu_run(st0, 1, interp=interp)
     d32 = g32.diagnostics()
     print(f"FP32 Gauss {d32[0]:.2e} unitarity {d32[5]:.2e}")
     assert d32[0] < 1e-5 and d32[7] == 0
@@ -108,7 +110,7 @@ def test_config2_fp32_against_fp64(oracle_run):
         e_a = rel_err(a32, a64)
         print(f"{name}: dp2 {e_dp:.2e} kappa {e_k:.2e} anisotropy {e_a:.2e} "
               f"(final <dp_L^2>/<dp_T^2> = {a64[-1]:.3f})")
-        assert e_dp < 1e-4 and e_a < 1e-4 and e_k < 3e-4, name
+        assert e_dp < 1e-4 and e_a < 1e-4 and e_k < kappa_tol, name
         assert np.all(np.isfinite(a64)) and np.all(a64 > 0)
         drift = c32[name].casimir_drift()
         assert drift[0] < 1e-3 and drift[1] < 1e-3, (name, drift)
