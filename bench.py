@@ -52,11 +52,12 @@ def parse():
     p.add_argument("--field-variant", type=int, default=-1,
                    help="fixed field tile variant (default: tuned on the batch)")
     p.add_argument("--push-variant", type=int, default=-1, help="fixed push kernel with --field-variant")
-    p.add_argument("--workload", default="batch", choices=["batch", "warm_start", "correlators", "single_512", "scans"],
+    p.add_argument("--workload", default="batch", choices=["batch", "warm_start", "correlators", "single_512", "scans", "jets"],
                    help="batch: the 64-event coupled evolution (default); warm_start: the tau = 0+ link "
                         "solve of 16 events at 1024^2, cold vs learned warm start; correlators: the lattice-"
                         "correlator estimators of Eqs. 4-5 on a 1024^2 event; single_512: one 512^2 event with "
-                        "100k charm + 100k beauty, FP32 and FP64; scans: the p_T and p_x scans of Figs. 1-2")
+                        "100k charm + 100k beauty, FP32 and FP64; scans: the p_T and p_x scans of Figs. 1-2; "
+                        "jets: 4 events of 1024^2 with 1M partons each")
     return p.parse_args()
 
 
@@ -151,8 +152,10 @@ def measured_peak():
 
 
 def kernel_source_hash():
+    """Hash of the field kernel's device code (su3.cuh, field.cuh); kernels_field.cu only
+    instantiates tile shapes, which the profile summary names."""
     h = hashlib.sha256()
-    for f in ("su3.cuh", "field.cuh", "kernels_field.cu"):
+    for f in ("su3.cuh", "field.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2307_07999_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -761,6 +764,105 @@ def run_scans(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- jets at 1024^2
+def run_jets(args, ws, rank, local):
+    """Jets: 4 MV events of 1024^2 (L = 10 fm, g2mu = 2 GeV, m = 0.2 GeV, 10 sheets), each
+    probed by 1M massless partons along +x in three ensembles of |p_x| = 2, 5, 10 GeV
+    (333,334 / 333,333 / 333,333), formed at 0.3 fm/c, FP32 (FP64 sums) to 1 fm/c: 819
+    coupled steps per event, the partons pushed from step 246.  A step is the whole job
+    (all 4 events from their initial states, uploaded untimed); value = site-updates/s,
+    particle-steps/s beside it; q^_y, q^_z at tau = 0.5 fm/c and their peak."""
+    import torch
+
+    import paper_2307_07999_gb300 as G
+
+    torch.cuda.set_device(local)
+    n, L, n_ev = 1024, 10.0, 4
+    counts = [333334, 333333, 333333]
+    stream = torch.cuda.Stream()
+    n_steps = int(math.ceil(1.0 / (0.125 * L / n) - 1e-9))
+    states = []
+    for e in range(n_ev):
+        g = G.Glasma(n, L, precision=G.GLASMA_FP32, tau_end_fm=1.0, seed=(4 << 32) + e + 1000 * rank,
+                     reunit_every=64, stream=stream)
+        g.init()
+        states.append(g.export_state())
+    g = G.Glasma(n, L, precision=G.GLASMA_FP32, tau_end_fm=1.0, seed=4 << 32, reunit_every=64, stream=stream)
+    cs = [G.CPIC(g, cnt, 0.0, 0.3, p_min_GeV=p, p_max_GeV=p, init_kind=1,
+                 seed=((4 << 32) + 7919 * (k + 1) + 1000 * rank) ^ 0x5A5A5A5A5A5A5A5A)
+          for k, (p, cnt) in enumerate(zip((2.0, 5.0, 10.0), counts))]
+
+    def job():
+        ms, tabs = 0.0, []
+        for e in range(n_ev):
+            g.import_state(states[e])
+            for c in cs:
+                c.init()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.push_many(cs, n_steps - 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            tabs.append([c.broadening() for c in cs])
+        return ms, tabs
+
+    for _ in range(args.warmup):
+        job()
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(ws)
+    runs = [job() for _ in range(args.steps)]
+    clocks = clk.stop()
+    ms = max_over_ranks(statistics.mean(r[0] for r in runs), ws)
+    tabs = runs[-1][1]
+    su = n_ev * n * n * (n_steps - 1)
+    ps = sum(int(t[1:, 4].sum()) for ev in tabs for t in ev)
+    # field step alone (single-event kernel), for the roofline
+    g.import_state(states[0])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(200)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    field_ms = e0.elapsed_time(e1) / 200
+    peak, kind = measured_peak()
+    field_bw = BYTES_PER_SITE * n * n / (field_ms / 1000.0) / 1e9
+    whole_bw = (BYTES_PER_SITE * su + BYTES_PER_PARTICLE * ps) / (ms / 1000.0) / 1e9
+    qh = {}
+    for k, p in enumerate((2.0, 5.0, 10.0)):
+        cnt = sum(ev[k][:, 4] for ev in tabs)
+        pooled = tabs[0][k].copy()
+        pooled[:, 1:4] = sum(ev[k][:, 1:4] * ev[k][:, 4:5] for ev in tabs) / np.where(cnt > 0, cnt, 1.0)[:, None]
+        q = G.kappa_qhat(pooled)
+        i5 = int(np.argmin(np.abs(q[:, 0] - 0.5)))
+        tot = q[:, 2] + q[:, 3]
+        qh[f"p_x={p:g} GeV"] = {"qhat_y_at_0.5fm": float(q[i5, 2]), "qhat_z_at_0.5fm": float(q[i5, 3]),
+                                "qhat_total_peak": float(tot.max()), "peak_tau_fm": float(q[int(tot.argmax()), 0]),
+                                "anisotropy_at_end": float(G.anisotropy(pooled, "jet")[-1, 1])}
+    if rank == 0:
+        line = {
+            "metric": "jets at 1024^2: Glasma site-updates/s & Wong particle-steps/s (4 events x 1M partons)",
+            "value": su * ws / (ms / 1000.0), "unit": "site-updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 accumulators)", "data": "synthetic",
+            "particle_steps_per_s": ps * ws / (ms / 1000.0),
+            "config": {"workload": "4 MV events of 1024^2 (L=10 fm, g2mu=2 GeV), 1M massless partons each along +x, "
+                                   "|p_x| in {2,5,10} GeV by thirds, tau_form=0.3 fm/c, FP32 to 1 fm/c (819 steps)",
+                       "l2": "inputs larger than L2 (235 MB per FP32 field buffer, 60 MB of partons per event)"},
+            "site_updates_per_step": su, "particle_steps_per_step": ps,
+            "roofline": {"bound": "hbm", "achieved": field_bw, "peak": peak, "unit": "GB/s", "frac": field_bw / peak,
+                         "traffic": None, "kernel": "k_field_step<float> (one event)", "field_step_ms": field_ms,
+                         "peak_kind": f"{kind} HBM copy (burst)",
+                         "whole_step": {"achieved": whole_bw, "frac": whole_bw / peak, "unit": "GB/s"}},
+            "qhat_GeV2_per_fm": qh,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -774,6 +876,8 @@ def main():
         run_single_512(args, ws, rank, local)
     elif args.workload == "scans":
         run_scans(args, ws, rank, local)
+    elif args.workload == "jets":
+        run_jets(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

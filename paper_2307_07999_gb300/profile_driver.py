@@ -7,6 +7,7 @@
     (both batch workloads tune the field tile shape first: 8 variants x 5 field launches;
      a last argument v=<k> sets field tile variant k instead, without tuning)
   python -m paper_2307_07999_gb300.profile_driver ic 1024            # tau = 0+ solve: cold, then warm start
+  python -m paper_2307_07999_gb300.profile_driver corr 512           # 4 FP32 field steps with both correlators
 """
 import sys
 
@@ -46,6 +47,13 @@ def main(argv):
         return
     g = Glasma(n, 10.0, precision=1, tau_end_fm=1.0, seed=3)
     g.init()
+    if what == "corr":
+        from . import Correlators
+        c = Correlators(g, tau_start_fm=0.0, ox0=0.5)
+        g.step(4)
+        torch.cuda.synchronize()
+        print("ok")
+        return
     g.step(4)
     if what == "push":
         c = CPIC(g, int(argv[3]) if len(argv) > 3 else 100000, 1.5, 0.0, p_max_GeV=5.0, bin_every=1, seed=4)
