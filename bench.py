@@ -380,8 +380,9 @@ def run_ours(args, ws, rank, local):
             "particle_steps_per_s": pvalue,
             "config": {"workload": WORKLOAD, "mode": mode,
                        "field_tile": f"{tile[0]}x{tile[1]}, {tile[2]} CTAs/SM " + ("(fixed)" if args.field_variant >= 0 else "(autotuned)"),
-                       "push_kernel": ("fields staged in shared memory (32-thread blocks)" if B.push_variant == 1
-                                       else "fields through L1 (128-thread blocks)") + (" (fixed)" if args.field_variant >= 0 else " (autotuned)"),
+                       "push_kernel": {0: "fields through L1 (128-thread blocks, 3 per SM)",
+                                       1: "fields staged in shared memory (32-thread blocks)"}.get(B.push_variant, "?")
+                                      + (" (fixed)" if args.field_variant >= 0 else " (autotuned)"),
                        "tile_tuning_ms_per_8_steps": ({f"{a}x{b}/{c}": round(t, 3) for (a, b, c), t in zip(shapes, tile_ms)}
                                                       if args.field_variant < 0 else None),
                        "site_updates_per_step": su,
