@@ -54,8 +54,8 @@ struct Plans {
     }
 };
 static bool make_plans(int n, Plans& P, size_t* work, const char** err) {
-    int dims[2] = {n, n};
-    const int ns = n * n, nh = n * (n / 2 + 1);
+    long long dims[2] = {n, n};
+    const long long ns = (long long)n * n, nh = (long long)n * (n / 2 + 1);  // 8 transforms: > 2^31 reals at n = 16384
     size_t w1 = 0, w2 = 0;
     if (cufftCreate(&P.fwd) != CUFFT_SUCCESS) { *err = "cufftCreate failed"; return false; }
     P.ok_fwd = true;
@@ -65,9 +65,9 @@ static bool make_plans(int n, Plans& P, size_t* work, const char** err) {
         *err = "cufftSetAutoAllocation failed";
         return false;
     }
-    if (cufftMakePlanMany(P.fwd, 2, dims, nullptr, 1, ns, nullptr, 1, nh, CUFFT_D2Z, 8, &w1) != CUFFT_SUCCESS ||
-        cufftMakePlanMany(P.inv, 2, dims, nullptr, 1, nh, nullptr, 1, ns, CUFFT_Z2D, 8, &w2) != CUFFT_SUCCESS) {
-        *err = "cufftMakePlanMany failed";
+    if (cufftMakePlanMany64(P.fwd, 2, dims, nullptr, 1, ns, nullptr, 1, nh, CUFFT_D2Z, 8, &w1) != CUFFT_SUCCESS ||
+        cufftMakePlanMany64(P.inv, 2, dims, nullptr, 1, nh, nullptr, 1, ns, CUFFT_Z2D, 8, &w2) != CUFFT_SUCCESS) {
+        *err = "cufftMakePlanMany64 failed";
         return false;
     }
     *work = std::max(w1, w2);
