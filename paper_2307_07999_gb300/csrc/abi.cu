@@ -211,7 +211,7 @@ extern "C" glasma_status glasma_get_state(glasma_ctx* g, double* U, double* E, d
 
 static glasma_status corr_after_step(glasma_ctx* g, const void* fo, const void* fn);
 static glasma_status one_field_step(glasma_ctx* g) {
-    const int reunit = g->p.reunit_every > 0 && ((g->step + 1) % g->p.reunit_every == 0);
+    const int reunit = reunit_code(g->p.reunit_every, g->step);
     const StepHost a = step_coeffs(g->buf[g->cur], g->buf[g->cur ^ 1], g->n, g->step, g->dtau, g->p.expanding, reunit);
     CK(launch_field_step(g->prec, a, g->st));
     if (g->corr) {

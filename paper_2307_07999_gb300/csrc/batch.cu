@@ -288,7 +288,7 @@ static glasma_status build_tables(glasma_batch* b) {
             if (on) act = i + 1;
             const void* src = x.buf[k % 3];
             void* dst = x.buf[(k + 1) % 3];
-            const int reunit = x.gp.reunit_every > 0 && ((s + 1) % x.gp.reunit_every == 0);
+            const int reunit = reunit_code(x.gp.reunit_every, s);
             const StepHost st = step_coeffs(src, dst, x.n, s, x.dtau, 1, reunit);
             pack_step_args(b->prec, st, hs.data() + ((size_t)k * E + i) * sa);
             PushHost ph;
@@ -414,7 +414,7 @@ static cudaError_t enqueue_per_event(glasma_batch* b) {
         for (int s = 1; s < x.n_steps; s++) {
             const int k = s - 1;
             const StepHost st = step_coeffs(x.buf[k % 3], x.buf[(k + 1) % 3], x.n, s, x.dtau, 1,
-                                            x.gp.reunit_every > 0 && ((s + 1) % x.gp.reunit_every == 0));
+                                            reunit_code(x.gp.reunit_every, s));
             e = launch_field_step(b->prec, st, b->st);
             if (e != cudaSuccess) return e;
             if (s >= x.n_form && x.np > 0) {

@@ -29,7 +29,7 @@ template <class T> struct StepArgs {
     T dtau;
     T ue;          // link drift:  dtau / tau_{n+1/2} (or dtau)
     T pe;          // phi drift:   dtau * tau_{n+1/2} (or dtau)
-    int reunit;    // Gram-Schmidt the new links in FP64
+    int reunit;    // re-projection of the new links: 1 FP64 Gram-Schmidt, 2 FP32 renormalisation, 0 none
 };
 
 struct TileItem { int ev, x0, y0; };
@@ -373,8 +373,8 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
 #pragma unroll
             for (int c = 0; c < 3; c++)
                 V.m[r][c] = val(cmac(cmac(cmul(W.m[r][0], U.m[0][c]), W.m[r][1], U.m[1][c]), W.m[r][2], U.m[2][c]));
-        if (A.reunit) reunit_rows(V);
-        else if (sizeof(T) == 4) renorm_rows(V);
+        if (A.reunit == 1) reunit_rows(V);
+        else if (A.reunit == 2 && sizeof(T) == 4) renorm_rows(V);
         Vn[d] = V;
     }
     store_links(dst, ns, s, Vn[0], Vn[1]);

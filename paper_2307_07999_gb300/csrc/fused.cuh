@@ -177,8 +177,8 @@ DEV void fused_tile(const StepArgs<T>& A, const PushArgs<T>& PA, int x0, int y0,
 #pragma unroll
                 for (int c = 0; c < 3; c++)
                     V.m[r][c] = val(cmac(cmac(cmul(W.m[r][0], U.m[0][c]), W.m[r][1], U.m[1][c]), W.m[r][2], U.m[2][c]));
-            if (A.reunit) reunit_rows(V);
-            else if (sizeof(T) == 4) renorm_rows(V);
+            if (A.reunit == 1) reunit_rows(V);
+            else if (A.reunit == 2 && sizeof(T) == 4) renorm_rows(V);
             Vn[d] = V;
         }
         store_links(dst, ns, s, Vn[0], Vn[1]);
