@@ -314,22 +314,43 @@ def run_ours(args, ws, rank, local):
     # end to end through the public API, right after the device-timed steps (same GPU state):
     # H2D of the initial state from pinned host memory, the run, D2H of every event's
     # broadening table, each step
+    # The host-to-device copy of step k+1's state runs on a copy stream into a device
+    # staging buffer while step k runs; each step then imports from the staging buffer
+    # (device to device, on the batch stream).  Every step's H2D is inside the timed
+    # region (the first one is not overlapped).
     nbytes = B.state_bytes()
     host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     B.export_state(host)
-    for _ in range(1):
-        B.import_state(host)
-        B.run(mode)
-        tabs = [B.broadening(e) for e in range(B.E)]
+    staging = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    copy_stream = torch.cuda.Stream(device=dev)
+
+    def e2e(K):
+        d2h = 0
+        staged = torch.cuda.Event()
+        with torch.cuda.stream(copy_stream):
+            staging.copy_(host, non_blocking=True)
+            staged.record(copy_stream)
+        for k in range(K):
+            stream.wait_event(staged)
+            B.import_state(staging)
+            loaded = torch.cuda.Event()
+            loaded.record(stream)
+            B.run(mode)
+            if k + 1 < K:
+                copy_stream.wait_event(loaded)
+                with torch.cuda.stream(copy_stream):
+                    staging.copy_(host, non_blocking=True)
+                    staged = torch.cuda.Event()
+                    staged.record(copy_stream)
+            tabs = [B.broadening(e) for e in range(B.E)]
+            d2h = sum(t.nbytes for t in tabs)
+        return d2h
+
+    e2e(1)
     torch.cuda.synchronize()
     barrier(ws)
     t0 = time.perf_counter()
-    d2h = 0
-    for _ in range(args.steps):
-        B.import_state(host)
-        B.run(mode)
-        tabs = [B.broadening(e) for e in range(B.E)]
-        d2h = sum(t.nbytes for t in tabs)
+    d2h = e2e(args.steps)
     torch.cuda.synchronize()
     barrier(ws)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0 / args.steps, ws)
@@ -392,7 +413,8 @@ def run_ours(args, ws, rank, local):
             "cpu_baseline": cpu,
             "plain_one_event_per_launch": plain,
             "e2e": {"value": su * ws / (e2e_ms / 1000.0), "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "pipeline": "H2D of step k+1 (pinned host -> device staging, copy stream) overlaps step k"},
             "gpu_launches": launches,
             "clocks": clocks,
         }

@@ -350,7 +350,12 @@ glasma_status glasma_batch_broadening(glasma_batch* b, int32_t event, double* ho
 glasma_status glasma_batch_diagnostics(glasma_batch* b, int32_t event, double out[8]);
 /* Raw initial state of all events (device layout, event order): size, copy out,
  * copy in (the next glasma_batch_run starts from it).  A checkpoint of the
- * batch's starting point; export synchronises, import only enqueues. */
+ * batch's starting point; export synchronises, import only enqueues.  The import
+ * source may be host memory or device memory: a caller that streams inputs can copy
+ * the next state from pinned host memory into a device staging buffer of its own on
+ * another stream while the current run executes, then import from that buffer (a
+ * device-to-device copy on the batch stream, ordered after the caller's copy by the
+ * caller, e.g. with an event). */
 int64_t glasma_batch_state_bytes(const glasma_batch* b);
 glasma_status glasma_batch_export_state(glasma_batch* b, void* host, int64_t bytes);
 glasma_status glasma_batch_import_state(glasma_batch* b, const void* host, int64_t bytes);

@@ -549,11 +549,11 @@ extern "C" glasma_status glasma_batch_export_state(glasma_batch* b, void* host, 
 extern "C" glasma_status glasma_batch_import_state(glasma_batch* b, const void* host, int64_t bytes) {
     if (!b || !host || bytes < glasma_batch_state_bytes(b)) return bfail(GLASMA_ERR_INVALID, "bad arguments");
     if (!b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
-    const char* h = (const char*)host;
+    const char* h = (const char*)host;  // host memory, or device memory staged by the caller
     for (auto& x : b->ev) {
-        BCK(cudaMemcpyAsync(x.init_buf, h, fbytes(x.gp), cudaMemcpyHostToDevice, b->st));
+        BCK(cudaMemcpyAsync(x.init_buf, h, fbytes(x.gp), cudaMemcpyDefault, b->st));
         h += fbytes(x.gp);
-        BCK(cudaMemcpyAsync(x.part_init, h, x.part_bytes, cudaMemcpyHostToDevice, b->st));
+        BCK(cudaMemcpyAsync(x.part_init, h, x.part_bytes, cudaMemcpyDefault, b->st));
         h += x.part_bytes;
     }
     return GLASMA_OK;

@@ -207,3 +207,24 @@ def test_full_size_batch_sampled():
     print(f"event {big} ({gp.n}^2): energies {d[1:5]} vs oracle {want_e}")
     assert rel_err(d[1:5], want_e) < 1e-4, (d[1:5], want_e)
     assert abs(d[6] - st.step * gp.dtau_over_a) < 1e-9
+
+
+def test_batch_import_from_device_memory(fp64_batch):
+    """The batch's initial state imported from a device buffer (a caller's staging copy)
+    gives the run of the state imported from host memory."""
+    import torch
+
+    B, evs, pps = fp64_batch
+    nb = B.state_bytes()
+    host = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    B.export_state(host)
+    B.import_state(host)
+    B.run("graph")
+    want = [B.broadening(e) for e in range(len(evs))]
+    staged = host.to("cuda")
+    torch.cuda.synchronize()
+    B.import_state(staged)
+    B.run("graph")
+    for e in range(len(evs)):
+        got = B.broadening(e)
+        assert rel_err(got[:, 1:4], want[e][:, 1:4]) < 1e-13, e
