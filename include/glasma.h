@@ -367,6 +367,15 @@ glasma_status glasma_batch_import_state(glasma_batch* b, const void* host, int64
  * total time of the other kernels.  Synchronises. */
 glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, double* main_ms, int64_t* main_launches,
                                    int64_t* main_sites, int64_t* main_particle_steps, double* other_ms);
+/* Kernel timing inside the timed runs themselves: with on != 0, the batched path (graph and
+ * eager modes) brackets every batched field launch with CUDA event records, captured in
+ * the graph as event-record nodes (the graph is captured again when this changes).
+ * glasma_batch_graph_times then returns, for the last run, the summed duration of its
+ * field launches (ms), their number, and the span from the first field launch's start to
+ * the last one's end (ms).  Synchronises on the last event.  No counterpart in the paper:
+ * measurement. */
+glasma_status glasma_batch_set_graph_timing(glasma_batch* b, int32_t on);
+glasma_status glasma_batch_graph_times(glasma_batch* b, double* field_ms, int64_t* launches, double* span_ms);
 /* Particles of event i (original order; double[n] each, Q double[n][8]; NULL skips). */
 glasma_status glasma_batch_get_particles(glasma_batch* b, int32_t event, double* x, double* y, double* eta,
                                          double* px, double* py, double* peta, double* Q);

@@ -94,6 +94,8 @@ SIGNATURES = {
     "cpic_get_particles": (C.c_int, [_p] + [_p] * 7),
     "cpic_push": (C.c_int, [_p, _i32]),
     "cpic_push_many": (C.c_int, [_p, _i32, _i32]),
+    "glasma_batch_set_graph_timing": (C.c_int, [_p, _i32]),
+    "glasma_batch_graph_times": (C.c_int, [_p, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_d)]),
     "glasma_state_bytes": (_i64, [_p]),
     "glasma_export_state": (C.c_int, [_p, _p, _i64]),
     "glasma_import_state": (C.c_int, [_p, _p, _i64]),

@@ -377,6 +377,15 @@ class Batch:
     def import_state(self, host_tensor):
         check(lib().glasma_batch_import_state(self.handle, C.c_void_p(host_tensor.data_ptr()), host_tensor.numel()))
 
+    def set_graph_timing(self, on=True):
+        check(lib().glasma_batch_set_graph_timing(self.handle, 1 if on else 0))
+
+    def graph_times(self):
+        """(field-kernel ms summed over the last run's launches, launches, span ms)."""
+        f, n, sp = C.c_double(), C.c_int64(), C.c_double()
+        check(lib().glasma_batch_graph_times(self.handle, C.byref(f), C.byref(n), C.byref(sp)))
+        return f.value, n.value, sp.value
+
     def profile(self, mode="graph"):
         """CUDA-event timing of one eager run: the main kernel (batched field step, or the
         fused field+push kernel for mode="fused") and the other kernels."""

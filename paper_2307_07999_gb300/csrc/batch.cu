@@ -394,12 +394,23 @@ static cudaError_t enqueue_batched(glasma_batch* b) {
     cudaError_t e = enqueue_restore(b);
     if (e != cudaSuccess) return e;
     const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
+    b->tev_used = 0;
     for (int k = 0; k < b->max_iter; k++) {
         const int act = b->active[k];
         if (act == 0) break;
+        // (timing: external event records, so that a captured graph keeps them as nodes)
+        if (b->timing) {
+            e = cudaEventRecordWithFlags(b->tev[2 * k], b->st, cudaEventRecordExternal);
+            if (e != cudaSuccess) return e;
+        }
         e = launch_field_step_variant(b->prec, b->fvar, (char*)b->step_args + (size_t)k * b->E * sa, b->gtiles_dev,
                                       b->gtiles_upto[act], b->st);
         if (e != cudaSuccess) return e;
+        if (b->timing) {
+            e = cudaEventRecordWithFlags(b->tev[2 * k + 1], b->st, cudaEventRecordExternal);
+            if (e != cudaSuccess) return e;
+            b->tev_used = k + 1;
+        }
         e = launch_push_batched(b->prec, b->any_sub ? PUSH_VARIANT_SUB : b->pvar, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
                                 b->pitems_upto[act], b->st);
         if (e != cudaSuccess) return e;
@@ -642,6 +653,38 @@ extern "C" glasma_status glasma_batch_set_variant(glasma_batch* b, int32_t v) {
     }
     return build_gtiles(b);
 }
+extern "C" glasma_status glasma_batch_set_graph_timing(glasma_batch* b, int32_t on) {
+    if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    if ((on != 0) == b->timing) return GLASMA_OK;
+    if (on && b->tev.empty()) {
+        b->tev.assign(2 * (size_t)std::max(1, b->max_iter), nullptr);
+        for (auto& e : b->tev) BCK(cudaEventCreate(&e));
+    }
+    b->timing = on != 0;
+    if (b->graph_unfused_ready) {  // captured again with (or without) the event nodes
+        cudaGraphExecDestroy(b->exec_unfused);
+        b->graph_unfused_ready = false;
+    }
+    return GLASMA_OK;
+}
+extern "C" glasma_status glasma_batch_graph_times(glasma_batch* b, double* field_ms, int64_t* launches,
+                                                  double* span_ms) {
+    if (!b || !field_ms || !launches || !span_ms) return bfail(GLASMA_ERR_INVALID, "null argument");
+    if (!b->timing || b->tev_used == 0) return bfail(GLASMA_ERR_INVALID, "no timed run (set graph timing, then run)");
+    BCK(cudaEventSynchronize(b->tev[2 * (size_t)b->tev_used - 1]));
+    double t = 0.0;
+    for (int k = 0; k < b->tev_used; k++) {
+        float ms = 0.f;
+        BCK(cudaEventElapsedTime(&ms, b->tev[2 * k], b->tev[2 * k + 1]));
+        t += ms;
+    }
+    float span = 0.f;
+    BCK(cudaEventElapsedTime(&span, b->tev[0], b->tev[2 * (size_t)b->tev_used - 1]));
+    *field_ms = t;
+    *launches = b->tev_used;
+    *span_ms = span;
+    return GLASMA_OK;
+}
 extern "C" int32_t glasma_push_variants(void) { return push_variants(); }
 extern "C" int32_t glasma_batch_push_variant(const glasma_batch* b) { return b ? b->pvar : GLASMA_ERR_INVALID; }
 extern "C" glasma_status glasma_batch_set_push_variant(glasma_batch* b, int32_t v) {
@@ -768,6 +811,8 @@ extern "C" void glasma_batch_destroy(glasma_batch* b) {
     if (!b) return;
     if (b->graph_ready) cudaGraphExecDestroy(b->exec);
     if (b->graph_unfused_ready) cudaGraphExecDestroy(b->exec_unfused);
+    for (auto& e : b->tev)
+        if (e) cudaEventDestroy(e);
     batch_free_persistent(b);
     delete b;
 }

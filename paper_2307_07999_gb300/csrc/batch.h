@@ -41,6 +41,10 @@ struct glasma_batch {
     int fvar = 0;                 // FP32 field tile variant of the graph and eager paths
     int pvar = 0;                 // batched push kernel of the graph and eager paths
     bool any_sub = false;         // some event takes several particle steps per field step or the CIC gather
+    // graph timing: event-record nodes around every field launch of the batched path
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;  // [2 * max_iter]: start, end of field launch k
+    int tev_used = 0;              // pairs recorded by the last enqueue
     void* pitems_dev = nullptr;   // PushItem list, grouped by event
     void* scratch = nullptr;      // initial-condition / sort scratch
     std::vector<int> tiles_upto, gtiles_upto, pitems_upto, active;

@@ -228,3 +228,22 @@ def test_batch_import_from_device_memory(fp64_batch):
     for e in range(len(evs)):
         got = B.broadening(e)
         assert rel_err(got[:, 1:4], want[e][:, 1:4]) < 1e-13, e
+
+
+def test_graph_timing_nodes(fp64_batch):
+    """Event-record nodes around the field launches of the captured graph: one pair per
+    iteration of the run, durations that fit in the span, and the same results."""
+    B, evs, pps = fp64_batch
+    B.run("graph")
+    want = [B.broadening(e) for e in range(len(evs))]
+    B.set_graph_timing(True)
+    B.run("graph")
+    field_ms, n, span = B.graph_times()
+    n_iter = max(int(np.ceil(gp.tau_end_fm / (gp.dtau_over_a * gp.L_fm / gp.n) - 1e-9)) for gp in evs) - 1
+    assert n == n_iter and 0 < field_ms <= span
+    for e in range(len(evs)):
+        assert rel_err(B.broadening(e)[:, 1:4], want[e][:, 1:4]) < 1e-13
+    B.set_graph_timing(False)
+    B.run("graph")
+    with pytest.raises(G.GlasmaError):
+        B.graph_times()
