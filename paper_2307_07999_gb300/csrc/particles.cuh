@@ -226,24 +226,21 @@ DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
 template <class T, class S>
 DEV void gather_qf_cic(const S& F, int n, int cx, int cy, T ox, T oy, T te, const Al<T>& q, T qE[3], T qB[3]) {
     const int xp = cx == n - 1 ? 0 : cx + 1, yp = cy == n - 1 ? 0 : cy + 1;
-    const auto C = F.view(cx, cy);
-    const Al<T> q10 = transport_alg(C.link(0, 0, 0), q);
-    const Al<T> q01 = transport_alg(C.link(1, 0, 0), q);
-    const Al<T> q11 = transport_alg(C.link(1, 1, 0), q10);
-    const T w00 = (T(1) - ox) * (T(1) - oy), w10 = ox * (T(1) - oy), w01 = (T(1) - ox) * oy, w11 = ox * oy;
-    T e[3], b[3];
-    gather_qf_view(C, te, q, qE, qB);
 #pragma unroll
-    for (int i = 0; i < 3; i++) { qE[i] *= w00; qB[i] *= w00; }
-    gather_qf_view(F.view(xp, cy), te, q10, e, b);
+    for (int i = 0; i < 3; i++) { qE[i] = T(0); qB[i] = T(0); }
+    // one site per iteration, not unrolled: one copy of the gather (four inlined copies spill)
+#pragma unroll 1
+    for (int k = 0; k < 4; k++) {
+        const auto C = F.view(cx, cy);
+        Al<T> qk = q;
+        if (k & 1) qk = transport_alg(C.link(0, 0, 0), qk);                   // c -> c+x
+        if (k & 2) qk = transport_alg(C.link(1, (k & 1) ? 1 : 0, 0), qk);     // -> +y (x first)
+        const T w = ((k & 1) ? ox : T(1) - ox) * ((k & 2) ? oy : T(1) - oy);
+        T e[3], b[3];
+        gather_qf_view(F.view((k & 1) ? xp : cx, (k & 2) ? yp : cy), te, qk, e, b);
 #pragma unroll
-    for (int i = 0; i < 3; i++) { qE[i] = fma(w10, e[i], qE[i]); qB[i] = fma(w10, b[i], qB[i]); }
-    gather_qf_view(F.view(cx, yp), te, q01, e, b);
-#pragma unroll
-    for (int i = 0; i < 3; i++) { qE[i] = fma(w01, e[i], qE[i]); qB[i] = fma(w01, b[i], qB[i]); }
-    gather_qf_view(F.view(xp, yp), te, q11, e, b);
-#pragma unroll
-    for (int i = 0; i < 3; i++) { qE[i] = fma(w11, e[i], qE[i]); qB[i] = fma(w11, b[i], qB[i]); }
+        for (int i = 0; i < 3; i++) { qE[i] = fma(w, e[i], qE[i]); qB[i] = fma(w, b[i], qB[i]); }
+    }
 }
 
 // The site-centred fields at the view's cell, as 8-vectors (the same formulas as
