@@ -39,6 +39,14 @@ template <class T> struct PushArgs {
     double* acc;   // this step's row: {sum dpx^2, sum dpy^2, sum dpz^2, count}
 };
 
+template <class T> DEV M3<T> dagger(const M3<T>& A) {
+    M3<T> D;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) D.m[i][j] = cj(A.m[j][i]);
+    return D;
+}
 template <class T> DEV M3<T> mul_dn(const M3<T>& A, const M3<T>& B) {  // A^dag B
     M3<T> C;
 #pragma unroll
@@ -206,14 +214,26 @@ DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
                     dot8(q, transport_alg(C.link(0, -1, 0), C.phi(-1, 0)))) / te;
     qB[0] = -half * (dot8(q, conj_alg(C.link(1, 0, 0), C.phi(0, 1))) -
                      dot8(q, transport_alg(C.link(1, 0, -1), C.phi(0, -1)))) / te;
-    // B_z = -F_xy, F_xy = clover average of the four plaquettes based at c
-    T bz = dot8(q, im_tl(mul_nd(mul(C.link(0, 0, 0), C.link(1, 1, 0)), mul(C.link(1, 0, 0), C.link(0, 0, 1)))));
-    // +y,-x: U_y(c) [U_y(c-x) U_x(c-x+y)]^dag U_x(c-x)
-    bz += dot8(q, im_tl(mul(mul_nd(C.link(1, 0, 0), mul(C.link(1, -1, 0), C.link(0, -1, 1))), C.link(0, -1, 0))));
-    // -x,-y: [U_y(c-x-y) U_x(c-x)]^dag [U_x(c-x-y) U_y(c-y)]
-    bz += dot8(q, im_tl(mul_dn(mul(C.link(1, -1, -1), C.link(0, -1, 0)), mul(C.link(0, -1, -1), C.link(1, 0, -1)))));
-    // -y,+x: U_y(c-y)^dag [U_x(c-y) U_y(c+x-y)] U_x(c)^dag
-    bz += dot8(q, im_tl(mul_nd(mul_dn(C.link(1, 0, -1), mul(C.link(0, 0, -1), C.link(1, 1, -1))), C.link(0, 0, 0))));
+    // B_z = -F_xy, F_xy = clover average of the four plaquettes based at c, each
+    // counter-clockwise from c as P = (L0 L1)(L3 L2)^dag:
+    //   +x,+y: U_x(c) U_y(c+x) [U_y(c) U_x(c+y)]^dag
+    //   +y,-x: U_y(c) U_x(c-x+y)^dag U_y(c-x)^dag U_x(c-x) = [U_y(c) U_x(c-x+y)^dag] [U_x(c-x)^dag U_y(c-x)]^dag
+    //   -x,-y: U_x(c-x)^dag U_y(c-x-y)^dag U_x(c-x-y) U_y(c-y) = [U_x(c-x)^dag U_y(c-x-y)^dag] [U_y(c-y)^dag U_x(c-x-y)^dag]^dag
+    //   -y,+x: U_y(c-y)^dag U_x(c-y) U_y(c+x-y) U_x(c)^dag = [U_y(c-y)^dag U_x(c-y)] [U_x(c) U_y(c+x-y)^dag]^dag
+    // one plaquette per iteration, not unrolled: one copy of the products (fewer live
+    // matrices, no spilling of four inlined copies)
+    T bz = T(0);
+#pragma unroll 1
+    for (int k = 0; k < 4; k++) {
+        M3<T> A, B;
+        switch (k) {
+            case 0: A = mul(C.link(0, 0, 0), C.link(1, 1, 0)); B = mul(C.link(1, 0, 0), C.link(0, 0, 1)); break;
+            case 1: A = mul_nd(C.link(1, 0, 0), C.link(0, -1, 1)); B = mul_dn(C.link(0, -1, 0), C.link(1, -1, 0)); break;
+            case 2: A = mul_dn(C.link(0, -1, 0), dagger(C.link(1, -1, -1))); B = mul_dn(C.link(1, 0, -1), dagger(C.link(0, -1, -1))); break;
+            default: A = mul_dn(C.link(1, 0, -1), C.link(0, 0, -1)); B = mul_nd(C.link(0, 0, 0), C.link(1, 1, -1)); break;
+        }
+        bz += dot8(q, im_tl(mul_nd(A, B)));
+    }
     qB[2] = -T(0.25) * bz;
 }
 
