@@ -197,6 +197,23 @@ template <class T> struct StagedSrc {
     DEV View view(int, int) const { return View{rec}; }
 };
 
+// Plaquette k (0..3) of the clover at the view's cell, counter-clockwise from the cell,
+// written as (L0 L1)(L3 L2)^dag:
+//   0 +x,+y: U_x(c) U_y(c+x) [U_y(c) U_x(c+y)]^dag
+//   1 +y,-x: U_y(c) U_x(c-x+y)^dag U_y(c-x)^dag U_x(c-x) = [U_y(c) U_x(c-x+y)^dag] [U_x(c-x)^dag U_y(c-x)]^dag
+//   2 -x,-y: U_x(c-x)^dag U_y(c-x-y)^dag U_x(c-x-y) U_y(c-y) = [U_x(c-x)^dag U_y(c-x-y)^dag] [U_y(c-y)^dag U_x(c-x-y)^dag]^dag
+//   3 -y,+x: U_y(c-y)^dag U_x(c-y) U_y(c+x-y) U_x(c)^dag = [U_y(c-y)^dag U_x(c-y)] [U_x(c) U_y(c+x-y)^dag]^dag
+template <class T, class V> DEV M3<T> clover_plaquette(const V& C, int k) {
+    M3<T> A, B;
+    switch (k) {
+        case 0: A = mul(C.link(0, 0, 0), C.link(1, 1, 0)); B = mul(C.link(1, 0, 0), C.link(0, 0, 1)); break;
+        case 1: A = mul_nd(C.link(1, 0, 0), C.link(0, -1, 1)); B = mul_dn(C.link(0, -1, 0), C.link(1, -1, 0)); break;
+        case 2: A = mul_dn(C.link(0, -1, 0), dagger(C.link(1, -1, -1))); B = mul_dn(C.link(1, 0, -1), dagger(C.link(0, -1, -1))); break;
+        default: A = mul_dn(C.link(1, 0, -1), C.link(0, 0, -1)); B = mul_nd(C.link(0, 0, 0), C.link(1, 1, -1)); break;
+    }
+    return mul_nd(A, B);
+}
+
 // Q-contracted site-centred fields at the particle's cell for the push of step n:
 // qE = Q.(E_x, E_y, E_z), qB = Q.(B_x, B_y, B_z)
 template <class T, class V>
@@ -214,26 +231,11 @@ DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
                     dot8(q, transport_alg(C.link(0, -1, 0), C.phi(-1, 0)))) / te;
     qB[0] = -half * (dot8(q, conj_alg(C.link(1, 0, 0), C.phi(0, 1))) -
                      dot8(q, transport_alg(C.link(1, 0, -1), C.phi(0, -1)))) / te;
-    // B_z = -F_xy, F_xy = clover average of the four plaquettes based at c, each
-    // counter-clockwise from c as P = (L0 L1)(L3 L2)^dag:
-    //   +x,+y: U_x(c) U_y(c+x) [U_y(c) U_x(c+y)]^dag
-    //   +y,-x: U_y(c) U_x(c-x+y)^dag U_y(c-x)^dag U_x(c-x) = [U_y(c) U_x(c-x+y)^dag] [U_x(c-x)^dag U_y(c-x)]^dag
-    //   -x,-y: U_x(c-x)^dag U_y(c-x-y)^dag U_x(c-x-y) U_y(c-y) = [U_x(c-x)^dag U_y(c-x-y)^dag] [U_y(c-y)^dag U_x(c-x-y)^dag]^dag
-    //   -y,+x: U_y(c-y)^dag U_x(c-y) U_y(c+x-y) U_x(c)^dag = [U_y(c-y)^dag U_x(c-y)] [U_x(c) U_y(c+x-y)^dag]^dag
-    // one plaquette per iteration, not unrolled: one copy of the products (fewer live
-    // matrices, no spilling of four inlined copies)
+    // B_z = -F_xy, F_xy = clover average of the four plaquettes based at c (one per
+    // iteration, not unrolled: one copy of the products, fewer live matrices)
     T bz = T(0);
 #pragma unroll 1
-    for (int k = 0; k < 4; k++) {
-        M3<T> A, B;
-        switch (k) {
-            case 0: A = mul(C.link(0, 0, 0), C.link(1, 1, 0)); B = mul(C.link(1, 0, 0), C.link(0, 0, 1)); break;
-            case 1: A = mul_nd(C.link(1, 0, 0), C.link(0, -1, 1)); B = mul_dn(C.link(0, -1, 0), C.link(1, -1, 0)); break;
-            case 2: A = mul_dn(C.link(0, -1, 0), dagger(C.link(1, -1, -1))); B = mul_dn(C.link(1, 0, -1), dagger(C.link(0, -1, -1))); break;
-            default: A = mul_dn(C.link(1, 0, -1), C.link(0, 0, -1)); B = mul_nd(C.link(0, 0, 0), C.link(1, 1, -1)); break;
-        }
-        bz += dot8(q, im_tl(mul_nd(A, B)));
-    }
+    for (int k = 0; k < 4; k++) bz += dot8(q, im_tl(clover_plaquette<T>(C, k)));
     qB[2] = -T(0.25) * bz;
 }
 
@@ -293,13 +295,17 @@ template <class T, class V> DEV void site_fields(const V& C, T te, Al<T> E[3], A
 #pragma unroll
         for (int k = 0; k < 8; k++) B[0].a[k] = -half * (fw.a[k] - bw.a[k]) / te;  // -D_y phi / tau
     }
-    Al<T> acc = im_tl(mul_nd(mul(C.link(0, 0, 0), C.link(1, 1, 0)), mul(C.link(1, 0, 0), C.link(0, 0, 1))));
-    const Al<T> t2 = im_tl(mul(mul_nd(C.link(1, 0, 0), mul(C.link(1, -1, 0), C.link(0, -1, 1))), C.link(0, -1, 0)));
-    const Al<T> t3 =
-        im_tl(mul_dn(mul(C.link(1, -1, -1), C.link(0, -1, 0)), mul(C.link(0, -1, -1), C.link(1, 0, -1))));
-    const Al<T> t4 = im_tl(mul_nd(mul_dn(C.link(1, 0, -1), mul(C.link(0, 0, -1), C.link(1, 1, -1))), C.link(0, 0, 0)));
+    Al<T> acc;
 #pragma unroll
-    for (int k = 0; k < 8; k++) B[2].a[k] = -T(0.25) * (acc.a[k] + t2.a[k] + t3.a[k] + t4.a[k]);
+    for (int a = 0; a < 8; a++) acc.a[a] = T(0);
+#pragma unroll 1
+    for (int k = 0; k < 4; k++) {
+        const Al<T> t = im_tl(clover_plaquette<T>(C, k));
+#pragma unroll
+        for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 8; a++) B[2].a[a] = -T(0.25) * acc.a[a];
 }
 
 // one particle: gather, kick, drift, color transport; returns its broadening terms.
