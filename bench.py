@@ -11,6 +11,11 @@ Metric: site-updates/s (value) and particle-steps/s, whole job over N GPUs.
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
   python bench.py --workload warm_start  (tau = 0+ link solve of 16 events at 1024^2: Newton
                                           iterations and wall time, cold vs learned warm start)
+  python bench.py --workload single_512  (one 512^2 event, 100k charm + 100k beauty, FP32 and
+                                          FP64, nearest-grid-point and cloud-in-cell gathers)
+  python bench.py --workload jets        (4 events of 1024^2, 1M massless partons each)
+  python bench.py --workload scans       (the p_T and p_x scans of Figs. 1-2)
+  python bench.py --workload correlators (the estimators of Eqs. 4-5 on a 1024^2 event)
 
 N > 1: launched by torchrun, one rank per GPU; each rank runs an independent
 replica batch (different event seeds), no data-path collective ("weak").
