@@ -743,6 +743,7 @@ def run_scans(args, ws, rank, local):
     jets = [(1.5, p, 0.0) for p in (1.0, 2.0, 5.0, 10.0)]
     stream = torch.cuda.Stream()
     tabs = [[] for _ in range(len(hq) + len(jets))]
+    ctabs = []  # lattice-correlator estimators (Eqs. 4-5) of each event, from the beauty formation step
     n_steps = int(math.ceil(1.0 / (0.125 * L / n) - 1e-9))
     ms_total, psteps = 0.0, 0
     for e in range(n_ev):
@@ -756,6 +757,7 @@ def run_scans(args, ws, rank, local):
                        seed=((6 << 32) + 100 * e + k + 1000 * rank) ^ 0x5A5A5A5A5A5A5A5A)
             c.init()
             cs.append(c)
+        corr = G.Correlators(g, tau_start_fm=hq[0][2], ox0=0.5)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -767,7 +769,8 @@ def run_scans(args, ws, rank, local):
             t = c.broadening()
             tabs[k].append(t)
             psteps += int(t[1:, 4].sum())
-        del cs, g
+        ctabs.append(corr.table())
+        del corr, cs, g
 
     def pooled(ts):
         out = ts[0].copy()
@@ -791,6 +794,25 @@ def run_scans(args, ws, rank, local):
                  "anisotropy_at_0.3fm": float(a[j, 1]), "anisotropy_at_end": float(a[-1, 1]),
                  "dp2_at_end_GeV2": t[-1, 1:4].tolist()}
         res["jets" if jet else "heavy_quarks"].append(entry)
+    # the paper's qualitative claims (Sec. 2): static quarks (Eq. 4) less anisotropic than
+    # dynamical ones at p_T = 0 and more than the fastest; dynamical jets more anisotropic
+    # than lightlike ones (Eq. 5); late kappa_L < 0 (heavy quarks)
+    ct = sum(ctabs) / len(ctabs)
+    jc = int(np.argmin(np.abs((ct[:, 0] - ct[0, 0]) - 0.3)))
+    static_an = float(ct[jc, 3] / (ct[jc, 1] + ct[jc, 2]))
+    light_an = float(ct[jc, 6] / ct[jc, 5])
+    hq_an = [e["anisotropy_at_0.3fm"] for e in res["heavy_quarks"]]
+    jet_an = [e["anisotropy_at_0.3fm"] for e in res["jets"]]
+    late_kl = []
+    for k in range(len(hq)):
+        q = G.kappa_qhat(pooled(tabs[k]))
+        late_kl.append(float(q[q[:, 0] >= 0.7, 3].mean()))
+    checks = {"static_anisotropy_at_0.3fm": static_an, "lightlike_anisotropy_at_0.3fm": light_an,
+              "static_less_anisotropic_than_pT0": static_an < hq_an[0],
+              "pT10_less_anisotropic_than_static": hq_an[-1] < static_an,
+              "anisotropy_ordered_with_1/pT": all(a > b for a, b in zip(hq_an, hq_an[1:])),
+              "jets_more_anisotropic_than_lightlike": all(a > light_an for a in jet_an),
+              "late_kappa_L_GeV2_per_fm (tau >= 0.7 fm/c, p_T = 0/2/5/10)": late_kl}
     if rank == 0:
         line = {
             "metric": "parameter scans of Figs. 1-2: particle-steps/s (8 ensembles x 25k on 4 events of 512^2)",
@@ -801,6 +823,7 @@ def run_scans(args, ws, rank, local):
                                    "GeV (tau_form=1/2m), quarks m=1.5 GeV p_x in {1,2,5,10} GeV (tau_form=0); 25k "
                                    "each, FP32 to 1 fm/c"},
             "results": res,
+            "qualitative_checks": checks,
             "paper_context": {"kappa_total_peak_GeV2_per_fm": "19-22 at delta tau 0.03-0.05 fm/c (beauty, m=4.2 GeV)",
                               "qhat_total_peak_GeV2_per_fm": "24-30 at tau 0.04 fm/c",
                               "note": "Q_s = 2 GeV there, lattice parameters not given: qualitative only"},
