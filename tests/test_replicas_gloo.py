@@ -42,7 +42,7 @@ def _rank(rank, ws, port, out):
 def test_two_gloo_replicas_barrier_max_and_distinct_seeds():
     ws = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)
@@ -80,7 +80,7 @@ def test_pool_broadening_is_the_count_weighted_mean_over_replicas():
 
     ws = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_pool_rank, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)
