@@ -367,6 +367,12 @@ glasma_status glasma_batch_import_state(glasma_batch* b, const void* host, int64
  * total time of the other kernels.  Synchronises. */
 glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, double* main_ms, int64_t* main_launches,
                                    int64_t* main_sites, int64_t* main_particle_steps, double* other_ms);
+/* Pushes on a second stream (graph and eager modes), with separate != 0: the push of
+ * iteration k waits for field launch k, field launch k+2 for push k (the buffer it writes
+ * is the one push k reads), so a push overlaps the next field launch; the run still ends
+ * on the batch stream.  Results are unchanged.  The graph is captured again when this
+ * changes. */
+glasma_status glasma_batch_set_push_stream(glasma_batch* b, int32_t separate);
 /* Kernel timing inside the timed runs themselves: with on != 0, the batched path (graph and
  * eager modes) brackets every batched field launch with CUDA event records, captured in
  * the graph as event-record nodes (the graph is captured again when this changes).

@@ -377,6 +377,9 @@ class Batch:
     def import_state(self, host_tensor):
         check(lib().glasma_batch_import_state(self.handle, C.c_void_p(host_tensor.data_ptr()), host_tensor.numel()))
 
+    def set_push_stream(self, separate=True):
+        check(lib().glasma_batch_set_push_stream(self.handle, 1 if separate else 0))
+
     def set_graph_timing(self, on=True):
         check(lib().glasma_batch_set_graph_timing(self.handle, 1 if on else 0))
 

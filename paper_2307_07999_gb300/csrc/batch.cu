@@ -394,10 +394,23 @@ static cudaError_t enqueue_batched(glasma_batch* b) {
     cudaError_t e = enqueue_restore(b);
     if (e != cudaSuccess) return e;
     const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
+    const bool two = b->two_streams && b->st2 != nullptr;
+    cudaStream_t sp = two ? b->st2 : b->st;  // the stream of the pushes
+    const int K = b->max_iter;
+    if (two) {  // the pushes see the restore
+        e = cudaEventRecord(b->sev[2 * (size_t)K], b->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st2, b->sev[2 * (size_t)K], 0);
+        if (e != cudaSuccess) return e;
+    }
+    int last_push = -1;
     b->tev_used = 0;
     for (int k = 0; k < b->max_iter; k++) {
         const int act = b->active[k];
         if (act == 0) break;
+        if (two && k >= 2) {  // field k overwrites the buffer push k-2 reads
+            e = cudaStreamWaitEvent(b->st, b->sev[2 * (size_t)(k - 2) + 1], 0);
+            if (e != cudaSuccess) return e;
+        }
         // (timing: external event records, so that a captured graph keeps them as nodes)
         if (b->timing) {
             e = cudaEventRecordWithFlags(b->tev[2 * k], b->st, cudaEventRecordExternal);
@@ -411,8 +424,22 @@ static cudaError_t enqueue_batched(glasma_batch* b) {
             if (e != cudaSuccess) return e;
             b->tev_used = k + 1;
         }
+        if (two) {
+            e = cudaEventRecord(b->sev[2 * (size_t)k], b->st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(sp, b->sev[2 * (size_t)k], 0);
+            if (e != cudaSuccess) return e;
+        }
         e = launch_push_batched(b->prec, b->any_sub ? PUSH_VARIANT_SUB : b->pvar, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
-                                b->pitems_upto[act], b->st);
+                                b->pitems_upto[act], sp);
+        if (e != cudaSuccess) return e;
+        if (two) {
+            e = cudaEventRecord(b->sev[2 * (size_t)k + 1], sp);
+            if (e != cudaSuccess) return e;
+            last_push = k;
+        }
+    }
+    if (two && last_push >= 0) {  // join: the run ends with its last push
+        e = cudaStreamWaitEvent(b->st, b->sev[2 * (size_t)last_push + 1], 0);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -653,6 +680,21 @@ extern "C" glasma_status glasma_batch_set_variant(glasma_batch* b, int32_t v) {
     }
     return build_gtiles(b);
 }
+extern "C" glasma_status glasma_batch_set_push_stream(glasma_batch* b, int32_t separate) {
+    if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
+    if ((separate != 0) == b->two_streams) return GLASMA_OK;
+    if (separate && !b->st2) {
+        BCK(cudaStreamCreateWithFlags(&b->st2, cudaStreamNonBlocking));
+        b->sev.assign(2 * (size_t)std::max(1, b->max_iter) + 1, nullptr);
+        for (auto& e : b->sev) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    b->two_streams = separate != 0;
+    if (b->graph_unfused_ready) {  // captured again with (or without) the second stream
+        cudaGraphExecDestroy(b->exec_unfused);
+        b->graph_unfused_ready = false;
+    }
+    return GLASMA_OK;
+}
 extern "C" glasma_status glasma_batch_set_graph_timing(glasma_batch* b, int32_t on) {
     if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
     if ((on != 0) == b->timing) return GLASMA_OK;
@@ -813,6 +855,9 @@ extern "C" void glasma_batch_destroy(glasma_batch* b) {
     if (b->graph_unfused_ready) cudaGraphExecDestroy(b->exec_unfused);
     for (auto& e : b->tev)
         if (e) cudaEventDestroy(e);
+    for (auto& e : b->sev)
+        if (e) cudaEventDestroy(e);
+    if (b->st2) cudaStreamDestroy(b->st2);
     batch_free_persistent(b);
     delete b;
 }

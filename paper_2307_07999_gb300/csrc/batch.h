@@ -41,6 +41,11 @@ struct glasma_batch {
     int fvar = 0;                 // FP32 field tile variant of the graph and eager paths
     int pvar = 0;                 // batched push kernel of the graph and eager paths
     bool any_sub = false;         // some event takes several particle steps per field step or the CIC gather
+    // pushes on a second stream (graph and eager modes): push k after field k, field k+2
+    // after push k (the buffer field k+2 writes is the one push k reads as fo)
+    bool two_streams = false;
+    cudaStream_t st2 = nullptr;
+    std::vector<cudaEvent_t> sev;  // [2 * max_iter + 1]: after field k, after push k, after the restore
     // graph timing: event-record nodes around every field launch of the batched path
     bool timing = false;
     std::vector<cudaEvent_t> tev;  // [2 * max_iter]: start, end of field launch k

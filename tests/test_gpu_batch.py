@@ -247,3 +247,20 @@ def test_graph_timing_nodes(fp64_batch):
     B.run("graph")
     with pytest.raises(G.GlasmaError):
         B.graph_times()
+
+
+def test_push_stream_gives_the_same_run(fp64_batch):
+    """Pushes on a second stream (push k after field k, field k+2 after push k): the same
+    particles bit for bit and the same broadening tables, in graph and eager modes."""
+    B, evs, pps = fp64_batch
+    B.run("graph")
+    want = [(B.broadening(e), B.get_particles(e)) for e in range(len(evs))]
+    B.set_push_stream(True)
+    for mode in ("graph", "eager", "graph"):
+        B.run(mode)
+        for e in range(len(evs)):
+            tab, part = B.broadening(e), B.get_particles(e)
+            assert rel_err(tab[:, 1:4], want[e][0][:, 1:4]) < 1e-13, (mode, e)
+            for k in part:
+                assert np.array_equal(part[k], want[e][1][k]), (mode, e, k)
+    B.set_push_stream(False)
