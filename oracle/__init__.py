@@ -70,6 +70,7 @@ def _declare(L):
         "o_corr_step": (None, [_i, _i, _d, _i] + [_p] * 9 + [_i, _i, _p]),
         "o_push": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p]),
         "o_push_int": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p, _i]),
+        "o_set_threads": (_i, [_i]),
         "o_push_sub": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p, _i, _i]),
         "o_push_ext": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p, _i, _i, _i]),
         "o_gather_cic": (None, [_i, _d, _i] + [_p] * 6 + [_i, _i, _d, _d, _p]),
@@ -505,3 +506,8 @@ def ic_target(U1, U2, U):
     args = [np.ascontiguousarray(m, dtype=np.complex128) for m in (U1, U2, U)]
     lib().o_ic_target(*[_ptr(m) for m in args], _ptr(d))
     return d
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's loops (n <= 0: query); returns the count in effect."""
+    return lib().o_set_threads(n)

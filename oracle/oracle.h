@@ -126,6 +126,8 @@ void o_push_sub(int np, int n, int expanding, double dtau, int step, double mass
                 double *x, double *y, double *eta, double *px, double *py, double *peta,
                 double *Q, const double *p0, double acc[4], int integrator, int substeps);
 void o_casimirs(const double Q[8], double *q2, double *q3);
+/* OpenMP threads of the oracle's loops (timing only); returns the count in effect */
+int o_set_threads(int n);
 double o_pz_lab(double mass, double px, double py, double peta, double eta);
 
 /* ---------------- correlators.c : Eqs. 4 and 5 ---------------- */

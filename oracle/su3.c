@@ -229,3 +229,18 @@ void o_icomm(const double a[8], const double b[8], double out[8]) {
     for (int k = 0; k < 9; k++) C[k] = I * (AB[k] - BA[k]);
     o_mat_to_alg(C, out);
 }
+
+/* Threads of the OpenMP loops (timing the oracle on one core or all cores; no effect
+ * without OpenMP).  Returns the count in effect. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int o_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
