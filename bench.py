@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--mode", default="auto", choices=["auto", "graph", "persistent", "eager", "per_event", "fused"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--g2mu", type=float, default=2.0, help="MV scale g^2 mu (GeV) of the scans workload")
     p.add_argument("--field-variant", type=int, default=-1,
                    help="fixed field tile variant (default: tuned on the batch)")
     p.add_argument("--push-variant", type=int, default=-1, help="fixed push kernel with --field-variant")
@@ -765,8 +766,8 @@ def run_scans(args, ws, rank, local):
     n_steps = int(math.ceil(1.0 / (0.125 * L / n) - 1e-9))
     ms_total, psteps = 0.0, 0
     for e in range(n_ev):
-        g = G.Glasma(n, L, precision=G.GLASMA_FP32, tau_end_fm=1.0, seed=(6 << 32) + e + 1000 * rank,
-                     reunit_every=64, stream=stream)
+        g = G.Glasma(n, L, g2mu_GeV=args.g2mu, precision=G.GLASMA_FP32, tau_end_fm=1.0,
+                     seed=(6 << 32) + e + 1000 * rank, reunit_every=64, stream=stream)
         assert g.init()[0] == 0
         cs = []
         for k, (m, p, tf) in enumerate(hq + jets):
@@ -837,9 +838,9 @@ def run_scans(args, ws, rank, local):
             "value": psteps * ws / (ms_total / 1000.0), "unit": "particle-steps/s", "n_gpus": ws, "steps": 1,
             "warmup": 0, "ms_per_step": ms_total, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (FP64 accumulators)", "data": "synthetic",
-            "config": {"workload": "4 MV events of 512^2 (L=10 fm, g2mu=2 GeV); beauty m=4.2 GeV p_T in {0,2,5,10} "
-                                   "GeV (tau_form=1/2m), quarks m=1.5 GeV p_x in {1,2,5,10} GeV (tau_form=0); 25k "
-                                   "each, FP32 to 1 fm/c"},
+            "config": {"workload": f"4 MV events of 512^2 (L=10 fm, g2mu={args.g2mu:g} GeV); beauty m=4.2 GeV p_T in "
+                                   "{0,2,5,10} GeV (tau_form=1/2m), quarks m=1.5 GeV p_x in {1,2,5,10} GeV "
+                                   "(tau_form=0); 25k each, FP32 to 1 fm/c"},
             "results": res,
             "qualitative_checks": checks,
             "paper_context": {"kappa_total_peak_GeV2_per_fm": "19-22 at delta tau 0.03-0.05 fm/c (beauty, m=4.2 GeV)",
