@@ -75,6 +75,8 @@ def _declare(L):
         "o_push_ext": (None, [_i, _i, _i, _d, _i, _d] + [_p] * 6 + [_p] * 7 + [_p, _p, _i, _i, _i]),
         "o_gather_cic": (None, [_i, _d, _i] + [_p] * 6 + [_i, _i, _d, _d, _p]),
         "o_casimirs": (None, [_p, _p, _p]),
+        "o_derivative": (None, [_i, _p, _i, _p, _i, _p, _i]),
+        "o_transport_coefficients": (None, [_i, _p, _i, _i, _p]),
         "o_pz_lab": (_d, [_d, _d, _d, _d, _d]),
         "o_mlp_forward": (None, [_i] + [_p] * 10),
         "o_mlp_loss_backward": (_d, [_i] + [_p] * 14),
@@ -454,6 +456,32 @@ def casimirs(Q):
 
 def pz_lab(mass, px, py, peta, eta):
     return lib().o_pz_lab(mass, px, py, peta, eta)
+
+
+# ---------------------------------------------------------------- Eq. 3 estimators
+def derivative(tau, f):
+    """d f / d tau on the grid tau: central differences inside, one-sided at the ends."""
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(len(tau))
+    lib().o_derivative(len(tau), _ptr(tau), 1, _ptr(f), 1, _ptr(out), 1)
+    return out
+
+
+def transport_coefficients(table, kind="hq"):
+    """Eq. 3 on a broadening table (rows {tau, <dpx^2>, <dpy^2>, <dpz^2>, ...}): rows
+    {tau, d<dpx^2>/dtau, d<dpy^2>/dtau, d<dpz^2>/dtau, transverse, longitudinal, total,
+    anisotropy}; kind "hq" (kappa_T, kappa_L, <dp_L^2>/<dp_T^2>) or "jet" (qhat_y, qhat_z,
+    <dp_z^2>/<dp_y^2>)."""
+    t = np.ascontiguousarray(table, dtype=np.float64)
+    out = np.zeros((t.shape[0], 8))
+    lib().o_transport_coefficients(t.shape[0], _ptr(t), t.shape[1], 0 if kind == "hq" else 1, _ptr(out))
+    return out
+
+
+def kappa_qhat(table):
+    """Rows {tau, d<dpx^2>/dtau, d<dpy^2>/dtau, d<dpz^2>/dtau} of Eq. 3."""
+    return transport_coefficients(table)[:, :4]
 
 
 # ---------------------------------------------------------------- warm-start network

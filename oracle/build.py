@@ -7,7 +7,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["su3.c", "philox.c", "fft.c", "ic.c", "field.c", "particles.c", "correlators.c", "mlp.c"]
+SOURCES = ["su3.c", "philox.c", "fft.c", "ic.c", "field.c", "particles.c", "correlators.c", "estimators.c", "mlp.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

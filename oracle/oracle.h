@@ -137,6 +137,15 @@ void o_corr_step(int n, int expanding, double dtau, int step, const cplx *U, con
                  const double *En, const double *phi, const double *pio, const double *pin,
                  double *Istat, cplx *W, double *J, int k_now, int k_next, double out[6]);
 
+/* ---------------- estimators.c : Eq. 3 transport coefficients ---------------- */
+/* d f / d tau on the table's tau grid: central inside, one-sided at the ends */
+void o_derivative(int rows, const double *tau, int tstride, const double *f, int fstride, double *df,
+                  int dstride);
+/* tab rows {tau, <dpx^2>, <dpy^2>, <dpz^2>, ...} (stride doubles); kind 0 heavy quarks,
+ * 1 jets along x; out rows {tau, d/dtau of the three, transverse, longitudinal, total,
+ * anisotropy} (8 doubles) */
+void o_transport_coefficients(int rows, const double *tab, int stride, int kind, double *out);
+
 /* ---------------- mlp.c : learned warm-start network ---------------- */
 void o_mlp_forward(int batch, const double *x, const double *W1, const double *b1,
                    const double *W2, const double *b2, const double *W3,
