@@ -145,8 +145,12 @@ glasma_status glasma_init_from_host(glasma_ctx* g, const double* U, const double
 glasma_status glasma_get_state(glasma_ctx* g, double* U, double* E, double* phi, double* pi,
                                int32_t* step);
 
-/* Advances the fields by n_steps leapfrog steps (kick at tau_n, drift with
- * tau_{n+1/2}); enqueue only. */
+/* Advances the fields by n_steps leapfrog steps (Sec. 1, "Glasma": the boost-invariant
+ * Yang-Mills equations on the transverse lattice of gauge links and plaquettes; kick of
+ * E_i and pi at tau_n by minus the group derivative of the lattice potential, built from
+ * the plaquettes, their staples and the covariant differences of phi; drift of U_i and
+ * phi with tau_{n+1/2}).  Enqueue only.  GLASMA_ERR_INVALID before an initial state
+ * (or at tau = 0 in the expanding evolution); a failed launch, GLASMA_ERR_CUDA. */
 glasma_status glasma_step(glasma_ctx* g, int32_t n_steps);
 
 /* FP64 monitors of the current state (synchronises):
@@ -202,9 +206,13 @@ glasma_status cpic_init_from_host(cpic_ctx* c, const double* x, const double* y,
 glasma_status cpic_get_particles(cpic_ctx* c, double* x, double* y, double* eta, double* px,
                                  double* py, double* peta, double* Q);
 
-/* Coupled step: n_steps x (field step; if tau_n >= tau_form, push every particle
- * with the fields of tau_n and add its broadening terms to the row of tau_{n+1}).
- * Enqueue only. */
+/* Coupled step (Sec. 1, "Probes in Glasma", Eq. 2: Wong's equations solved by the
+ * colored particle-in-cell method): n_steps x (field step as glasma_step; then, if
+ * tau_n >= tau_form, push every particle: gather E and B at its nearest-grid-point cell
+ * from the fields of tau_n, kick p by the color Lorentz force Q.(E + v x B) in Milne
+ * coordinates, drift x, y, eta, and rotate Q by exp(-i phi deta) and by the link of every
+ * cell face it crosses; then add its broadening terms to the row of tau_{n+1}).
+ * Enqueue only; GLASMA_ERR_INVALID on a negative count or an uninitialised context. */
 glasma_status cpic_push(cpic_ctx* c, int32_t n_steps);
 
 /* Coupled step for several ensembles in the same event (Sec. 2: charm and beauty quarks,
@@ -215,12 +223,35 @@ glasma_status cpic_push(cpic_ctx* c, int32_t n_steps);
  * rejected with GLASMA_ERR_INVALID before any work is enqueued.  Enqueue only. */
 glasma_status cpic_push_many(cpic_ctx* const* cs, int32_t n_ctx, int32_t n_steps);
 
-/* Broadening table (synchronises): rows r = 0..n-1 from the first pushed step (tau_form,
- * or the field step at particle initialisation if later) to the current
- * step, each {tau_fm, <dp_x^2>, <dp_y^2>, <dp_z^2> (GeV^2), particle count},
- * p_z the lab longitudinal momentum.  cap_rows: rows available in host_out. */
+/* Broadening table (Sec. 2, "Quantifying the effect of Glasma": dp_i^2(tau) =
+ * p_i^2(tau) - p_i^2(tau_form), averaged over the particles; the FP64 sums are
+ * accumulated on the GPU at every push).  Synchronises.  Rows r = 0..n-1 from the first
+ * pushed step (tau_form, or the field step at particle initialisation if later) to the
+ * current step, each {tau_fm, <dp_x^2>, <dp_y^2>, <dp_z^2> (GeV^2), particle count},
+ * p_z the lab longitudinal momentum.  host_out: caller-owned double[cap_rows][5];
+ * GLASMA_ERR_NOSPACE if cap_rows is too small (nothing useful written). */
 glasma_status broadening_accumulate(cpic_ctx* c, double* host_out, int64_t cap_rows,
                                     int64_t* n_rows);
+
+/* Transport coefficients of Eq. 3 (Sec. 2): kappa_i = d<dp_i^2>/dtau for heavy quarks,
+ * with i = L (the beam axis z) and T (x + y); qhat_i for jets along x, with i = z, y.  Also
+ * the paragraph's anisotropy, <dp_L^2>/<dp_T^2> (heavy quarks) or <dp_z^2>/<dp_y^2> (jets).
+ * The derivative is taken on the table's own tau grid: (f[r+1] - f[r-1])/(tau[r+1] -
+ * tau[r-1]) inside, the one-sided secant at the first and last rows (0 for a one-row
+ * table); "total" is the sum of the transverse and longitudinal coefficients.
+ *   table: host double[rows][stride], stride >= 4, rows {tau, <dp_x^2>, <dp_y^2>, <dp_z^2>,
+ *          ...} with tau strictly increasing (broadening_accumulate and
+ *          glasma_batch_broadening write stride 5; any pooled table of that form works);
+ *   kind:  GLASMA_HEAVY_QUARKS or GLASMA_JETS_X;
+ *   out:   host double[rows][8] = {tau, d<dp_x^2>/dtau, d<dp_y^2>/dtau, d<dp_z^2>/dtau,
+ *          transverse, longitudinal, total, anisotropy} (units of the table per unit of
+ *          its tau: GeV^2/fm for the tables above; the anisotropy is NaN where the
+ *          transverse broadening is zero, e.g. at the formation row).
+ * Host computation in FP64, no device work; GLASMA_ERR_INVALID on a null pointer, a bad
+ * kind or stride, or a tau column that does not increase. */
+enum { GLASMA_HEAVY_QUARKS = 0, GLASMA_JETS_X = 1 };
+glasma_status broadening_transport(const double* table, int64_t rows, int32_t stride, int32_t kind,
+                                   double* out);
 
 /* Checkpoint and resume of a coupled run (the paper has no counterpart: a long evolution,
  * e.g. 820 steps of 1024^2 with millions of partons, can be stopped and continued with

@@ -26,6 +26,7 @@ from .api import (  # noqa: F401
     ic_dataset,
     init_warm,
     broadening_accumulate,
+    broadening_transport,
     cpic_create,
     cpic_init,
     cpic_push,

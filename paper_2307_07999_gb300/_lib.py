@@ -8,6 +8,9 @@ LIB_PATH = os.path.join(HERE, "libglasma.so")
 GLASMA_FP64 = 0
 GLASMA_FP32 = 1
 
+GLASMA_HEAVY_QUARKS = 0
+GLASMA_JETS_X = 1
+
 GLASMA_BATCH_GRAPH = 0
 GLASMA_BATCH_PERSISTENT = 1
 GLASMA_BATCH_PER_EVENT = 2
@@ -104,6 +107,7 @@ SIGNATURES = {
     "cpic_export_state": (C.c_int, [_p, _p, _i64]),
     "cpic_import_state": (C.c_int, [_p, _p, _i64]),
     "broadening_accumulate": (C.c_int, [_p, _p, _i64, C.POINTER(_i64)]),
+    "broadening_transport": (C.c_int, [_p, _i64, _i32, _i32, _p]),
     "cpic_casimir_drift": (C.c_int, [_p, _p]),
     "cpic_destroy": (None, [_p]),
     "glasma_batch_workspace_bytes": (_i64, [C.POINTER(GlasmaParams), C.POINTER(CpicParams), _i32]),

@@ -9,7 +9,7 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import CorrParams, CpicParams, GlasmaParams, check, lib
+from ._lib import GLASMA_HEAVY_QUARKS, GLASMA_JETS_X, CorrParams, CpicParams, GlasmaParams, check, lib
 
 HBARC = 0.1973269804  # GeV fm
 
@@ -465,28 +465,31 @@ def pool_broadening(table, group=None):
     return out
 
 
+def broadening_transport(table, kind="hq"):
+    """Eq. 3 through the library's broadening_transport: rows {tau, d<dpx^2>/dtau,
+    d<dpy^2>/dtau, d<dpz^2>/dtau, transverse, longitudinal, total, anisotropy}; kind "hq"
+    (kappa_T, kappa_L, <dp_L^2>/<dp_T^2>) or "jet" (qhat_y, qhat_z, <dp_z^2>/<dp_y^2>)."""
+    t = np.ascontiguousarray(table, dtype=np.float64)
+    out = np.zeros((t.shape[0], 8))
+    if t.shape[0] == 0:
+        return out
+    if kind not in ("hq", "jet"):
+        raise ValueError("kind must be 'hq' or 'jet'")
+    k = GLASMA_HEAVY_QUARKS if kind == "hq" else GLASMA_JETS_X
+    check(lib().broadening_transport(_dp(t), t.shape[0], t.shape[1], k, _dp(out)))
+    return out
+
+
 def anisotropy(table, kind="hq"):
-    """Ratio of longitudinal over transverse broadening (Sec. 2): heavy quarks
-    <dp_z^2> / (<dp_x^2> + <dp_y^2>); jets along x <dp_z^2> / <dp_y^2>.  table rows
-    {tau_fm, <dpx^2>, <dpy^2>, <dpz^2>, ...}; returns rows {tau_fm, ratio} (NaN where the
-    transverse broadening is zero)."""
-    t = np.asarray(table)
-    den = t[:, 1] + t[:, 2] if kind == "hq" else t[:, 2]
-    with np.errstate(divide="ignore", invalid="ignore"):
-        r = np.where(den != 0, t[:, 3] / np.where(den != 0, den, 1.0), np.nan)
-    return np.stack([t[:, 0], r], axis=1)
+    """Rows {tau_fm, ratio}: <dp_L^2>/<dp_T^2> for heavy quarks, <dp_z^2>/<dp_y^2> for
+    jets along x (NaN where the transverse broadening is zero); broadening_transport."""
+    return broadening_transport(table, kind)[:, [0, 7]]
 
 
 def kappa_qhat(table):
-    """d/dtau of the broadening table (Eq. 3): central differences inside, one-sided
-    at the ends.  table rows {tau_fm, <dpx^2>, <dpy^2>, <dpz^2>, count}; returns
-    rows {tau_fm, d<dpx^2>/dtau, d<dpy^2>/dtau, d<dpz^2>/dtau} in GeV^2/fm."""
-    t = table[:, 0]
-    out = np.zeros((len(t), 4))
-    out[:, 0] = t
-    if len(t) >= 2:
-        out[:, 1:] = np.gradient(table[:, 1:4], t, axis=0, edge_order=1)
-    return out
+    """Rows {tau_fm, d<dpx^2>/dtau, d<dpy^2>/dtau, d<dpz^2>/dtau} (GeV^2/fm) of Eq. 3;
+    broadening_transport."""
+    return broadening_transport(table)[:, :4]
 
 
 def field_tile_shape(precision, v):

@@ -102,7 +102,7 @@ def test_batch_fp32_matches_oracle():
         want, P, st = oracle_event(evs[e], pps[e], 1e-14)
         got = B.broadening(e)
         e_dp = rel_err(got[:, 1:4], want[:, 1:4])
-        e_k = rel_err(G.kappa_qhat(got)[:, 1:], G.kappa_qhat(want)[:, 1:])
+        e_k = rel_err(G.kappa_qhat(got)[:, 1:], O.kappa_qhat(want)[:, 1:])
         d = B.diagnostics(e)
         print(f"event {e}: dp2 {e_dp:.2e} kappa {e_k:.2e} gauss {d[0]:.2e} unitarity {d[5]:.2e}")
         assert e_dp < 1e-4 and e_k < 1e-4

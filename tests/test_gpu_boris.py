@@ -120,7 +120,7 @@ def test_config1_boris(config1, prec, tol):
     tab = c.broadening()
     assert tab.shape == want.shape
     e_dp = rel_err(tab[:, 1:4], want[:, 1:4])
-    e_k = rel_err(G.kappa_qhat(tab)[:, 1:], G.kappa_qhat(want)[:, 1:])
+    e_k = rel_err(G.kappa_qhat(tab)[:, 1:], O.kappa_qhat(want)[:, 1:])
     print(f"boris prec {prec}: dp2 {e_dp:.2e} kappa {e_k:.2e}")
     assert e_dp < tol and e_k < tol
     if prec:

@@ -105,8 +105,8 @@ def test_config2_fp32_against_fp64(oracle_run, interp, kappa_tol):
         assert t64.shape == t32.shape and t64.shape[0] == 410 - int(round(tau_form(SPECIES[name][0]) /
                                                                            (0.125 * L / N))) + 1
         e_dp = rel_err(t32[:, 1:4], t64[:, 1:4])
-        e_k = rel_err(G.kappa_qhat(t32)[:, 1:], G.kappa_qhat(t64)[:, 1:])
-        a64, a32 = G.anisotropy(t64)[1:, 1], G.anisotropy(t32)[1:, 1]
+        e_k = rel_err(G.kappa_qhat(t32)[:, 1:], O.kappa_qhat(t64)[:, 1:])
+        a64, a32 = O.transport_coefficients(t64)[1:, 7], G.anisotropy(t32)[1:, 1]
         e_a = rel_err(a32, a64)
         print(f"{name}: dp2 {e_dp:.2e} kappa {e_k:.2e} anisotropy {e_a:.2e} "
               f"(final <dp_L^2>/<dp_T^2> = {a64[-1]:.3f})")

@@ -68,7 +68,7 @@ def test_jets_small_vs_oracle(prec):
             assert rel_err(part["px"], P.px) < 1e-10 and rel_err(part["Q"], P.Q) < 1e-10
         else:
             assert rel_err(got[:, 1:4], want[:, 1:4]) < 1e-4, e
-            q_got, q_want = G.kappa_qhat(got), G.kappa_qhat(want)
+            q_got, q_want = G.kappa_qhat(got), O.kappa_qhat(want)
             assert rel_err(q_got[:, 2:], q_want[:, 2:]) < 1e-4, e  # q^_y, q^_z
     # the three ensembles saw the same fields: same monitors
     d = [B.diagnostics(e) for e in range(3)]

@@ -213,7 +213,7 @@ def test_config1_broadening_fp64():
     assert tab.shape == want.shape
     assert np.abs(tab[:, 0] - want[:, 0]).max() < 1e-12
     assert rel_err(tab[:, 1:4], want[:, 1:4]) < 1e-10
-    k_gpu, k_ref = G.kappa_qhat(tab), G.kappa_qhat(want)
+    k_gpu, k_ref = G.kappa_qhat(tab), O.kappa_qhat(want)
     assert rel_err(k_gpu[:, 1:], k_ref[:, 1:]) < 1e-10
     drift = c.casimir_drift()
     assert drift[0] < 1e-11 and drift[1] < 1e-11
@@ -232,7 +232,7 @@ def test_config1_broadening_fp32_tolerance():
     c.push(int(np.ceil(1.0 / (0.125 * 6.0 / 32) - 1e-9)) - n_form)
     tab = c.broadening()
     e_dp = rel_err(tab[:, 1:4], want[:, 1:4])
-    e_k = rel_err(G.kappa_qhat(tab)[:, 1:], G.kappa_qhat(want)[:, 1:])
+    e_k = rel_err(G.kappa_qhat(tab)[:, 1:], O.kappa_qhat(want)[:, 1:])
     d = g.diagnostics()
     print("fp32 errors: dp2", e_dp, "kappa", e_k, "gauss", d[0], "unitarity", d[5])
     assert d[0] < 1e-5
