@@ -174,13 +174,17 @@ void glasma_destroy(glasma_ctx* g);
  *           ((p / 8) * n*n + s) * 8 + p % 8), read only, 16-byte aligned.
  *   tau: tau in lattice units (divides E and D phi in the expanding case).
  *   out: host double[8], as glasma_diagnostics.
+ *   expanding: 1 the Milne evolution (tau > 0 required), 0 the static box.
  * Scratch: a file-scope device array of 4096 x 8 doubles (256 KB) that every
  * GPU which loads the library holds until the process exits; n*n above
- * 1,048,576 sites, or an unaligned buffer, is rejected with GLASMA_ERR_INVALID.  The
- * first call on a
- * device resolves the array's address on that device (make it before any
- * stream capture).  All calls share the array: calls that overlap on the GPU
- * (other streams or threads) race.  Allocates nothing; synchronises stream. */
+ * 1,048,576 sites, or an unaligned buffer, is rejected with GLASMA_ERR_INVALID, and so is
+ * a buffer that is not device (or managed) memory of the current device.  Each call
+ * looks up the array's address on the current device (cudaGetSymbolAddress, which
+ * allocates nothing), so it stays right across a device reset.  All calls share the
+ * array: calls that overlap on the GPU (other streams or threads) race.  Allocates
+ * nothing.  Synchronous: it copies the result to the host and waits for the stream, so
+ * it cannot be captured (a capturing stream is refused with GLASMA_ERR_INVALID).
+ * Non-finite values: GLASMA_ERR_NONFINITE with out filled. */
 glasma_status glasma_diagnostics_noalloc(const void* fields, int32_t n, int32_t precision,
                                          int32_t expanding, double tau, void* stream, double out[8]);
 
@@ -413,6 +417,15 @@ glasma_status glasma_batch_set_push_stream(glasma_batch* b, int32_t separate);
  * measurement. */
 glasma_status glasma_batch_set_graph_timing(glasma_batch* b, int32_t on);
 glasma_status glasma_batch_graph_times(glasma_batch* b, double* field_ms, int64_t* launches, double* span_ms);
+/* Bound of the GLASMA_BATCH_PERSISTENT mode's grid-barrier wait, in polls of about 100 ns
+ * (0: the default 2^24, about 2 s; at most 2^40).  A CTA whose wait runs out raises the
+ * kernel's error word and returns; every other CTA returns at its next barrier (each wait
+ * is bounded the same way), so the launch always ends.  The next glasma_batch_broadening
+ * of the batch then reports GLASMA_ERR_TIMEOUT once (the word is cleared when read), and
+ * the next run starts from the initial state as usual.  Failure detection: a limit far
+ * below a step's duration makes the wait run out on purpose.  Host only, no device work;
+ * GLASMA_ERR_INVALID on a null batch or a limit out of range. */
+glasma_status glasma_batch_set_wait_limit(glasma_batch* b, int64_t polls);
 /* Particles of event i (original order; double[n] each, Q double[n][8]; NULL skips). */
 glasma_status glasma_batch_get_particles(glasma_batch* b, int32_t event, double* x, double* y, double* eta,
                                          double* px, double* py, double* peta, double* Q);

@@ -99,6 +99,7 @@ SIGNATURES = {
     "cpic_push_many": (C.c_int, [_p, _i32, _i32]),
     "glasma_batch_set_graph_timing": (C.c_int, [_p, _i32]),
     "glasma_batch_set_push_stream": (C.c_int, [_p, _i32]),
+    "glasma_batch_set_wait_limit": (C.c_int, [_p, _i64]),
     "glasma_batch_graph_times": (C.c_int, [_p, C.POINTER(_d), C.POINTER(_i64), C.POINTER(_d)]),
     "glasma_state_bytes": (_i64, [_p]),
     "glasma_export_state": (C.c_int, [_p, _p, _i64]),

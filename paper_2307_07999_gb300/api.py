@@ -380,6 +380,11 @@ class Batch:
     def set_push_stream(self, separate=True):
         check(lib().glasma_batch_set_push_stream(self.handle, 1 if separate else 0))
 
+    def set_wait_limit(self, polls=0):
+        """glasma_batch_set_wait_limit: the persistent mode's grid-barrier wait in polls of
+        ~100 ns (0: the default, ~2 s)."""
+        check(lib().glasma_batch_set_wait_limit(self.handle, int(polls)))
+
     def set_graph_timing(self, on=True):
         check(lib().glasma_batch_set_graph_timing(self.handle, 1 if on else 0))
 

@@ -66,7 +66,7 @@ struct glasma_batch {
     // persistent mode
     void* pers_ctrl = nullptr;    // barrier counters + error word + per-iteration prefixes (device)
     int pers_blocks = 0;
-    int pers_timeout = 0;
+    unsigned long long pers_spin = 1ull << 24;  // grid-barrier polls (~100 ns each) before giving up
     bool pers_launched = false;   // the error word is meaningful only after a persistent run
 };
 

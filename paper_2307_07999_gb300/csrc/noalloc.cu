@@ -8,8 +8,6 @@
 // serves them: it reads a field buffer the caller already owns and keeps its
 // reduction scratch (per-block partial sums) in the file-scope array below,
 // which every GPU that loads this library holds until the process exits.
-#include <mutex>
-
 #include "../../include/glasma.h"
 #include "field.cuh"
 
@@ -111,20 +109,14 @@ __global__ void k_monitor_final(double* __restrict__ part, int nb) {
 
 using namespace glasma;
 
-// device address of g_monitor_scratch, resolved once per device with that device current
-static std::mutex g_scratch_mu;
-static double* g_scratch_ptr[256] = {nullptr};
-
+// Device address of g_monitor_scratch on the current device.  Looked up at every call
+// (cudaGetSymbolAddress allocates nothing): an address cached across calls would go stale
+// when the device's context is torn down and created again (cudaDeviceReset), and the
+// kernel would then write to memory that is no longer the array.
 static glasma_status scratch_for_current_device(double** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return GLASMA_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_monitor_scratch) != cudaSuccess || !p) return GLASMA_ERR_CUDA;
-        g_scratch_ptr[dev] = (double*)p;
-    }
-    *out = g_scratch_ptr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_monitor_scratch) != cudaSuccess || !p) return GLASMA_ERR_CUDA;
+    *out = (double*)p;
     return GLASMA_OK;
 }
 
@@ -140,6 +132,37 @@ extern "C" glasma_status glasma_diagnostics_noalloc(const void* fields, int32_t 
         glasma_set_error("glasma_diagnostics_noalloc: field buffer not 16-byte aligned");
         return GLASMA_ERR_INVALID;
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    {  // synchronous (a device-to-host copy, then a wait): it cannot be part of a capture
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            glasma_set_error("glasma_diagnostics_noalloc: bad stream");
+            return GLASMA_ERR_INVALID;
+        }
+        if (cs != cudaStreamCaptureStatusNone) {
+            glasma_set_error("glasma_diagnostics_noalloc: the call synchronises and cannot be captured");
+            return GLASMA_ERR_INVALID;
+        }
+    }
+    if (expanding && !(tau > 0)) {  // E and D phi are divided by tau
+        glasma_set_error("glasma_diagnostics_noalloc: the expanding evolution needs tau > 0");
+        return GLASMA_ERR_INVALID;
+    }
+    {  // the buffer must be memory of the current device (a host pointer or another GPU's
+       // buffer would pass the checks above and make the kernel fault)
+        int dev = -1;
+        cudaPointerAttributes pa;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&pa, fields) != cudaSuccess) {
+            cudaGetLastError();
+            glasma_set_error("glasma_diagnostics_noalloc: cannot query the field buffer");
+            return GLASMA_ERR_INVALID;
+        }
+        if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev) {
+            glasma_set_error("glasma_diagnostics_noalloc: fields is not device memory of the current device");
+            return GLASMA_ERR_INVALID;
+        }
+    }
     const size_t ns = (size_t)n * n;
     const size_t nb = (ns + NOALLOC_BLOCK - 1) / NOALLOC_BLOCK;
     if (nb > (size_t)NOALLOC_MAX_BLOCKS) {
@@ -151,7 +174,6 @@ extern "C" glasma_status glasma_diagnostics_noalloc(const void* fields, int32_t 
         glasma_set_error("glasma_diagnostics_noalloc: cudaGetSymbolAddress failed");
         return GLASMA_ERR_CUDA;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     const double te = expanding ? tau : 1.0;
     if (precision == GLASMA_FP32)
         k_monitor_partials<float><<<(unsigned)nb, NOALLOC_BLOCK, 0, st>>>((const float*)fields, n, te, part);
@@ -175,5 +197,9 @@ extern "C" glasma_status glasma_diagnostics_noalloc(const void* fields, int32_t 
     out[5] = m[6];
     out[6] = tau;
     out[7] = m[7];
-    return m[7] > 0 ? GLASMA_ERR_NONFINITE : GLASMA_OK;
+    if (m[7] > 0) {
+        glasma_set_error("glasma_diagnostics_noalloc: nonfinite field values");
+        return GLASMA_ERR_NONFINITE;
+    }
+    return GLASMA_OK;
 }

@@ -154,7 +154,7 @@ template <class T> static glasma_status run_impl(glasma_batch* b) {
     a.pitems_upto = ints + (K + 1) + K + (E + 1);
     a.E = E;
     a.K = b->max_iter;
-    a.spin_limit = 1ull << 24;  // ~2 s of polling at ~100 ns per poll
+    a.spin_limit = b->pers_spin;  // default 2^24 polls: ~2 s at ~100 ns per poll
     if (cudaMemsetAsync(base, 0, 256 + (size_t)(K + 1) * 4, b->st) != cudaSuccess) return GLASMA_ERR_CUDA;
     void* args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_persistent<T>, dim3(b->pers_blocks), dim3(TX, TY), args,
@@ -199,3 +199,12 @@ bool batch_timed_out(glasma_batch* b) {
 }
 
 void batch_free_persistent(glasma_batch* b) { (void)b; }
+
+extern "C" glasma_status glasma_batch_set_wait_limit(glasma_batch* b, int64_t polls) {
+    if (!b || polls < 0 || polls > (int64_t(1) << 40)) {
+        glasma_set_error("glasma_batch_set_wait_limit: bad arguments");
+        return GLASMA_ERR_INVALID;
+    }
+    b->pers_spin = polls == 0 ? (1ull << 24) : (unsigned long long)polls;
+    return GLASMA_OK;
+}

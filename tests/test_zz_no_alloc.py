@@ -34,23 +34,39 @@ def plane_buffer(st, prec):
     return torch.tensor(g.astype(np.float32 if prec else np.float64), device="cuda").contiguous()
 
 
-def call(buf, n, prec, tau):
+def call(buf_ptr, n, prec, tau, expanding=1):
     out = np.zeros(8)
-    rc = G.lib().glasma_diagnostics_noalloc(C.c_void_p(buf.data_ptr()), n, prec, 1, tau, None,
+    rc = G.lib().glasma_diagnostics_noalloc(C.c_void_p(buf_ptr), n, prec, expanding, tau, None,
                                             out.ctypes.data_as(C.c_void_p))
     return rc, out
 
 
-@pytest.mark.parametrize("prec,n,tol", [(0, 24, 1e-12), (1, 40, 2e-5), (0, 67, 1e-12)])
-def test_noalloc_diagnostics_match_context_diagnostics(prec, n, tol):
-    st = random_state(n, seed=500 + n, step=5)
-    g = G.Glasma(n, 6.0, precision=prec, tau_end_fm=100.0)
+def tiled_state(small, n):
+    """A periodic n x n state repeating a small periodic state (n a multiple of its size)."""
+    m = small.n
+    X, Y = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    idx = ((X % m) + m * (Y % m)).reshape(-1)
+    st = type(small)(n, step=small.step)
+    st.U[...] = small.U[idx]
+    st.E[...] = small.E[idx]
+    st.phi[...] = small.phi[idx]
+    st.pi[...] = small.pi[idx]
+    return st
+
+
+@pytest.mark.parametrize("prec,n,tol,expanding", [(0, 24, 1e-12, 1), (1, 40, 2e-5, 1), (0, 67, 1e-12, 1),
+                                                  (0, 30, 1e-12, 0), (1, 33, 2e-5, 0), (1, 1024, 2e-5, 1)])
+def test_noalloc_diagnostics_match_context_diagnostics(prec, n, tol, expanding):
+    # n = 1024: the largest lattice the static scratch takes (4096 blocks, the last partials
+    # right before the slot of the final sums)
+    st = random_state(n, seed=500 + n, step=5) if n <= 67 else tiled_state(random_state(32, seed=532, step=5), n)
+    g = G.Glasma(n, 6.0, precision=prec, tau_end_fm=100.0, expanding=expanding)
     g.set_state(st.U, st.E, st.phi, st.pi, st.step)
     want = g.diagnostics()
     buf = plane_buffer(st, prec)
     torch.cuda.synchronize()
     for _ in range(2):  # the static scratch keeps the previous call's contents
-        rc, got = call(buf, n, prec, st.step * 0.125)
+        rc, got = call(buf.data_ptr(), n, prec, st.step * 0.125, expanding)
         assert rc == 0
         assert abs(got[0] - want[0]) <= tol * max(want[0], 1e-300) + 1e-15
         assert rel_err(got[1:5], want[1:5]) < tol
@@ -60,7 +76,7 @@ def test_noalloc_diagnostics_match_context_diagnostics(prec, n, tol):
 
 def test_noalloc_rejects_lattices_beyond_the_scratch():
     buf = torch.zeros(16, dtype=torch.float32, device="cuda")
-    rc, _ = call(buf, 1025, 1, 1.0)
+    rc, _ = call(buf.data_ptr(), 1025, 1, 1.0)
     assert rc == -1
     assert b"static scratch" in G.lib().glasma_last_error()
 
@@ -71,3 +87,28 @@ def test_noalloc_rejects_unaligned_buffers():
                                             np.zeros(8).ctypes.data_as(C.c_void_p))
     assert rc == -1
     assert b"aligned" in G.lib().glasma_last_error()
+
+
+def test_noalloc_rejects_host_memory_and_bad_tau():
+    host = np.zeros(56 * 64, dtype=np.float32)
+    rc, _ = call(host.ctypes.data, 8, 1, 1.0)
+    assert rc == -1
+    assert b"device memory" in G.lib().glasma_last_error()
+    buf = torch.zeros(56 * 64, dtype=torch.float32, device="cuda")
+    rc, _ = call(buf.data_ptr(), 8, 1, 0.0, expanding=1)
+    assert rc == -1
+    assert b"tau > 0" in G.lib().glasma_last_error()
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    buf = torch.zeros(56 * 64, dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    out = np.zeros(8)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    rc = None
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        rc = G.lib().glasma_diagnostics_noalloc(C.c_void_p(buf.data_ptr()), 8, 1, 1, 1.0, C.c_void_p(s.cuda_stream),
+                                                out.ctypes.data_as(C.c_void_p))
+    assert rc == -1
+    assert b"captured" in G.lib().glasma_last_error()
