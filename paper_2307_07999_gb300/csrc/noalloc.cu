@@ -132,6 +132,16 @@ extern "C" glasma_status glasma_diagnostics_noalloc(const void* fields, int32_t 
         glasma_set_error("glasma_diagnostics_noalloc: field buffer not 16-byte aligned");
         return GLASMA_ERR_INVALID;
     }
+    const size_t ns = (size_t)n * n;
+    const size_t nb = (ns + NOALLOC_BLOCK - 1) / NOALLOC_BLOCK;
+    if (nb > (size_t)NOALLOC_MAX_BLOCKS) {
+        glasma_set_error("glasma_diagnostics_noalloc: lattice larger than the static scratch (n*n <= 1048576)");
+        return GLASMA_ERR_INVALID;
+    }
+    if (expanding && !(tau > 0)) {  // E and D phi are divided by tau
+        glasma_set_error("glasma_diagnostics_noalloc: the expanding evolution needs tau > 0");
+        return GLASMA_ERR_INVALID;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     {  // synchronous (a device-to-host copy, then a wait): it cannot be part of a capture
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -144,10 +154,6 @@ extern "C" glasma_status glasma_diagnostics_noalloc(const void* fields, int32_t 
             glasma_set_error("glasma_diagnostics_noalloc: the call synchronises and cannot be captured");
             return GLASMA_ERR_INVALID;
         }
-    }
-    if (expanding && !(tau > 0)) {  // E and D phi are divided by tau
-        glasma_set_error("glasma_diagnostics_noalloc: the expanding evolution needs tau > 0");
-        return GLASMA_ERR_INVALID;
     }
     {  // the buffer must be memory of the current device (a host pointer or another GPU's
        // buffer would pass the checks above and make the kernel fault)
@@ -162,12 +168,6 @@ extern "C" glasma_status glasma_diagnostics_noalloc(const void* fields, int32_t 
             glasma_set_error("glasma_diagnostics_noalloc: fields is not device memory of the current device");
             return GLASMA_ERR_INVALID;
         }
-    }
-    const size_t ns = (size_t)n * n;
-    const size_t nb = (ns + NOALLOC_BLOCK - 1) / NOALLOC_BLOCK;
-    if (nb > (size_t)NOALLOC_MAX_BLOCKS) {
-        glasma_set_error("glasma_diagnostics_noalloc: lattice larger than the static scratch (n*n <= 1048576)");
-        return GLASMA_ERR_INVALID;
     }
     double* part = nullptr;
     if (scratch_for_current_device(&part) != GLASMA_OK) {
