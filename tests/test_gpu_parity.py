@@ -156,6 +156,26 @@ def test_push_sorting_is_invisible():
     assert rel_err(c2.broadening()[:, 1:4], c1.broadening()[:, 1:4]) < 1e-13
 
 
+@pytest.mark.parametrize("prec,bin_every,tol", [(0, 3, 1e-10), (0, 1, 1e-10), (1, 2, 1e-4)])
+def test_push_sorted_matches_oracle(prec, bin_every, tol):
+    """Particles sorted by cell every k steps (a counting sort that reorders the particle
+    planes; results are reported in the original order) against the oracle, which keeps
+    its particles unsorted."""
+    n, np_ = 16, 600
+    g, c, st, P, accs, a_gev = run_pair(n, np_, 14, prec, 43, bin_every=bin_every)
+    got = c.get_particles()
+    dx = np.abs(got["x"] - P.x)
+    dy = np.abs(got["y"] - P.y)
+    assert np.minimum(dx, n - dx).max() < tol * n and np.minimum(dy, n - dy).max() < tol * n
+    for k in ("px", "py", "peta", "eta"):
+        assert rel_err(got[k], getattr(P, k)) < tol, k
+    assert rel_err(got["Q"], P.Q) < tol
+    tab = c.broadening()
+    want = accs[:, :3] / accs[:, 3:4] / a_gev ** 2
+    assert rel_err(tab[1:, 1:4], want) < tol
+    assert np.all(tab[1:, 4] == np_)
+
+
 def test_push_massless_and_empty():
     n = 10
     g, c, st, P, accs, a_gev = run_pair(n, 64, 6, 0, 51, mass=0.0)
