@@ -417,6 +417,19 @@ def run_ours(args, ws, rank, local):
     # 132 per particle-step (the gather's field reads counted as fused, 0 B)
     whole = (BYTES_PER_SITE * su + BYTES_PER_PARTICLE * ps) / (ms / 1000.0) / 1e9
     roofline["whole_step"] = {"achieved": whole, "frac": whole / peak, "unit": "GB/s"}
+    # the push's own roofline: its time per run is the step minus the field launches;
+    # algorithmic bytes 132 per particle-step (particle state read + written), the field
+    # reads of its gather listed beside them (35 groups of 32 B around the cell, or the
+    # 18-group record of the record push, which the field launch also writes)
+    if pmode != "fused" and other_ms > 0:
+        pa = BYTES_PER_PARTICLE * ps / (other_ms / 1000.0) / 1e9
+        rec_push = B.push_variant == 2
+        roofline["push"] = {"achieved": pa, "frac": pa / peak, "unit": "GB/s", "ms_per_run": other_ms,
+                            "particle_steps_per_s": ps / (other_ms / 1000.0),
+                            "algorithmic_bytes_per_particle_step": BYTES_PER_PARTICLE,
+                            "gather_bytes_per_particle_step": 18 * 32 if rec_push else 35 * 32,
+                            "gather": ("one 576 B record per particle (written by the field launch for occupied cells)"
+                                       if rec_push else "35 field groups of 32 B around the particle's cell")}
 
     # plain one-event-per-launch GPU path on the same GPU
     plain = None
@@ -442,7 +455,9 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": WORKLOAD, "mode": mode,
                        "field_tile": f"{tile[0]}x{tile[1]}, {tile[2]} CTAs/SM " + ("(fixed)" if args.field_variant >= 0 else "(autotuned)"),
                        "push_kernel": {0: "fields through L1 (128-thread blocks, 3 per SM)",
-                                       1: "fields staged in shared memory (32-thread blocks)"}.get(B.push_variant, "?")
+                                       1: "fields staged in shared memory (32-thread blocks)",
+                                       2: "gather records written by the field launch (128-thread blocks, 4 per SM)"}
+                       .get(B.push_variant, "?")
                                       + (" (fixed)" if args.field_variant >= 0 else " (autotuned)"),
                        "tile_tuning_ms_per_8_steps": ({f"{a}x{b}/{c}": round(t, 3) for (a, b, c), t in zip(shapes, tile_ms)}
                                                       if args.field_variant < 0 else None),

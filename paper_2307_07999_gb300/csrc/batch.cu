@@ -61,6 +61,8 @@ static Layout layout(const glasma_params* ev, const cpic_params* pp, int E, size
     size_t npmax = 0;
     for (int e = 0; e < E; e++) {
         L.fields += 4 * fbytes(ev[e]);
+        const size_t ns = (size_t)ev[e].n * ev[e].n;
+        L.fields += align256(ns * record_bytes(ev[e].precision)) + align256(ns * 4);
         L.parts += 2 * part_bytes(pp[e].n_particles, ev[e].precision);
         L.accs += align256(((size_t)steps_of(ev[e]) + 2) * 4 * 8);
         nmax = std::max(nmax, ev[e].n);
@@ -170,6 +172,8 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
         x.buf[1] = A.take(fbytes(ev[e]));
         x.buf[2] = A.take(fbytes(ev[e]));
         x.init_buf = A.take(fbytes(ev[e]));
+        x.rec = A.take(x.ns * record_bytes(b->prec));
+        x.occ = (int*)A.take(x.ns * 4);
         const size_t pb = part_bytes(x.np, b->prec);
         x.part_bytes = pb;
         x.part_base = A.take(pb);
@@ -178,7 +182,7 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
         x.acc_rows = x.n_steps + 2;
         x.acc = (double*)A.take((size_t)x.acc_rows * 4 * 8);
         x.mon = (double*)A.take(256);
-        if (!x.buf[0] || !x.buf[1] || !x.buf[2] || !x.init_buf || !x.part_base || !x.part_init || !x.acc || !x.mon) {
+        if (!x.buf[0] || !x.buf[1] || !x.buf[2] || !x.init_buf || !x.rec || !x.occ || !x.part_base || !x.part_init || !x.acc || !x.mon) {
             delete b;
             return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
         }
@@ -289,13 +293,21 @@ static glasma_status build_tables(glasma_batch* b) {
             const void* src = x.buf[k % 3];
             void* dst = x.buf[(k + 1) % 3];
             const int reunit = reunit_code(x.gp.reunit_every, s);
-            const StepHost st = step_coeffs(src, dst, x.n, s, x.dtau, 1, reunit);
+            StepHost st = step_coeffs(src, dst, x.n, s, x.dtau, 1, reunit);
+            // gather records (used by the REC field kernels of the record push): at the
+            // particles' first step every cell gets one, later the cells stamped by the push
+            st.rec = x.rec;
+            st.occ = x.occ;
+            st.all_rec = s == x.n_form ? 1 : 0;
             pack_step_args(b->prec, st, hs.data() + ((size_t)k * E + i) * sa);
             PushHost ph;
             ph.fo = src; ph.fn = dst; ph.n = x.n; ph.np = x.np;
             push_coeffs(ph, s, x.dtau, 1, x.pp.integrator, x.pp.substeps, x.pp.interp);
             ph.mass = x.mass;
             ph.acc = (on && s >= x.n_form) ? x.acc + 4 * (size_t)(s + 1) : nullptr;
+            ph.rec = x.rec;
+            ph.occ = x.occ;
+            ph.epoch_next = s + 1;
             pack_push_args(b->prec, ph, x.P, hp.data() + ((size_t)k * E + i) * pa);
         }
         b->active[k] = act;
@@ -372,6 +384,10 @@ static cudaError_t enqueue_restore(glasma_batch* b) {
     return cudaSuccess;
 }
 
+// the graph and eager modes run the record push (and the field kernels that write its
+// records) when it is the chosen push kernel and no event needs the sub-stepped push
+static bool batch_records(const glasma_batch* b) { return !b->any_sub && b->pvar == PUSH_VARIANT_RECORD; }
+
 static cudaError_t enqueue_fused(glasma_batch* b) {
     cudaError_t e = enqueue_restore(b);
     if (e != cudaSuccess) return e;
@@ -394,7 +410,10 @@ static cudaError_t enqueue_batched(glasma_batch* b) {
     cudaError_t e = enqueue_restore(b);
     if (e != cudaSuccess) return e;
     const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
-    const bool two = b->two_streams && b->st2 != nullptr;
+    // record push: field launch k writes the records push k reads, and push k stamps the
+    // cells field launch k+1 writes records for, so both stay on one stream
+    const bool rec = batch_records(b);
+    const bool two = !rec && b->two_streams && b->st2 != nullptr;
     cudaStream_t sp = two ? b->st2 : b->st;  // the stream of the pushes
     const int K = b->max_iter;
     if (two) {  // the pushes see the restore
@@ -417,7 +436,7 @@ static cudaError_t enqueue_batched(glasma_batch* b) {
             if (e != cudaSuccess) return e;
         }
         e = launch_field_step_variant(b->prec, b->fvar, (char*)b->step_args + (size_t)k * b->E * sa, b->gtiles_dev,
-                                      b->gtiles_upto[act], b->st);
+                                      b->gtiles_upto[act], b->st, rec);
         if (e != cudaSuccess) return e;
         if (b->timing) {
             e = cudaEventRecordWithFlags(b->tev[2 * k + 1], b->st, cudaEventRecordExternal);
@@ -627,7 +646,8 @@ extern "C" glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, dou
             BCK(launch_fused_batched(b->prec, sargs, pargs, b->tiles_dev, b->tiles_upto[act], b->bin_start,
                                      b->bin_count, b->bin_perm, b->st));
         else
-            BCK(launch_field_step_variant(b->prec, b->fvar, sargs, b->gtiles_dev, b->gtiles_upto[act], b->st));
+            BCK(launch_field_step_variant(b->prec, b->fvar, sargs, b->gtiles_dev, b->gtiles_upto[act], b->st,
+                                          batch_records(b)));
         BCK(cudaEventRecord(ev[4 * k + 1], b->st));
         BCK(cudaEventRecord(ev[4 * k + 2], b->st));
         if (fused)
@@ -786,13 +806,16 @@ extern "C" glasma_status glasma_batch_tune(glasma_batch* b, int32_t steps, int32
     std::vector<cudaEvent_t> ev(2 * (size_t)std::max(1, k1 - k0));
     for (auto& x : ev) BCK(cudaEventCreate(&x));
     for (int v = 0; v < push_variants(); v++) {
+        // each push kernel is timed with the field launches of its iterations: the record
+        // push needs field launches that also write its records, and that cost is its own
+        const bool rec = !b->any_sub && v == PUSH_VARIANT_RECORD;
         BCK(enqueue_restore(b));
         for (int k = 0; k < k1; k++) {
             const int act = b->active[k];
             if (act == 0) break;
-            BCK(launch_field_step_variant(b->prec, b->fvar, (char*)b->step_args + (size_t)k * b->E * sa,
-                                          b->gtiles_dev, b->gtiles_upto[act], b->st));
             if (k >= k0) BCK(cudaEventRecord(ev[2 * (k - k0)], b->st));
+            BCK(launch_field_step_variant(b->prec, b->fvar, (char*)b->step_args + (size_t)k * b->E * sa,
+                                          b->gtiles_dev, b->gtiles_upto[act], b->st, rec));
             BCK(launch_push_batched(b->prec, b->any_sub ? PUSH_VARIANT_SUB : v, (char*)b->push_args + (size_t)k * b->E * pa, b->pitems_dev,
                                     b->pitems_upto[act], b->st));
             if (k >= k0) BCK(cudaEventRecord(ev[2 * (k - k0) + 1], b->st));

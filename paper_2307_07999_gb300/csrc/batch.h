@@ -17,6 +17,8 @@ struct BatchEvent {
     double a_fm, a_gev, dtau, mass;
     void* buf[3];        // rotating: iteration k reads buf[k % 3], writes buf[(k + 1) % 3]
     void* init_buf;
+    void* rec;           // gather records of the record push, REC_STRIDE groups per cell
+    int* occ;            // occupancy stamps of the record push, one per cell
     void* part_base;
     void* part_init;
     size_t part_bytes;

@@ -30,6 +30,33 @@ template <class T> struct StepArgs {
     T ue;          // link drift:  dtau / tau_{n+1/2} (or dtau)
     T pe;          // phi drift:   dtau * tau_{n+1/2} (or dtau)
     int reunit;    // re-projection of the new links: 1 FP64 Gram-Schmidt, 2 FP32 renormalisation, 0 none
+    // gather records (kernels compiled with REC only): for every cell whose occupancy
+    // stamp equals `epoch` (every cell if all_rec), the pieces of the site-centred fields
+    // that the push of this step gathers there (layout below)
+    T* rec;
+    const int* occ;
+    int epoch, all_rec;
+};
+
+// Gather record of a cell c for the push of step n (8-real groups, record stride
+// REC_STRIDE groups so that a record is whole 128-byte lines in FP32).  Written by the
+// field step of step n, which computes each piece anyway:
+//   R_EX, R_EY, R_PI  time-centred E_x(c), E_y(c), pi(c): (X_{n-1/2} + X_{n+1/2}) / 2
+//   R_PHI             phi_n(c)
+//   R_PSX, R_CHX      U_x(c) phi(c+x) U_x(c)^dag and U_x(c-x)^dag phi(c-x) U_x(c-x)
+//   R_PSY, R_CHY      the same along y
+//   R_F0              ImTL of the plaquette based at c
+//   R_T1, R_T2        ImTL of the plaquettes at c-y and c-x carried to c by U_y(c-y), U_x(c-x)
+//                     (the clover leaves (-y,+x) and (+y,-x) of c)
+// and by the owners of the neighbours c-x and c-y:
+//   R_EXL             time-centred E_x(c-x)      R_T1L   R_T1 of c-x
+//   R_UXL (2 groups)  U_x(c-x) rows 0, 1          R_EYB   time-centred E_y(c-y)
+//   R_UYB (2 groups)  U_y(c-y) rows 0, 1
+// so that Q.E_x(c) = (Q.E_x(c) + Q'.E_x(c-x)) / 2 with Q' = U_x(c-x) Q U_x(c-x)^dag, and the
+// fourth clover leaf (-x,-y) of c contracts as Q'.R_T1L.
+enum {
+    R_EX = 0, R_EY, R_PI, R_PHI, R_PSX, R_CHX, R_PSY, R_CHY, R_F0, R_T1, R_T2,
+    R_EXL, R_T1L, R_EYB, R_UXL, R_UYB = R_UXL + 2, REC_GROUPS = R_UYB + 2, REC_STRIDE = 20
 };
 
 struct TileItem { int ev, x0, y0; };
@@ -242,8 +269,31 @@ template <class T> DEV void rec_put_alg(T* s, int h, const Al<T>& x) {
     for (int k = 0; k < 8; k += NV) sts_v(s + h * REC_A + k, x.a + k);
 }
 
+template <class T> DEV T* rec_at(T* rec, size_t cell, int slot) {
+    return rec + (cell * REC_STRIDE + (size_t)slot) * 8;
+}
+template <class T> DEV void rec_store(T* rec, size_t cell, int slot, const Al<T>& x) {
+    V8<T> q;
+#pragma unroll
+    for (int a = 0; a < 8; a++) q.v[a] = x.a[a];
+    st8(rec_at(rec, cell, slot), q);
+}
+// rows 0, 1 of a link into two groups (entries 0..3, then 4, 5)
+template <class T> DEV void rec_store_link(T* rec, size_t cell, int slot, const M3<T>& U) {
+    V8<T> a;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        a.v[2 * e] = U.m[e / 3][e % 3].r;
+        a.v[2 * e + 1] = U.m[e / 3][e % 3].i;
+    }
+    st8(rec_at(rec, cell, slot), a);
+    st4(rec_at(rec, cell, slot + 1), U.m[1][1].r, U.m[1][1].i, U.m[1][2].r, U.m[1][2].i);
+}
+
 // One tile [x0, x0+TX) x [y0, y0+TY) of one step: kick at tau_n, drift with tau_{n+1/2}.
-template <class T, int TX, int TY, bool CG = false>
+// REC: also the gather records of the occupied cells (StepArgs::rec); the field
+// arithmetic is the same with and without them.
+template <class T, int TX, int TY, bool CG = false, bool REC = false>
 DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_raw) {
     using G = RecTile<T, TX, TY>;
     constexpr int HX = G::HX, HS = G::HS, FX = G::FX, FS = G::FS;
@@ -261,6 +311,16 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     const bool active = (x < n) && (y < n);
     const size_t s = active ? (size_t)x + (size_t)n * y : 0;
     Al<T> Ex = load_alg<T, CG>(src, ns, P_EX, s), Ey = load_alg<T, CG>(src, ns, P_EY, s), pi = load_alg<T, CG>(src, ns, P_PI, s);
+    // occupancy stamps of the own cell and of the cells +x, +y (whose records take this
+    // site's neighbour pieces), loaded with the fields
+    int o0 = 0, ox = 0, oy = 0;
+    if constexpr (REC) {
+        if (active && !A.all_rec) {
+            o0 = __ldg(A.occ + s);
+            ox = __ldg(A.occ + (x == n - 1 ? s - (size_t)(n - 1) : s + 1));
+            oy = __ldg(A.occ + (y == n - 1 ? s - (size_t)n * (n - 1) : s + (size_t)n));
+        }
+    }
 
     // phase 1: links (completed to 3 rows) and phi of the tile plus a one-site halo.
     // Every load of the thread is issued before the first store, so the CTA waits for
@@ -312,17 +372,29 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     const int f = (threadIdx.y + 1) * FX + threadIdx.x + 1;
     const Al<T> phi = rec_alg(sP, h);
     const T dt = A.dtau, tb = A.tb, tp = A.tp;
+    // which records this thread writes: bit 0 its own cell's, bit 1 the pieces of cell +x,
+    // bit 2 those of cell +y (REC only)
+    unsigned rm = 0;
+    if constexpr (REC) {
+        rm = A.all_rec ? 7u : ((o0 == A.epoch ? 1u : 0u) | (ox == A.epoch ? 2u : 0u) | (oy == A.epoch ? 4u : 0u));
+        if (rm & 1u) rec_store(A.rec, s, R_PHI, phi);
+    }
+    // neighbour cells +x, +y (periodic)
+    const auto cell_xp = [&]() { return x == n - 1 ? s - (size_t)(n - 1) : s + 1; };
+    const auto cell_yp = [&]() { return y == n - 1 ? s - (size_t)n * (n - 1) : s + (size_t)n; };
     // Each link is read from shared memory where it is used and its terms are folded
     // into the increments at once, which keeps few values live per thread.
     Al<T> dEx, dEy, dpi;
     {  // forward x link: U phi(x+x) U^dag, and its commutator with phi (E_x)
         const Al<T> psx = conj_alg(rec_link(sUx, h), rec_alg(sP, h + 1));
+        if (REC && (rm & 1u)) rec_store(A.rec, s, R_PSX, psx);
         const Al<T> cm = icomm(phi, psx);
 #pragma unroll
         for (int a = 0; a < 8; a++) { dpi.a[a] = psx.a[a]; dEx.a[a] = -tp * cm.a[a]; }
     }
     {  // forward y link (E_y)
         const Al<T> psy = conj_alg(rec_link(sUy, h), rec_alg(sP, h + HX));
+        if (REC && (rm & 1u)) rec_store(A.rec, s, R_PSY, psy);
         const Al<T> cm = icomm(phi, psy);
 #pragma unroll
         for (int a = 0; a < 8; a++) { dpi.a[a] += psy.a[a]; dEy.a[a] = -tp * cm.a[a]; }
@@ -331,6 +403,10 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         const M3<T> uxm = rec_link(sUx, h - 1);
         const Al<T> chx = transport_alg(uxm, rec_alg(sP, h - 1));
         const Al<T> t2 = transport_alg(uxm, rec_alg(sF, f - 1));
+        if (REC && (rm & 1u)) {
+            rec_store(A.rec, s, R_CHX, chx);
+            rec_store(A.rec, s, R_T2, t2);
+        }
 #pragma unroll
         for (int a = 0; a < 8; a++) { dpi.a[a] += chx.a[a]; dEy.a[a] -= tb * t2.a[a]; }
     }
@@ -338,16 +414,51 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         const M3<T> uym = rec_link(sUy, h - HX);
         const Al<T> chy = transport_alg(uym, rec_alg(sP, h - HX));
         const Al<T> t1 = transport_alg(uym, rec_alg(sF, f - FX));
+        if (REC && (rm & 1u)) {
+            rec_store(A.rec, s, R_CHY, chy);
+            rec_store(A.rec, s, R_T1, t1);
+        }
+        if (REC && (rm & 2u)) rec_store(A.rec, cell_xp(), R_T1L, t1);
 #pragma unroll
         for (int a = 0; a < 8; a++) { dpi.a[a] += chy.a[a]; dEx.a[a] += tb * t1.a[a]; }
     }
     {
         const Al<T> F0 = rec_alg(sF, f);
+        if constexpr (REC) {
+            // the same updates, one field at a time, each followed by its time average
+            // (E_{n-1/2} + E_{n+1/2}) / 2 formed exactly as the unfused gather forms it
+            if (rm & 1u) rec_store(A.rec, s, R_F0, F0);
+            Al<T> av;
 #pragma unroll
-        for (int a = 0; a < 8; a++) {
-            Ex.a[a] += dt * (dEx.a[a] - tb * F0.a[a]);
-            Ey.a[a] += dt * (dEy.a[a] + tb * F0.a[a]);
-            pi.a[a] += dt * tp * (dpi.a[a] - T(4) * phi.a[a]);
+            for (int a = 0; a < 8; a++) {
+                const T o = Ex.a[a];
+                Ex.a[a] += dt * (dEx.a[a] - tb * F0.a[a]);
+                av.a[a] = T(0.5) * (o + Ex.a[a]);
+            }
+            if (rm & 1u) rec_store(A.rec, s, R_EX, av);
+            if (rm & 2u) rec_store(A.rec, cell_xp(), R_EXL, av);
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const T o = Ey.a[a];
+                Ey.a[a] += dt * (dEy.a[a] + tb * F0.a[a]);
+                av.a[a] = T(0.5) * (o + Ey.a[a]);
+            }
+            if (rm & 1u) rec_store(A.rec, s, R_EY, av);
+            if (rm & 4u) rec_store(A.rec, cell_yp(), R_EYB, av);
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const T o = pi.a[a];
+                pi.a[a] += dt * tp * (dpi.a[a] - T(4) * phi.a[a]);
+                av.a[a] = T(0.5) * (o + pi.a[a]);
+            }
+            if (rm & 1u) rec_store(A.rec, s, R_PI, av);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                Ex.a[a] += dt * (dEx.a[a] - tb * F0.a[a]);
+                Ey.a[a] += dt * (dEy.a[a] + tb * F0.a[a]);
+                pi.a[a] += dt * tp * (dpi.a[a] - T(4) * phi.a[a]);
+            }
         }
     }
     T* __restrict__ dst = A.dst;
@@ -367,6 +478,10 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         for (int a = 0; a < 8; a++) e.a[a] *= A.ue;
         const M3<T> W = expi(herm(e));
         const M3<T> U = rec_link(d == 0 ? sUx : sUy, h);
+        if constexpr (REC) {  // U_n of this site for the record of cell +x (U_x) or +y (U_y)
+            if (d == 0 && (rm & 2u)) rec_store_link(A.rec, cell_xp(), R_UXL, U);
+            if (d == 1 && (rm & 4u)) rec_store_link(A.rec, cell_yp(), R_UYB, U);
+        }
         M3<T> V;
 #pragma unroll
         for (int r = 0; r < 2; r++)

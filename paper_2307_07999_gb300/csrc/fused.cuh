@@ -22,6 +22,7 @@ template <class T, int TX, int TY> struct FusedTile {
 
 // shared-memory field source for the push of the particles of one tile
 template <class T, int TX, int TY> struct SmemSrc {
+    static constexpr bool kRecord = false;
     using FT = FusedTile<T, TX, TY>;
     const T *sU, *sP, *sEx, *sEy, *sPi;
     int x0, y0, n;
@@ -219,7 +220,7 @@ DEV void fused_tile(const StepArgs<T>& A, const PushArgs<T>& PA, int x0, int y0,
     const SmemSrc<T, TX, TY> S{sU, sP, sEx, sEy, sPi, x0, y0, n};
     double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
     for (int k = tid; k < tcount; k += TX * TY) {
-        double a0, a1, a2, a3;
+        T a0, a1, a2, a3;
         push_one_src(PA, S, perm[ts + k], a0, a1, a2, a3);
         sx += a0; sy += a1; sz += a2; sc += a3;
     }

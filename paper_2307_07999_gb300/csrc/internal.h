@@ -21,6 +21,10 @@ struct StepHost {
     int n;
     double tb, tp, dtau, ue, pe;
     int reunit;
+    void* rec;        // gather records written by the REC kernels (null otherwise)
+    const int* occ;   // occupancy stamps they test
+    int epoch;        // the step index: a cell whose stamp equals it gets a record
+    int all_rec;      // 1: every cell gets a record (the particles' first step)
 };
 // leapfrog coefficients of step n (state at tau_n = n dtau)
 StepHost step_coeffs(const void* src, void* dst, int n, int step, double dtau, int expanding, int reunit);
@@ -37,7 +41,7 @@ inline int reunit_code(int reunit_every, int s) {
 cudaError_t launch_field_step(int prec, const StepHost& a, cudaStream_t st);
 // batched: args[n_ev], items[n_items] (device arrays), one CTA per item
 cudaError_t launch_field_step_batched(int prec, const void* args_dev, const void* items_dev, int n_items,
-                                      cudaStream_t st);
+                                      cudaStream_t st, bool rec = false);
 int field_tile_x(int prec);
 int field_tile_y(int prec);
 int field_variants(int prec);
@@ -45,7 +49,9 @@ void field_variant_shape(int prec, int v, int* tx, int* ty, int* minb);
 cudaError_t prepare_field_variants(int prec);
 cudaError_t prepare_push_staged();
 cudaError_t launch_field_step_variant(int prec, int v, const void* args, const void* items, int n_items,
-                                      cudaStream_t st);
+                                      cudaStream_t st, bool rec = false);
+// bytes of one cell's gather record (REC_STRIDE groups of 8 reals)
+size_t record_bytes(int prec);
 size_t step_args_size(int prec);
 void pack_step_args(int prec, const StepHost& a, void* out);
 
@@ -76,6 +82,9 @@ struct PushHost {
     int interp;          // gather: 0 nearest grid point, 1 cloud in cell
     double dec0, dec1;   // Boris: p_eta^ decay factors tau_n/tau_{n+1/2}, tau_{n+1/2}/tau_{n+1} (1: static box)
     double* acc;
+    const void* rec;     // record push: the gather records of this step
+    int* occ;            // record push: occupancy stamps, set to epoch_next at the new cells
+    int epoch_next;
 };
 // the step-dependent coefficients of the push from tau_n = step * dtau to tau_{n+1}
 inline void push_coeffs(PushHost& a, int step, double dtau, int expanding, int integrator, int substeps,
@@ -101,7 +110,9 @@ void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out);
 int push_variants();
 // the batched push of batches with sub-stepped or cloud-in-cell events (global source, any
 // cell; not tuned)
-constexpr int PUSH_VARIANT_SUB = 2;
+constexpr int PUSH_VARIANT_SUB = 99;
+// the record push (tuned variant 2): the field launches of the same run write gather records
+constexpr int PUSH_VARIANT_RECORD = 2;
 // lattice-correlator estimators (kernels_corr.cu): state = I [24][ns], J [24][ns], W [18][ns]
 size_t corr_state_bytes(int prec, int n);
 cudaError_t launch_corr_reset(int prec, void* state, int n, cudaStream_t st);

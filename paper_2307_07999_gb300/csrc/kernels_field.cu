@@ -23,18 +23,19 @@ k_field_step(StepArgs<T> A) {
     constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
     field_tile<T, TX, TY>(A, blockIdx.x * TX, blockIdx.y * TY, smem);
 }
-template <class T>
+template <class T, bool REC = false>
 __global__ void __launch_bounds__(TileCfg<T>::TX * TileCfg<T>::TY, TileCfg<T>::MINB)
 k_field_step_batched(const StepArgs<T>* __restrict__ args, const TileItem* __restrict__ items) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
     const TileItem it = items[blockIdx.x];
-    field_tile<T, TX, TY>(args[it.ev], it.x0, it.y0, smem);
+    field_tile<T, TX, TY, false, REC>(args[it.ev], it.x0, it.y0, smem);
 }
 
 StepHost step_coeffs(const void* src, void* dst, int n, int step, double dtau, int expanding, int reunit) {
     StepHost a;
     a.src = src; a.dst = dst; a.n = n; a.dtau = dtau; a.reunit = reunit;
+    a.rec = nullptr; a.occ = nullptr; a.epoch = step; a.all_rec = 0;
     const double tn = step * dtau, th = (step + 0.5) * dtau;
     a.tb = expanding ? tn : 1.0;
     a.tp = expanding ? 1.0 / tn : 1.0;
@@ -48,6 +49,7 @@ template <class T> static StepArgs<T> to_args(const StepHost& a) {
     A.src = (const T*)a.src; A.dst = (T*)a.dst; A.n = a.n;
     A.tb = (T)a.tb; A.tp = (T)a.tp; A.dtau = (T)a.dtau; A.ue = (T)a.ue; A.pe = (T)a.pe;
     A.reunit = a.reunit;
+    A.rec = (T*)a.rec; A.occ = a.occ; A.epoch = a.epoch; A.all_rec = a.all_rec;
     return A;
 }
 size_t step_args_size(int prec) { return prec ? sizeof(StepArgs<float>) : sizeof(StepArgs<double>); }
@@ -66,6 +68,8 @@ template <class T> static cudaError_t set_smem() {
         cudaError_t e = cudaFuncSetAttribute(k_field_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_field_step_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_field_step_batched<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         done = true;
     }
@@ -106,36 +110,46 @@ template <> cudaError_t step_impl<float>(const StepHost& a, cudaStream_t st) {
 cudaError_t launch_field_step(int prec, const StepHost& a, cudaStream_t st) {
     return prec ? step_impl<float>(a, st) : step_impl<double>(a, st);
 }
-template <class T> static cudaError_t batched_impl(const void* args, const void* items, int n_items, cudaStream_t st) {
+template <class T>
+static cudaError_t batched_impl(const void* args, const void* items, int n_items, bool rec, cudaStream_t st) {
     constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
     cudaError_t e = set_smem<T>();
     if (e != cudaSuccess) return e;
     if (n_items <= 0 || !args) return cudaSuccess;
-    k_field_step_batched<T><<<n_items, dim3(TX, TY), RecTile<T, TX, TY>::smem, st>>>((const StepArgs<T>*)args,
-                                                                              (const TileItem*)items);
+    const size_t sm = RecTile<T, TX, TY>::smem;
+    if (rec)
+        k_field_step_batched<T, true><<<n_items, dim3(TX, TY), sm, st>>>((const StepArgs<T>*)args,
+                                                                          (const TileItem*)items);
+    else
+        k_field_step_batched<T><<<n_items, dim3(TX, TY), sm, st>>>((const StepArgs<T>*)args, (const TileItem*)items);
     return cudaGetLastError();
 }
-cudaError_t launch_field_step_batched(int prec, const void* args, const void* items, int n_items, cudaStream_t st) {
-    return prec ? batched_impl<float>(args, items, n_items, st) : batched_impl<double>(args, items, n_items, st);
+cudaError_t launch_field_step_batched(int prec, const void* args, const void* items, int n_items, cudaStream_t st,
+                                      bool rec) {
+    return prec ? batched_impl<float>(args, items, n_items, rec, st)
+                : batched_impl<double>(args, items, n_items, rec, st);
 }
 
 // ---------------------------------------------------------------- FP32 tile variants
 // The batched FP32 field step compiled for several tile shapes; a batch picks one by
 // timing them on its own events (glasma_batch_tune).  The arithmetic per site is the
 // same in every shape, so the results are identical.
-template <int TX, int TY, int MINB>
+template <int TX, int TY, int MINB, bool REC = false>
 __global__ void __launch_bounds__(TX * TY, MINB)
 k_field_step_tiles(const StepArgs<float>* __restrict__ args, const TileItem* __restrict__ items) {
     extern __shared__ __align__(16) unsigned char smem[];
     const TileItem it = items[blockIdx.x];
-    field_tile<float, TX, TY>(args[it.ev], it.x0, it.y0, smem);
+    field_tile<float, TX, TY, false, REC>(args[it.ev], it.x0, it.y0, smem);
 }
 struct FieldVariant {
     int tx, ty, minb;
     const void* fn;
     size_t smem;
+    const void* fn_rec;  // the same shape writing the gather records
 };
-#define GL_FV(TX, TY, MB) {TX, TY, MB, (const void*)k_field_step_tiles<TX, TY, MB>, RecTile<float, TX, TY>::smem}
+#define GL_FV(TX, TY, MB)                                                                                \
+    {TX, TY, MB, (const void*)k_field_step_tiles<TX, TY, MB>, RecTile<float, TX, TY>::smem,             \
+     (const void*)k_field_step_tiles<TX, TY, MB, true>}
 static const FieldVariant g_fvar[] = {GL_FV(32, 4, 3), GL_FV(16, 8, 3), GL_FV(8, 16, 3), GL_FV(32, 6, 2),
                                       GL_FV(16, 12, 2), GL_FV(32, 8, 2), GL_FV(32, 4, 4), GL_FV(16, 8, 4),
                                       GL_FV(8, 8, 8), GL_FV(8, 16, 4), GL_FV(16, 16, 2)};
@@ -155,19 +169,21 @@ cudaError_t prepare_field_variants(int prec) {
     if (e != cudaSuccess || done) return e;
     for (int v = 0; v < N_FVAR; v++) {
         e = cudaFuncSetAttribute(g_fvar[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_fvar[v].smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(g_fvar[v].fn_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_fvar[v].smem);
         if (e != cudaSuccess) return e;
     }
     done = true;
     return cudaSuccess;
 }
 cudaError_t launch_field_step_variant(int prec, int v, const void* args, const void* items, int n_items,
-                                      cudaStream_t st) {
-    if (!prec) return launch_field_step_batched(prec, args, items, n_items, st);
+                                      cudaStream_t st, bool rec) {
+    if (!prec) return launch_field_step_batched(prec, args, items, n_items, st, rec);
     if (v < 0 || v >= N_FVAR) return cudaErrorInvalidValue;
     if (n_items <= 0 || !args) return cudaSuccess;
     const FieldVariant& f = g_fvar[v];
     void* kargs[2] = {(void*)&args, (void*)&items};
-    return cudaLaunchKernel(f.fn, dim3((unsigned)n_items), dim3(f.tx, f.ty), kargs, f.smem, st);
+    return cudaLaunchKernel(rec ? f.fn_rec : f.fn, dim3((unsigned)n_items), dim3(f.tx, f.ty), kargs, f.smem, st);
 }
 
 // ---------------------------------------------------------------- canonical layout

@@ -41,8 +41,10 @@ template <class T> static PushArgs<T> push_args(const PushHost& a, const PartHos
     A.expanding = a.expanding; A.acc = a.acc;
     A.boris = a.boris; A.dec0 = (T)a.dec0; A.dec1 = (T)a.dec1;
     A.nsub = a.nsub; A.hsub = (T)a.hsub; A.tau0 = (T)a.tau0; A.interp = a.interp;
+    A.rec = (const T*)a.rec; A.occ = a.occ; A.epoch_next = a.epoch_next;
     return A;
 }
+size_t record_bytes(int prec) { return (size_t)REC_STRIDE * 8 * (prec ? 4 : 8); }
 size_t push_args_size(int prec) { return prec ? sizeof(PushArgs<float>) : sizeof(PushArgs<double>); }
 void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out) {
     if (prec) *(PushArgs<float>*)out = push_args<float>(a, P);
@@ -51,7 +53,8 @@ void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out) {
 // Batched push kernels, chosen per batch by measurement (glasma_batch_tune):
 //   0: 128-thread blocks, 3 per SM, fields read through L1
 //   1: 32-thread blocks, 6 per SM, each particle's fields staged in shared memory first
-int push_variants() { return 2; }
+//   2: the fields from the gather records the field launch wrote (PUSH_VARIANT_RECORD)
+int push_variants() { return 3; }
 // shared-memory limit of the staged push (call outside stream capture)
 cudaError_t prepare_push_staged() {
     static bool done = false;
@@ -72,6 +75,8 @@ static cudaError_t push_batched_impl(int v, const void* args, const void* items,
         k_push_staged<T><<<(unsigned)n_items * (256 / PUSH_PPB), PUSH_PPB, push_staged_smem<T>(), st>>>(a, it);
     else if (v == PUSH_VARIANT_SUB)
         k_push_batched<T, 128, 3, true><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
+    else if (v == PUSH_VARIANT_RECORD)
+        k_push_record<T, 128, 4><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
     else
         k_push_batched<T, 128, 3><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
     return cudaGetLastError();

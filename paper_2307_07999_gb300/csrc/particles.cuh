@@ -37,6 +37,11 @@ template <class T> struct PushArgs {
     int boris;     // momentum kick: 0 explicit (first order), 1 Boris (second order)
     T dec0, dec1;  // Boris: p_eta^ decay tau_n/tau_{n+1/2}, tau_{n+1/2}/tau_{n+1} (1 in a static box)
     double* acc;   // this step's row: {sum dpx^2, sum dpy^2, sum dpz^2, count}
+    // record push (RecordSrc): the gather records the field step of this step wrote, and
+    // the occupancy stamps, set to epoch_next at every particle's new cell
+    const T* rec;
+    int* occ;
+    int epoch_next;
 };
 
 template <class T> DEV M3<T> dagger(const M3<T>& A) {
@@ -76,6 +81,7 @@ template <> DEV double clamp_below_one<double>(double v) { return fmin(v, 0.9999
 //                                            the link site -> site + i, pi likewise at c
 // Global source of the unfused push: the two field buffers of step n.
 template <class T, bool CG = false> struct GlobalSrc {
+    static constexpr bool kRecord = false;
     const T* fo;
     const T* fn;
     int n;
@@ -149,6 +155,7 @@ __host__ __device__ constexpr int stage_slot(int dx, int dy, int g, int b) {
     return -1;
 }
 template <class T> struct StagedSrc {
+    static constexpr bool kRecord = false;
     static constexpr int STRIDE = STAGE_SLOTS * 8 + (sizeof(T) == 4 ? 4 : 2);  // bank-spread record stride
     const T* rec;  // this thread's record
     struct View {
@@ -239,6 +246,62 @@ DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
     qB[2] = -T(0.25) * bz;
 }
 
+// Record source (batched push after a field step that wrote gather records, see the
+// record layout in field.cuh): the site-centred fields of the particle's cell come from
+// its record, one contiguous read, instead of 35 scattered field groups.  The pieces are
+// those gather_qf_view forms, contracted with Q in the same order; the pieces of the
+// neighbours c-x and c-y were stored untransported with their links, so Q is carried
+// there instead: Q.(U^dag X U) = (U Q U^dag).X.  Links for cell crossings and phi at
+// the cell come from the field buffer and the record.
+template <class T> struct RecordSrc {
+    static constexpr bool kRecord = true;
+    const T* rec;
+    GlobalSrc<T> g;
+    struct View {
+        const T* r;  // this cell's record
+        typename GlobalSrc<T>::View gv;
+        DEV Al<T> grp(int slot) const {
+            const V8<T> v = ld8<false>(r + 8 * slot);
+            Al<T> x;
+#pragma unroll
+            for (int a = 0; a < 8; a++) x.a[a] = v.v[a];
+            return x;
+        }
+        DEV M3<T> rlink(int slot) const {
+            const V8<T> a = ld8<false>(r + 8 * slot);
+            const V4<T> b = ld4<false>(r + 8 * (slot + 1));
+            M3<T> U;
+#pragma unroll
+            for (int e = 0; e < 4; e++) put_entry(U, e, a.v[2 * e], a.v[2 * e + 1]);
+            put_entry(U, 4, b.v[0], b.v[1]);
+            put_entry(U, 5, b.v[2], b.v[3]);
+            complete_row2(U);
+            return U;
+        }
+        DEV M3<T> link(int d, int dx, int dy) const { return gv.link(d, dx, dy); }
+        DEV Al<T> phi(int, int) const { return grp(R_PHI); }  // used at the cell itself only
+        DEV void gather(T te, const Al<T>& q, T qE[3], T qB[3]) const {
+            const T half = T(0.5);
+            const Al<T> ql = conj_alg(rlink(R_UXL), q);  // Q carried to c-x
+            const Al<T> qb = conj_alg(rlink(R_UYB), q);  // Q carried to c-y
+            qE[0] = half * (dot8(q, grp(R_EX)) + dot8(ql, grp(R_EXL))) / te;
+            qE[1] = half * (dot8(q, grp(R_EY)) + dot8(qb, grp(R_EYB))) / te;
+            qE[2] = dot8(q, grp(R_PI));
+            qB[1] = half * (dot8(q, grp(R_PSX)) - dot8(q, grp(R_CHX))) / te;
+            qB[0] = -half * (dot8(q, grp(R_PSY)) - dot8(q, grp(R_CHY))) / te;
+            // clover leaves in the order of clover_plaquette: +x+y, +y-x, -x-y, -y+x
+            T bz = dot8(q, grp(R_F0));
+            bz += dot8(q, grp(R_T2));
+            bz += dot8(ql, grp(R_T1L));
+            bz += dot8(q, grp(R_T1));
+            qB[2] = -T(0.25) * bz;
+        }
+    };
+    DEV View view(int cx, int cy) const {
+        return View{rec + ((size_t)cx + (size_t)g.n * cy) * REC_STRIDE * 8, g.view(cx, cy)};
+    }
+};
+
 // Cloud-in-cell gather: the Q-contracted fields of the four sites around the particle
 // (c, c+x, c+y, c+x+y) carried to c, with bilinear weights in the offsets (ox, oy).
 // Carrying the field F(s) to c is W F(s) W^dag with W the links from c to s (x before y
@@ -315,7 +378,7 @@ template <class T, class V> DEV void site_fields(const V& C, T te, Al<T> E[3], A
 // Without SUB the loop runs once with the host's coefficients (the kernels of the
 // default path are compiled without it: the loop's carried state costs registers).
 template <class T, class S, bool CG = false, bool SUB = false>
-DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, double& sy, double& sz, double& sc) {
+DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, T& sx, T& sy, T& sz, T& sc) {
     const PartSoA<T>& P = A.P;
     const int n = A.n;
     const int cell = CG ? __ldcg(P.cell + j) : P.cell[j];
@@ -349,7 +412,9 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
         }
         T qE[3], qB[3];
         const auto C = F.view(cx, cy);
-        if (SUB && A.interp)
+        if constexpr (S::kRecord)
+            C.gather(A.te, q, qE, qB);
+        else if (SUB && A.interp)
             gather_qf_cic(F, n, cx, cy, ox, oy, A.te, q, qE, qB);
         else
             gather_qf_view(C, A.te, q, qE, qB);
@@ -429,6 +494,7 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
         eta += deta;
     }
     P.cell[j] = cx + n * cy;
+    if constexpr (S::kRecord) A.occ[cx + n * cy] = A.epoch_next;  // the next field step writes its record
     P.ox[j] = ox;
     P.oy[j] = oy;
     P.eta[j] = eta;
@@ -437,24 +503,33 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, double& sx, doubl
     P.peta[j] = pz;
 #pragma unroll
     for (int a = 0; a < 8; a++) P.Q[(size_t)a * P.qs + j] = q.a[a];
-    // broadening terms: dp_i^2 = p_i^2 - p_i(tau_form)^2, lab p_z
-    const double pzl = A.expanding ? (double)ptn * sinh((double)eta) + (double)pz * cosh((double)eta)
-                                   : (double)pz;
-    const double p0z = (double)P.p0z[j];
-    sx = (double)dpx * (2.0 * (double)p0x + (double)dpx);
-    sy = (double)dpy * (2.0 * (double)p0y + (double)dpy);
-    sz = pzl * pzl - p0z * p0z;
-    sc = 1.0;
+    // broadening terms: dp_i^2 = p_i^2 - p_i(tau_form)^2, lab p_z.  The transverse terms
+    // are factored, dp (2 p0 + dp), so they carry no cancellation and are computed in the
+    // working precision; so is the longitudinal one when p_z(tau_form) = 0 (every particle
+    // formed at eta = 0 with p_eta^ = 0).  Otherwise p_z^2 - p0z^2 can cancel and is
+    // taken in FP64.  The sums over particles are FP64 (block_acc4).
+    const T p0z = P.p0z[j];
+    if (p0z == T(0)) {
+        const T pzl = A.expanding ? ptn * sinh(eta) + pz * cosh(eta) : pz;
+        sz = pzl * pzl;
+    } else {
+        const double pzl = A.expanding ? (double)ptn * sinh((double)eta) + (double)pz * cosh((double)eta)
+                                       : (double)pz;
+        sz = (T)(pzl * pzl - (double)p0z * (double)p0z);
+    }
+    sx = dpx * fma(T(2), p0x, dpx);
+    sy = dpy * fma(T(2), p0y, dpy);
+    sc = T(1);
 }
 
 template <class T, bool CG = false, bool SUB = false>
-DEV void push_one(const PushArgs<T>& A, int j, double& sx, double& sy, double& sz, double& sc) {
+DEV void push_one(const PushArgs<T>& A, int j, T& sx, T& sy, T& sz, T& sc) {
     GlobalSrc<T, CG> F{A.fo, A.fn, A.n, (size_t)A.n * A.n};
     push_one_src<T, GlobalSrc<T, CG>, CG, SUB>(A, F, j, sx, sy, sz, sc);
 }
 
 // warp -> block -> one FP64 atomic per block and term (any block shape, at most 256
-// threads, a multiple of 32)
+// threads, a multiple of 32).  FP64 terms: FP64 shuffles and sums.
 DEV void block_acc4(double sx, double sy, double sz, double sc, double* acc) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -476,10 +551,50 @@ DEV void block_acc4(double sx, double sy, double sz, double sc, double* acc) {
     }
 }
 
+// FP32 terms: the warp sums are compensated (Knuth's TwoSum keeps the rounding error of
+// every addition in a second FP32 word), so each warp's sum is the exact sum of its 32
+// terms to about 2^-48 relative, formed without FP64 arithmetic (slow on GB300); the
+// warp sums then go to FP64 and on as above.  The count term is an exact small integer.
+DEV void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+DEV void block_acc4(float tx, float ty, float tz, float tc, double* acc) {
+    float h[3] = {tx, ty, tz}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float oh = __shfl_down_sync(0xffffffffu, h[k], o), ol = __shfl_down_sync(0xffffffffu, l[k], o);
+            float sum, err;
+            two_sum(h[k], oh, sum, err);
+            h[k] = sum;
+            l[k] += ol + err;
+        }
+        tc += __shfl_down_sync(0xffffffffu, tc, o);
+    }
+    __shared__ double red[4][8];
+    const int lt = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+    const int w = lt >> 5, ln = lt & 31;
+    if (ln == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) red[k][w] = (double)h[k] + (double)l[k];
+        red[3][w] = (double)tc;
+    }
+    __syncthreads();
+    if (lt < 4) {
+        double t = 0.0;
+        for (int k = 0; k < nw; k++) t += red[lt][k];
+        atomicAdd(acc + lt, t);
+    }
+}
+
 template <class T, bool SUB = false>
 __global__ void __launch_bounds__(256) k_push(PushArgs<T> A) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
+    T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
     if (j < A.np) push_one<T, false, SUB>(A, j, sx, sy, sz, sc);
     block_acc4(sx, sy, sz, sc, A.acc);
 }
@@ -497,8 +612,26 @@ __global__ void __launch_bounds__(NT, MINB) k_push_batched(const PushArgs<T>* __
     const PushArgs<T> A = args[it.ev];
     if (A.acc == nullptr) return;
     const int j = it.j0 + (int)(blockIdx.x % SUB) * NT + threadIdx.x;
-    double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
+    T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
     if (j < A.np) push_one<T, false, MULTI>(A, j, sx, sy, sz, sc);
+    block_acc4(sx, sy, sz, sc, A.acc);
+}
+
+// batched record push: as k_push_batched, the fields from the gather records
+template <class T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_push_record(const PushArgs<T>* __restrict__ args,
+                                                          const PushItem* __restrict__ items) {
+    static_assert(256 % NT == 0 && NT % 32 == 0, "push block");
+    constexpr int SUB = 256 / NT;
+    const PushItem it = items[blockIdx.x / SUB];
+    const PushArgs<T> A = args[it.ev];
+    if (A.acc == nullptr) return;
+    const int j = it.j0 + (int)(blockIdx.x % SUB) * NT + threadIdx.x;
+    T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
+    if (j < A.np) {
+        const RecordSrc<T> F{A.rec, GlobalSrc<T>{A.fo, A.fn, A.n, (size_t)A.n * A.n}};
+        push_one_src<T, RecordSrc<T>>(A, F, j, sx, sy, sz, sc);
+    }
     block_acc4(sx, sy, sz, sc, A.acc);
 }
 
@@ -550,7 +683,7 @@ k_push_staged(const PushArgs<T>* __restrict__ args, const PushItem* __restrict__
     if (A.acc == nullptr) return;  // uniform over the block
     const int j = it.j0 + (int)(blockIdx.x % SUB) * PUSH_PPB + threadIdx.x;
     T* rec = reinterpret_cast<T*>(smem) + (size_t)threadIdx.x * StagedSrc<T>::STRIDE;
-    double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;
+    T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
     if (j < A.np) {
         const int n = A.n;
         const size_t ns = (size_t)n * n;

@@ -108,7 +108,7 @@ k_persistent(PersArgs<T> a) {
                     for (int h = 0; h < 256 / NT; h++) {
                         const int j = it.j0 + h * NT + tid;
                         if (j < A.np) {
-                            double a0, a1, a2, a3;
+                            T a0, a1, a2, a3;
                             push_one<T, true>(A, j, a0, a1, a2, a3);
                             sx += a0; sy += a1; sz += a2; sc += a3;
                         }

@@ -141,8 +141,10 @@ def test_tile_variants_are_bit_identical_and_tuning_picks_one():
                 assert rel_err(mons[e][:6], ref[2][e][:6]) < 1e-12, (shapes[v], mode, e)
     # the push kernels (fields through L1, or staged in shared memory): the same source
     # compiled into two kernels, whose FMA contractions may differ: equal to FP32 rounding
+    # (the record push, variant 2, contracts the same pieces in another order: its FP32
+    # results are checked against the oracle in test_gpu_records.py)
     B.set_variant(0)
-    assert G.lib().glasma_push_variants() == 2
+    assert G.lib().glasma_push_variants() == 3
     for pv in range(2):
         B.set_push_variant(pv)
         assert B.push_variant == pv
@@ -155,9 +157,10 @@ def test_tile_variants_are_bit_identical_and_tuning_picks_one():
     print("tile variant times (ms):", {shapes[v]: round(ms[v], 3) for v in range(nv)}, "chosen", shapes[chosen],
           "push kernel", B.push_variant)
     assert 0 <= chosen < nv and B.variant == chosen and all(m > 0 for m in ms)
-    assert B.push_variant in (0, 1)
+    assert B.push_variant in (0, 1, 2)
     B.run("graph")
-    assert rel_err(B.get_particles(0)["px"], ref[0][0]["px"]) < 2e-6
+    tol = 2e-6 if B.push_variant in (0, 1) else 1e-4
+    assert rel_err(B.get_particles(0)["px"], ref[0][0]["px"]) < tol
 
 
 def test_full_size_batch_sampled():
