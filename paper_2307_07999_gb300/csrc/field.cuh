@@ -356,8 +356,11 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     }
     __syncthreads();
 
-    // phase 2: ImTL P(x) for x in [x0-1, x0+TX) x [y0-1, y0+TY)
-    for (int i = tid; i < FS; i += TX * TY) {
+    // phase 2: ImTL P(x) for x in [x0-1, x0+TX) x [y0-1, y0+TY).  The plaquettes beyond
+    // the first TX*TY go to the threads that loaded one halo site fewer in phase 1, so that
+    // no thread does a second round of both before the barrier.
+    constexpr int NT2 = TX * TY, R1 = HS > NT2 ? (HS - NT2) % NT2 : 0;
+    for (int i = (tid + NT2 - R1) % NT2; i < FS; i += NT2) {
         const int fx = i % FX, fy = i / FX;
         const int h = fy * HX + fx;
         const M3<T> a1 = mul(rec_link(sUx, h), rec_link(sUy, h + 1));

@@ -5,7 +5,8 @@
   python -m paper_2307_07999_gb300.profile_driver batch              # one graph run of the 64-event batch
   python -m paper_2307_07999_gb300.profile_driver batch8             # 8 events of 384^2, 10k charm each
     (both batch workloads tune the field tile shape first: 8 variants x 5 field launches;
-     a last argument v=<k> sets field tile variant k instead, without tuning)
+     an argument v=<k> sets field tile variant k instead, without tuning, and p=<k> the
+     batched push kernel k, e.g. p=2 for the record push)
   python -m paper_2307_07999_gb300.profile_driver ic 1024            # tau = 0+ solve: cold, then warm start
   python -m paper_2307_07999_gb300.profile_driver corr 512           # 4 FP32 field steps with both correlators
 """
@@ -28,6 +29,9 @@ def main(argv):
             B.set_variant(int(fixed[0][2:]))
         else:
             B.tune(steps=4)  # the tile shape bench.py would run (8 variants x 5 launches first)
+        push = [a for a in argv[2:] if a.startswith("p=")]
+        if push:
+            B.set_push_variant(int(push[0][2:]))
         B.run("graph")
         torch.cuda.synchronize()
         print("ok")

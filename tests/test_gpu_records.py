@@ -86,8 +86,10 @@ def test_record_push_fp32_matches_oracle():
 @pytest.mark.parametrize("prec", [0, 1])
 def test_records_leave_the_fields_unchanged(prec):
     """The field launches that write records run the field arithmetic of the plain ones:
-    the final fields of every event agree (monitors to their FP64 summation order), and
-    eager and graph runs of the record push agree bit for bit."""
+    the final fields of every event agree (FP64: monitors to their FP64 summation order;
+    FP32: to the growth of rounding differences, since the compiler may contract some
+    multiply-adds of the two kernels differently), and eager and graph runs of the record
+    push agree bit for bit."""
     evs, pps = small_events(prec, tol=1e-14)
     B = G.Batch(evs, pps)
     B.init()
@@ -98,8 +100,9 @@ def test_records_leave_the_fields_unchanged(prec):
     B.run("graph")
     mon1 = [B.diagnostics(e) for e in range(len(evs))]
     parts_g = [B.get_particles(e) for e in range(len(evs))]
+    tol = 1e-12 if prec == 0 else 1e-5
     for e in range(len(evs)):
-        assert rel_err(mon1[e][:6], mon0[e][:6]) < 1e-12, e
+        assert rel_err(mon1[e][:6], mon0[e][:6]) < tol, e
     B.run("eager")
     for e in range(len(evs)):
         part = B.get_particles(e)
