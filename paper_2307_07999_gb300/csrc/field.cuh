@@ -272,22 +272,40 @@ template <class T> DEV void rec_put_alg(T* s, int h, const Al<T>& x) {
 template <class T> DEV T* rec_at(T* rec, size_t cell, int slot) {
     return rec + (cell * REC_STRIDE + (size_t)slot) * 8;
 }
-template <class T> DEV void rec_store(T* rec, size_t cell, int slot, const Al<T>& x) {
-    V8<T> q;
-#pragma unroll
-    for (int a = 0; a < 8; a++) q.v[a] = x.a[a];
-    st8(rec_at(rec, cell, slot), q);
+// Predicated stores: the record writes of the field step are issued under a predicate
+// instead of a branch, so that the step's arithmetic stays one straight-line block the
+// compiler schedules freely (branches around the stores cost the FP32 step 17 % even
+// with the stores themselves removed).  The address is in bounds either way.
+DEV void st8_if(bool p, float* a, const float* v) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
+        "@q st.global.v8.f32 [%1], {%2,%3,%4,%5,%6,%7,%8,%9};\n\t}"
+        ::"r"((int)p), "l"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+        : "memory");
 }
-// rows 0, 1 of a link into two groups (entries 0..3, then 4, 5)
-template <class T> DEV void rec_store_link(T* rec, size_t cell, int slot, const M3<T>& U) {
-    V8<T> a;
+DEV void st8_if(bool p, double* a, const double* v) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
+        "@q st.global.v2.f64 [%1], {%2,%3};\n\t@q st.global.v2.f64 [%1+16], {%4,%5};\n\t"
+        "@q st.global.v2.f64 [%1+32], {%6,%7};\n\t@q st.global.v2.f64 [%1+48], {%8,%9};\n\t}"
+        ::"r"((int)p), "l"(a), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3]), "d"(v[4]), "d"(v[5]), "d"(v[6]), "d"(v[7])
+        : "memory");
+}
+template <class T> DEV void rec_store(bool p, T* rec, size_t cell, int slot, const Al<T>& x) {
+    st8_if(p, rec_at(rec, cell, slot), x.a);
+}
+// rows 0, 1 of a link into two groups (entries 0..3, then 4, 5, and two unused reals)
+template <class T> DEV void rec_store_link(bool p, T* rec, size_t cell, int slot, const M3<T>& U) {
+    T a[8], b[8];
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-        a.v[2 * e] = U.m[e / 3][e % 3].r;
-        a.v[2 * e + 1] = U.m[e / 3][e % 3].i;
+        a[2 * e] = U.m[e / 3][e % 3].r;
+        a[2 * e + 1] = U.m[e / 3][e % 3].i;
     }
-    st8(rec_at(rec, cell, slot), a);
-    st4(rec_at(rec, cell, slot + 1), U.m[1][1].r, U.m[1][1].i, U.m[1][2].r, U.m[1][2].i);
+    b[0] = U.m[1][1].r; b[1] = U.m[1][1].i; b[2] = U.m[1][2].r; b[3] = U.m[1][2].i;
+    b[4] = b[5] = b[6] = b[7] = T(0);
+    st8_if(p, rec_at(rec, cell, slot), a);
+    st8_if(p, rec_at(rec, cell, slot + 1), b);
 }
 
 // One tile [x0, x0+TX) x [y0, y0+TY) of one step: kick at tau_n, drift with tau_{n+1/2}.
@@ -311,16 +329,6 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     const bool active = (x < n) && (y < n);
     const size_t s = active ? (size_t)x + (size_t)n * y : 0;
     Al<T> Ex = load_alg<T, CG>(src, ns, P_EX, s), Ey = load_alg<T, CG>(src, ns, P_EY, s), pi = load_alg<T, CG>(src, ns, P_PI, s);
-    // occupancy stamps of the own cell and of the cells +x, +y (whose records take this
-    // site's neighbour pieces), loaded with the fields
-    int o0 = 0, ox = 0, oy = 0;
-    if constexpr (REC) {
-        if (active && !A.all_rec) {
-            o0 = __ldg(A.occ + s);
-            ox = __ldg(A.occ + (x == n - 1 ? s - (size_t)(n - 1) : s + 1));
-            oy = __ldg(A.occ + (y == n - 1 ? s - (size_t)n * (n - 1) : s + (size_t)n));
-        }
-    }
 
     // phase 1: links (completed to 3 rows) and phi of the tile plus a one-site halo.
     // Every load of the thread is issued before the first store, so the CTA waits for
@@ -375,29 +383,40 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     const int f = (threadIdx.y + 1) * FX + threadIdx.x + 1;
     const Al<T> phi = rec_alg(sP, h);
     const T dt = A.dtau, tb = A.tb, tp = A.tp;
-    // which records this thread writes: bit 0 its own cell's, bit 1 the pieces of cell +x,
-    // bit 2 those of cell +y (REC only)
-    unsigned rm = 0;
-    if constexpr (REC) {
-        rm = A.all_rec ? 7u : ((o0 == A.epoch ? 1u : 0u) | (ox == A.epoch ? 2u : 0u) | (oy == A.epoch ? 4u : 0u));
-        if (rm & 1u) rec_store(A.rec, s, R_PHI, phi);
-    }
     // neighbour cells +x, +y (periodic)
     const auto cell_xp = [&]() { return x == n - 1 ? s - (size_t)(n - 1) : s + 1; };
     const auto cell_yp = [&]() { return y == n - 1 ? s - (size_t)n * (n - 1) : s + (size_t)n; };
+    // REC: the occupancy stamps of the own cell and of the cells +x, +y (whose records
+    // take this site's neighbour pieces), loaded here and first used after the first
+    // transport, so that their latency is hidden and no register holds them through
+    // phases 1-2.  rm: bit 0 this thread writes its own cell's record, bit 1 the pieces
+    // of cell +x, bit 2 those of cell +y.
+    int o0 = 0, ox = 0, oy = 0;
+    if constexpr (REC) {
+        const int* occ = A.occ;
+        o0 = __ldg(occ + s);
+        ox = __ldg(occ + cell_xp());
+        oy = __ldg(occ + cell_yp());
+    }
+    unsigned rm = 0;
     // Each link is read from shared memory where it is used and its terms are folded
     // into the increments at once, which keeps few values live per thread.
     Al<T> dEx, dEy, dpi;
     {  // forward x link: U phi(x+x) U^dag, and its commutator with phi (E_x)
         const Al<T> psx = conj_alg(rec_link(sUx, h), rec_alg(sP, h + 1));
-        if (REC && (rm & 1u)) rec_store(A.rec, s, R_PSX, psx);
+        if constexpr (REC) {
+            const int ep = A.epoch;
+            rm = A.all_rec ? 7u : ((o0 == ep ? 1u : 0u) | (ox == ep ? 2u : 0u) | (oy == ep ? 4u : 0u));
+            rec_store((rm & 1u) != 0, A.rec, s, R_PHI, phi);
+            rec_store((rm & 1u) != 0, A.rec, s, R_PSX, psx);
+        }
         const Al<T> cm = icomm(phi, psx);
 #pragma unroll
         for (int a = 0; a < 8; a++) { dpi.a[a] = psx.a[a]; dEx.a[a] = -tp * cm.a[a]; }
     }
     {  // forward y link (E_y)
         const Al<T> psy = conj_alg(rec_link(sUy, h), rec_alg(sP, h + HX));
-        if (REC && (rm & 1u)) rec_store(A.rec, s, R_PSY, psy);
+        if constexpr (REC) rec_store((rm & 1u) != 0, A.rec, s, R_PSY, psy);
         const Al<T> cm = icomm(phi, psy);
 #pragma unroll
         for (int a = 0; a < 8; a++) { dpi.a[a] += psy.a[a]; dEy.a[a] = -tp * cm.a[a]; }
@@ -406,9 +425,9 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         const M3<T> uxm = rec_link(sUx, h - 1);
         const Al<T> chx = transport_alg(uxm, rec_alg(sP, h - 1));
         const Al<T> t2 = transport_alg(uxm, rec_alg(sF, f - 1));
-        if (REC && (rm & 1u)) {
-            rec_store(A.rec, s, R_CHX, chx);
-            rec_store(A.rec, s, R_T2, t2);
+        if constexpr (REC) {
+            rec_store((rm & 1u) != 0, A.rec, s, R_CHX, chx);
+            rec_store((rm & 1u) != 0, A.rec, s, R_T2, t2);
         }
 #pragma unroll
         for (int a = 0; a < 8; a++) { dpi.a[a] += chx.a[a]; dEy.a[a] -= tb * t2.a[a]; }
@@ -417,11 +436,11 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         const M3<T> uym = rec_link(sUy, h - HX);
         const Al<T> chy = transport_alg(uym, rec_alg(sP, h - HX));
         const Al<T> t1 = transport_alg(uym, rec_alg(sF, f - FX));
-        if (REC && (rm & 1u)) {
-            rec_store(A.rec, s, R_CHY, chy);
-            rec_store(A.rec, s, R_T1, t1);
+        if constexpr (REC) {
+            rec_store((rm & 1u) != 0, A.rec, s, R_CHY, chy);
+            rec_store((rm & 1u) != 0, A.rec, s, R_T1, t1);
+            rec_store((rm & 2u) != 0, A.rec, cell_xp(), R_T1L, t1);
         }
-        if (REC && (rm & 2u)) rec_store(A.rec, cell_xp(), R_T1L, t1);
 #pragma unroll
         for (int a = 0; a < 8; a++) { dpi.a[a] += chy.a[a]; dEx.a[a] += tb * t1.a[a]; }
     }
@@ -430,7 +449,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         if constexpr (REC) {
             // the same updates, one field at a time, each followed by its time average
             // (E_{n-1/2} + E_{n+1/2}) / 2 formed exactly as the unfused gather forms it
-            if (rm & 1u) rec_store(A.rec, s, R_F0, F0);
+            rec_store((rm & 1u) != 0, A.rec, s, R_F0, F0);
             Al<T> av;
 #pragma unroll
             for (int a = 0; a < 8; a++) {
@@ -438,23 +457,23 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
                 Ex.a[a] += dt * (dEx.a[a] - tb * F0.a[a]);
                 av.a[a] = T(0.5) * (o + Ex.a[a]);
             }
-            if (rm & 1u) rec_store(A.rec, s, R_EX, av);
-            if (rm & 2u) rec_store(A.rec, cell_xp(), R_EXL, av);
+            rec_store((rm & 1u) != 0, A.rec, s, R_EX, av);
+            rec_store((rm & 2u) != 0, A.rec, cell_xp(), R_EXL, av);
 #pragma unroll
             for (int a = 0; a < 8; a++) {
                 const T o = Ey.a[a];
                 Ey.a[a] += dt * (dEy.a[a] + tb * F0.a[a]);
                 av.a[a] = T(0.5) * (o + Ey.a[a]);
             }
-            if (rm & 1u) rec_store(A.rec, s, R_EY, av);
-            if (rm & 4u) rec_store(A.rec, cell_yp(), R_EYB, av);
+            rec_store((rm & 1u) != 0, A.rec, s, R_EY, av);
+            rec_store((rm & 4u) != 0, A.rec, cell_yp(), R_EYB, av);
 #pragma unroll
             for (int a = 0; a < 8; a++) {
                 const T o = pi.a[a];
                 pi.a[a] += dt * tp * (dpi.a[a] - T(4) * phi.a[a]);
                 av.a[a] = T(0.5) * (o + pi.a[a]);
             }
-            if (rm & 1u) rec_store(A.rec, s, R_PI, av);
+            rec_store((rm & 1u) != 0, A.rec, s, R_PI, av);
         } else {
 #pragma unroll
             for (int a = 0; a < 8; a++) {
@@ -482,8 +501,8 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         const M3<T> W = expi(herm(e));
         const M3<T> U = rec_link(d == 0 ? sUx : sUy, h);
         if constexpr (REC) {  // U_n of this site for the record of cell +x (U_x) or +y (U_y)
-            if (d == 0 && (rm & 2u)) rec_store_link(A.rec, cell_xp(), R_UXL, U);
-            if (d == 1 && (rm & 4u)) rec_store_link(A.rec, cell_yp(), R_UYB, U);
+            if (d == 0) rec_store_link((rm & 2u) != 0, A.rec, cell_xp(), R_UXL, U);
+            else rec_store_link((rm & 4u) != 0, A.rec, cell_yp(), R_UYB, U);
         }
         M3<T> V;
 #pragma unroll
