@@ -38,25 +38,27 @@ template <class T> struct StepArgs {
     int epoch, all_rec;
 };
 
-// Gather record of a cell c for the push of step n (8-real groups, record stride
-// REC_STRIDE groups so that a record is whole 128-byte lines in FP32).  Written by the
-// field step of step n, which computes each piece anyway:
-//   R_EX, R_EY, R_PI  time-centred E_x(c), E_y(c), pi(c): (X_{n-1/2} + X_{n+1/2}) / 2
-//   R_PHI             phi_n(c)
-//   R_PSX, R_CHX      U_x(c) phi(c+x) U_x(c)^dag and U_x(c-x)^dag phi(c-x) U_x(c-x)
-//   R_PSY, R_CHY      the same along y
-//   R_F0              ImTL of the plaquette based at c
-//   R_T1, R_T2        ImTL of the plaquettes at c-y and c-x carried to c by U_y(c-y), U_x(c-x)
-//                     (the clover leaves (-y,+x) and (+y,-x) of c)
-// and by the owners of the neighbours c-x and c-y:
-//   R_EXL             time-centred E_x(c-x)      R_T1L   R_T1 of c-x
-//   R_UXL (2 groups)  U_x(c-x) rows 0, 1          R_EYB   time-centred E_y(c-y)
-//   R_UYB (2 groups)  U_y(c-y) rows 0, 1
+// Gather record of a cell c for the push of step n (8-real groups; REC_STRIDE groups per
+// record, so that in FP32 a record is five whole 128-byte lines).  Written by the field
+// step of step n, which computes each piece anyway.  Each writer fills whole lines (the
+// unused groups are written as zeros), so the records reach DRAM as full lines:
+//   lines 0-2, the owner of c:
+//     R_EX, R_EY, R_PI  time-centred E_x(c), E_y(c), pi(c): (X_{n-1/2} + X_{n+1/2}) / 2
+//     R_PHI             phi_n(c)
+//     R_PSX, R_CHX      U_x(c) phi(c+x) U_x(c)^dag and U_x(c-x)^dag phi(c-x) U_x(c-x)
+//     R_PSY, R_CHY      the same along y
+//     R_F0              ImTL of the plaquette based at c
+//     R_T1, R_T2        ImTL of the plaquettes at c-y and c-x carried to c by U_y(c-y), U_x(c-x)
+//                       (the clover leaves (-y,+x) and (+y,-x) of c)
+//   line 3, the owner of c-x:  R_EXL time-centred E_x(c-x), R_T1L its R_T1, R_UXL (2 groups)
+//                              U_x(c-x) rows 0, 1
+//   line 4, the owner of c-y:  R_EYB time-centred E_y(c-y), R_UYB (2 groups) U_y(c-y) rows 0, 1
 // so that Q.E_x(c) = (Q.E_x(c) + Q'.E_x(c-x)) / 2 with Q' = U_x(c-x) Q U_x(c-x)^dag, and the
 // fourth clover leaf (-x,-y) of c contracts as Q'.R_T1L.
 enum {
-    R_EX = 0, R_EY, R_PI, R_PHI, R_PSX, R_CHX, R_PSY, R_CHY, R_F0, R_T1, R_T2,
-    R_EXL, R_T1L, R_EYB, R_UXL, R_UYB = R_UXL + 2, REC_GROUPS = R_UYB + 2, REC_STRIDE = 20
+    R_EX = 0, R_EY, R_PI, R_PHI, R_PSX, R_CHX, R_PSY, R_CHY, R_F0, R_T1, R_T2, R_PAD0,
+    R_EXL = 12, R_T1L, R_UXL,
+    R_EYB = 16, R_UYB, R_PAD1 = 19, REC_STRIDE = 20
 };
 
 struct TileItem { int ev, x0, y0; };
@@ -272,24 +274,22 @@ template <class T> DEV void rec_put_alg(T* s, int h, const Al<T>& x) {
 template <class T> DEV T* rec_at(T* rec, size_t cell, int slot) {
     return rec + (cell * REC_STRIDE + (size_t)slot) * 8;
 }
-// Predicated stores: the record writes of the field step are issued under a predicate
-// instead of a branch, so that the step's arithmetic stays one straight-line block the
-// compiler schedules freely (branches around the stores cost the FP32 step 17 % even
-// with the stores themselves removed).  The address is in bounds either way.
+// Record stores, predicated rather than branched (a branch around each store splits the
+// step's arithmetic into blocks the scheduler cannot cross), and without a memory clobber
+// so that the shared-memory and global loads of the step may move across them (nothing
+// the step reads aliases the record buffer).
 DEV void st8_if(bool p, float* a, const float* v) {
     asm volatile(
         "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
         "@q st.global.v8.f32 [%1], {%2,%3,%4,%5,%6,%7,%8,%9};\n\t}"
-        ::"r"((int)p), "l"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
-        : "memory");
+        ::"r"((int)p), "l"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]));
 }
 DEV void st8_if(bool p, double* a, const double* v) {
     asm volatile(
         "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
         "@q st.global.v2.f64 [%1], {%2,%3};\n\t@q st.global.v2.f64 [%1+16], {%4,%5};\n\t"
         "@q st.global.v2.f64 [%1+32], {%6,%7};\n\t@q st.global.v2.f64 [%1+48], {%8,%9};\n\t}"
-        ::"r"((int)p), "l"(a), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3]), "d"(v[4]), "d"(v[5]), "d"(v[6]), "d"(v[7])
-        : "memory");
+        ::"r"((int)p), "l"(a), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3]), "d"(v[4]), "d"(v[5]), "d"(v[6]), "d"(v[7]));
 }
 template <class T> DEV void rec_store(bool p, T* rec, size_t cell, int slot, const Al<T>& x) {
     st8_if(p, rec_at(rec, cell, slot), x.a);
@@ -383,14 +383,15 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     const int f = (threadIdx.y + 1) * FX + threadIdx.x + 1;
     const Al<T> phi = rec_alg(sP, h);
     const T dt = A.dtau, tb = A.tb, tp = A.tp;
-    // neighbour cells +x, +y (periodic)
-    const auto cell_xp = [&]() { return x == n - 1 ? s - (size_t)(n - 1) : s + 1; };
-    const auto cell_yp = [&]() { return y == n - 1 ? s - (size_t)n * (n - 1) : s + (size_t)n; };
     // REC: the occupancy stamps of the own cell and of the cells +x, +y (whose records
     // take this site's neighbour pieces), loaded here and first used after the first
     // transport, so that their latency is hidden and no register holds them through
     // phases 1-2.  rm: bit 0 this thread writes its own cell's record, bit 1 the pieces
-    // of cell +x, bit 2 those of cell +y.
+    // of cell +x, bit 2 those of cell +y; bits 3 and 4 mark a site on the last column or
+    // row (the +x, +y neighbours wrap), so that no coordinate stays live for the stores.
+    unsigned rm = (x == n - 1 ? 8u : 0u) | (y == n - 1 ? 16u : 0u);
+    const auto cell_xp = [&]() { return (rm & 8u) ? s - (size_t)(n - 1) : s + 1; };
+    const auto cell_yp = [&]() { return (rm & 16u) ? s - (size_t)n * (n - 1) : s + (size_t)n; };
     int o0 = 0, ox = 0, oy = 0;
     if constexpr (REC) {
         const int* occ = A.occ;
@@ -398,7 +399,6 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         ox = __ldg(occ + cell_xp());
         oy = __ldg(occ + cell_yp());
     }
-    unsigned rm = 0;
     // Each link is read from shared memory where it is used and its terms are folded
     // into the increments at once, which keeps few values live per thread.
     Al<T> dEx, dEy, dpi;
@@ -406,7 +406,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         const Al<T> psx = conj_alg(rec_link(sUx, h), rec_alg(sP, h + 1));
         if constexpr (REC) {
             const int ep = A.epoch;
-            rm = A.all_rec ? 7u : ((o0 == ep ? 1u : 0u) | (ox == ep ? 2u : 0u) | (oy == ep ? 4u : 0u));
+            rm |= A.all_rec ? 7u : ((o0 == ep ? 1u : 0u) | (ox == ep ? 2u : 0u) | (oy == ep ? 4u : 0u));
             rec_store((rm & 1u) != 0, A.rec, s, R_PHI, phi);
             rec_store((rm & 1u) != 0, A.rec, s, R_PSX, psx);
         }
@@ -450,6 +450,12 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
             // the same updates, one field at a time, each followed by its time average
             // (E_{n-1/2} + E_{n+1/2}) / 2 formed exactly as the unfused gather forms it
             rec_store((rm & 1u) != 0, A.rec, s, R_F0, F0);
+            {
+                Al<T> z;
+#pragma unroll
+                for (int a = 0; a < 8; a++) z.a[a] = T(0);
+                rec_store((rm & 1u) != 0, A.rec, s, R_PAD0, z);
+            }
             Al<T> av;
 #pragma unroll
             for (int a = 0; a < 8; a++) {
@@ -502,7 +508,13 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         const M3<T> U = rec_link(d == 0 ? sUx : sUy, h);
         if constexpr (REC) {  // U_n of this site for the record of cell +x (U_x) or +y (U_y)
             if (d == 0) rec_store_link((rm & 2u) != 0, A.rec, cell_xp(), R_UXL, U);
-            else rec_store_link((rm & 4u) != 0, A.rec, cell_yp(), R_UYB, U);
+            else {
+                rec_store_link((rm & 4u) != 0, A.rec, cell_yp(), R_UYB, U);
+                Al<T> z;
+#pragma unroll
+                for (int a = 0; a < 8; a++) z.a[a] = T(0);
+                rec_store((rm & 4u) != 0, A.rec, cell_yp(), R_PAD1, z);
+            }
         }
         M3<T> V;
 #pragma unroll
