@@ -274,36 +274,39 @@ template <class T> DEV void rec_put_alg(T* s, int h, const Al<T>& x) {
 template <class T> DEV T* rec_at(T* rec, size_t cell, int slot) {
     return rec + (cell * REC_STRIDE + (size_t)slot) * 8;
 }
-// Record stores, predicated rather than branched (a branch around each store splits the
-// step's arithmetic into blocks the scheduler cannot cross), and without a memory clobber
-// so that the shared-memory and global loads of the step may move across them (nothing
-// the step reads aliases the record buffer).
-DEV void st8_if(bool p, float* a, const float* v) {
-    asm volatile(
-        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
-        "@q st.global.v8.f32 [%1], {%2,%3,%4,%5,%6,%7,%8,%9};\n\t}"
-        ::"r"((int)p), "l"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]));
+// Record stores: plain C++ 256-bit stores under a condition, which the compiler turns into
+// predicated stores and schedules with the step's arithmetic (inline-asm stores are kept in
+// program order, which holds their operands live and raised the step's local-memory use).
+DEV void st8_if(bool p, float* a, const V8<float>& v) {
+    ulonglong4_32a w;
+    w.x = ((unsigned long long)__float_as_uint(v.v[1]) << 32) | __float_as_uint(v.v[0]);
+    w.y = ((unsigned long long)__float_as_uint(v.v[3]) << 32) | __float_as_uint(v.v[2]);
+    w.z = ((unsigned long long)__float_as_uint(v.v[5]) << 32) | __float_as_uint(v.v[4]);
+    w.w = ((unsigned long long)__float_as_uint(v.v[7]) << 32) | __float_as_uint(v.v[6]);
+    if (p) *reinterpret_cast<ulonglong4_32a*>(a) = w;
 }
-DEV void st8_if(bool p, double* a, const double* v) {
-    asm volatile(
-        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t"
-        "@q st.global.v2.f64 [%1], {%2,%3};\n\t@q st.global.v2.f64 [%1+16], {%4,%5};\n\t"
-        "@q st.global.v2.f64 [%1+32], {%6,%7};\n\t@q st.global.v2.f64 [%1+48], {%8,%9};\n\t}"
-        ::"r"((int)p), "l"(a), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3]), "d"(v[4]), "d"(v[5]), "d"(v[6]), "d"(v[7]));
+DEV void st8_if(bool p, double* a, const V8<double>& v) {
+    if (p) {
+        reinterpret_cast<double4_32a*>(a)[0] = double4_32a{v.v[0], v.v[1], v.v[2], v.v[3]};
+        reinterpret_cast<double4_32a*>(a)[1] = double4_32a{v.v[4], v.v[5], v.v[6], v.v[7]};
+    }
 }
 template <class T> DEV void rec_store(bool p, T* rec, size_t cell, int slot, const Al<T>& x) {
-    st8_if(p, rec_at(rec, cell, slot), x.a);
+    V8<T> q;
+#pragma unroll
+    for (int a = 0; a < 8; a++) q.v[a] = x.a[a];
+    st8_if(p, rec_at(rec, cell, slot), q);
 }
 // rows 0, 1 of a link into two groups (entries 0..3, then 4, 5, and two unused reals)
 template <class T> DEV void rec_store_link(bool p, T* rec, size_t cell, int slot, const M3<T>& U) {
-    T a[8], b[8];
+    V8<T> a, b;
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-        a[2 * e] = U.m[e / 3][e % 3].r;
-        a[2 * e + 1] = U.m[e / 3][e % 3].i;
+        a.v[2 * e] = U.m[e / 3][e % 3].r;
+        a.v[2 * e + 1] = U.m[e / 3][e % 3].i;
     }
-    b[0] = U.m[1][1].r; b[1] = U.m[1][1].i; b[2] = U.m[1][2].r; b[3] = U.m[1][2].i;
-    b[4] = b[5] = b[6] = b[7] = T(0);
+    b.v[0] = U.m[1][1].r; b.v[1] = U.m[1][1].i; b.v[2] = U.m[1][2].r; b.v[3] = U.m[1][2].i;
+    b.v[4] = b.v[5] = b.v[6] = b.v[7] = T(0);
     st8_if(p, rec_at(rec, cell, slot), a);
     st8_if(p, rec_at(rec, cell, slot + 1), b);
 }
@@ -390,14 +393,14 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     // of cell +x, bit 2 those of cell +y; bits 3 and 4 mark a site on the last column or
     // row (the +x, +y neighbours wrap), so that no coordinate stays live for the stores.
     unsigned rm = (x == n - 1 ? 8u : 0u) | (y == n - 1 ? 16u : 0u);
-    const auto cell_xp = [&]() { return (rm & 8u) ? s - (size_t)(n - 1) : s + 1; };
-    const auto cell_yp = [&]() { return (rm & 16u) ? s - (size_t)n * (n - 1) : s + (size_t)n; };
+#define GL_CELL_XP ((rm & 8u) ? s - (size_t)(n - 1) : s + 1)
+#define GL_CELL_YP ((rm & 16u) ? s - (size_t)n * (n - 1) : s + (size_t)n)
     int o0 = 0, ox = 0, oy = 0;
     if constexpr (REC) {
         const int* occ = A.occ;
         o0 = __ldg(occ + s);
-        ox = __ldg(occ + cell_xp());
-        oy = __ldg(occ + cell_yp());
+        ox = __ldg(occ + GL_CELL_XP);
+        oy = __ldg(occ + GL_CELL_YP);
     }
     // Each link is read from shared memory where it is used and its terms are folded
     // into the increments at once, which keeps few values live per thread.
@@ -439,7 +442,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         if constexpr (REC) {
             rec_store((rm & 1u) != 0, A.rec, s, R_CHY, chy);
             rec_store((rm & 1u) != 0, A.rec, s, R_T1, t1);
-            rec_store((rm & 2u) != 0, A.rec, cell_xp(), R_T1L, t1);
+            rec_store((rm & 2u) != 0, A.rec, GL_CELL_XP, R_T1L, t1);
         }
 #pragma unroll
         for (int a = 0; a < 8; a++) { dpi.a[a] += chy.a[a]; dEx.a[a] += tb * t1.a[a]; }
@@ -464,7 +467,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
                 av.a[a] = T(0.5) * (o + Ex.a[a]);
             }
             rec_store((rm & 1u) != 0, A.rec, s, R_EX, av);
-            rec_store((rm & 2u) != 0, A.rec, cell_xp(), R_EXL, av);
+            rec_store((rm & 2u) != 0, A.rec, GL_CELL_XP, R_EXL, av);
 #pragma unroll
             for (int a = 0; a < 8; a++) {
                 const T o = Ey.a[a];
@@ -472,7 +475,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
                 av.a[a] = T(0.5) * (o + Ey.a[a]);
             }
             rec_store((rm & 1u) != 0, A.rec, s, R_EY, av);
-            rec_store((rm & 4u) != 0, A.rec, cell_yp(), R_EYB, av);
+            rec_store((rm & 4u) != 0, A.rec, GL_CELL_YP, R_EYB, av);
 #pragma unroll
             for (int a = 0; a < 8; a++) {
                 const T o = pi.a[a];
@@ -507,13 +510,13 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         const M3<T> W = expi(herm(e));
         const M3<T> U = rec_link(d == 0 ? sUx : sUy, h);
         if constexpr (REC) {  // U_n of this site for the record of cell +x (U_x) or +y (U_y)
-            if (d == 0) rec_store_link((rm & 2u) != 0, A.rec, cell_xp(), R_UXL, U);
+            if (d == 0) rec_store_link((rm & 2u) != 0, A.rec, GL_CELL_XP, R_UXL, U);
             else {
-                rec_store_link((rm & 4u) != 0, A.rec, cell_yp(), R_UYB, U);
+                rec_store_link((rm & 4u) != 0, A.rec, GL_CELL_YP, R_UYB, U);
                 Al<T> z;
 #pragma unroll
                 for (int a = 0; a < 8; a++) z.a[a] = T(0);
-                rec_store((rm & 4u) != 0, A.rec, cell_yp(), R_PAD1, z);
+                rec_store((rm & 4u) != 0, A.rec, GL_CELL_YP, R_PAD1, z);
             }
         }
         M3<T> V;
@@ -527,6 +530,8 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
         Vn[d] = V;
     }
     store_links(dst, ns, s, Vn[0], Vn[1]);
+#undef GL_CELL_XP
+#undef GL_CELL_YP
 }
 
 }  // namespace glasma
