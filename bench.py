@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="auto", choices=["auto", "graph", "persistent", "eager", "per_event", "fused"])
+    p.add_argument("--mode", default="auto", choices=["auto", "graph", "persistent", "eager", "per_event"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--g2mu", type=float, default=2.0, help="MV scale g^2 mu (GeV) of the scans workload")
@@ -336,7 +336,7 @@ def run_ours(args, ws, rank, local):
         barrier(ws)
         return e0.elapsed_time(e1) / K
 
-    modes = ["graph", "persistent", "fused"] if args.mode == "auto" else [args.mode]
+    modes = ["graph", "persistent"] if args.mode == "auto" else [args.mode]
     best = None
     for m in modes:
         try:
@@ -407,12 +407,11 @@ def run_ours(args, ws, rank, local):
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0 / args.steps, ws)
 
     # per-kernel durations (CUDA events around every launch, on the batch stream).  The dominant
-    # kernel is the batched field step (448 B per site-update); in the fused mode it is the fused
-    # field step + push (plus 132 B per particle-step)
-    pmode = "fused" if mode == "fused" else "graph"
+    # kernel is the batched field step (448 B per site-update)
+    pmode = "graph"
     if in_graph_timing:
         B.set_graph_timing(False)
-    prof = B.profile(pmode)  # site and particle-step counts per launch (and fused-mode times)
+    prof = B.profile(pmode)  # site counts per launch (and eager launch times)
     if graph_t is not None:
         # durations of the field launches of the last timed run (event-record nodes)
         field_ms, n_launch, _ = graph_t
@@ -429,22 +428,21 @@ def run_ours(args, ws, rank, local):
     tps = ncu_traffic_per_site()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tps * prof["main_sites"] / prof["main_launches"] if tps else None),
-                "kernel": ("k_fused_batched<float>" if pmode == "fused"
-                           else f"k_field_step_tiles<{tile[0]},{tile[1]},{tile[2]}>"),
+                "kernel": f"k_field_step_tiles<{tile[0]},{tile[1]},{tile[2]}>",
                 "peak_kind": f"{peak_kind} HBM copy (burst)",
                 "algorithmic_bytes_per_launch": bytes_per_launch, "ms_per_launch": per_launch_ms,
                 "launch_timing": timing_src,
                 "share_of_step": share,
                 "other_kernels_ms_per_run": other_ms}
     # the whole step against the same peak, algorithmic bytes 448 per site-update and
-    # 132 per particle-step (the gather's field reads counted as fused, 0 B)
+    # 132 per particle-step (BASELINE's count: the gather's field reads not counted)
     whole = (BYTES_PER_SITE * su + BYTES_PER_PARTICLE * ps) / (ms / 1000.0) / 1e9
     roofline["whole_step"] = {"achieved": whole, "frac": whole / peak, "unit": "GB/s"}
     # the push's own roofline: its time per run is the step minus the field launches;
     # algorithmic bytes 132 per particle-step (particle state read + written), the field
     # reads of its gather listed beside them (35 groups of 32 B around the cell, or the
     # 18-group record of the record push, which the field launch also writes)
-    if pmode != "fused" and other_ms > 0:
+    if other_ms > 0:
         pa = BYTES_PER_PARTICLE * ps / (other_ms / 1000.0) / 1e9
         rec_push = B.push_variant == 2
         roofline["push"] = {"achieved": pa, "frac": pa / peak, "unit": "GB/s", "ms_per_run": other_ms,

@@ -89,7 +89,7 @@ typedef struct {
                                 each gathering the fields of the field step at the particle's
                                 current cell (at most 64; a batch with such events pushes them
                                 with a kernel of its own, not the tuned variants, and rejects
-                                GLASMA_BATCH_FUSED and GLASMA_BATCH_PERSISTENT) */
+                                GLASMA_BATCH_PERSISTENT) */
     int32_t interp;          /* field gather: 0 nearest grid point (the site at the lower-left corner of
                                 the particle's cell); 1 cloud in cell (the four sites around the
                                 particle, their fields carried to that site by the links, x before
@@ -359,9 +359,9 @@ typedef enum {
     GLASMA_BATCH_PERSISTENT = 1, /* one persistent cooperative kernel for the whole run: field and push
                                     phases separated by a bounded grid barrier */
     GLASMA_BATCH_PER_EVENT = 2,  /* plain loop: one event after the other, one launch per kernel */
-    GLASMA_BATCH_EAGER = 3,      /* the launches of GLASMA_BATCH_GRAPH issued without a graph */
-    GLASMA_BATCH_FUSED = 4       /* per step: bin the particles by tile, then one fused launch that pushes
-                                    each tile's particles from the tile's shared-memory fields; graph */
+    GLASMA_BATCH_EAGER = 3       /* the launches of GLASMA_BATCH_GRAPH issued without a graph */
+    /* (mode 4, a field step fused with the push of each tile's particles after binning them by
+       tile, was measured 4-5x slower than GLASMA_BATCH_GRAPH and is no longer offered) */
 } glasma_batch_mode;
 
 /* Workspace for n_events events: ev[i], pp[i] give event i (all with the same
@@ -394,12 +394,11 @@ glasma_status glasma_batch_diagnostics(glasma_batch* b, int32_t event, double ou
 int64_t glasma_batch_state_bytes(const glasma_batch* b);
 glasma_status glasma_batch_export_state(glasma_batch* b, void* host, int64_t bytes);
 glasma_status glasma_batch_import_state(glasma_batch* b, const void* host, int64_t bytes);
-/* One run issued eagerly with CUDA events around every launch (batch stream).
- * mode GLASMA_BATCH_FUSED: main = the fused field+push kernel (the binning step
- * runs after it, timed as other); any other mode: main = the batched field
- * kernel, other = the batched push.  Returns the total main-kernel time (ms),
- * its launches, the site-updates and particle-steps it performed, and the
- * total time of the other kernels.  Synchronises. */
+/* One run of the graph mode's launches issued eagerly with CUDA events around every launch
+ * (batch stream): main = the batched field kernel, other = the batched push (mode is
+ * ignored).  Returns the total main-kernel time (ms), its launches, the site-updates it
+ * performed, 0 particle-steps (the push is separate), and the total time of the pushes.
+ * Synchronises. */
 glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, double* main_ms, int64_t* main_launches,
                                    int64_t* main_sites, int64_t* main_particle_steps, double* other_ms);
 /* Pushes on a second stream (graph and eager modes), with separate != 0: the push of

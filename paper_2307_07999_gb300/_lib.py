@@ -15,7 +15,6 @@ GLASMA_BATCH_GRAPH = 0
 GLASMA_BATCH_PERSISTENT = 1
 GLASMA_BATCH_PER_EVENT = 2
 GLASMA_BATCH_EAGER = 3
-GLASMA_BATCH_FUSED = 4
 
 STATUS = {
     0: "GLASMA_OK",

@@ -319,7 +319,7 @@ class CPIC:
 class Batch:
     """Many events (each a GlasmaParams + CpicParams pair) advanced together."""
 
-    MODES = {"graph": 0, "persistent": 1, "per_event": 2, "eager": 3, "fused": 4}
+    MODES = {"graph": 0, "persistent": 1, "per_event": 2, "eager": 3}
 
     def __init__(self, events, particles, device="cuda", stream=None):
         # a created stream of our own: the legacy default stream cannot be captured into a graph
@@ -395,8 +395,8 @@ class Batch:
         return f.value, n.value, sp.value
 
     def profile(self, mode="graph"):
-        """CUDA-event timing of one eager run: the main kernel (batched field step, or the
-        fused field+push kernel for mode="fused") and the other kernels."""
+        """CUDA-event timing of one eager run of the graph mode's launches: the batched field
+        kernel (main) and the batched push (other)."""
         mm, om = C.c_double(), C.c_double()
         ml, ms, mp = C.c_int64(), C.c_int64(), C.c_int64()
         check(lib().glasma_batch_profile(self.handle, self.MODES[mode], C.byref(mm), C.byref(ml), C.byref(ms),

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libglasma.so")
 BUILD = os.path.join(HERE, "_build")
 UNITS = ["abi.cu", "batch.cu", "persistent.cu", "kernels_field.cu", "kernels_particles.cu", "kernels_ic.cu",
-         "noalloc.cu", "kernels_fused.cu", "mlp.cu", "kernels_corr.cu", "estimators.cu"]
+         "noalloc.cu", "mlp.cu", "kernels_corr.cu", "estimators.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

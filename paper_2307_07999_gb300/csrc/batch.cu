@@ -70,16 +70,8 @@ static Layout layout(const glasma_params* ev, const cpic_params* pp, int E, size
         npmax = std::max(npmax, (size_t)pp[e].n_particles);
     }
     const int prec = ev[0].precision;
-    size_t tiles = 0, parts = 0;
-    for (int e = 0; e < E; e++) {
-        const int tx = field_tile_x(prec), ty = field_tile_y(prec);
-        tiles += (size_t)((ev[e].n + tx - 1) / tx) * ((ev[e].n + ty - 1) / ty);
-        parts += (size_t)pp[e].n_particles;
-    }
     L.tables = align256((size_t)smax * E * step_args_size(prec)) + align256((size_t)smax * E * push_args_size(prec)) +
-               3 * align256((size_t)4 << 20) + align256((size_t)E * sizeof(BinArgs)) +
-               3 * align256(tiles * 4) + align256((tiles / 1024 + 2) * 4) + align256(parts * 4 + 4) +
-               align256(256 + ((size_t)smax + 2) * 8 + ((size_t)E + 1) * 8);
+               3 * align256((size_t)4 << 20) + align256(256 + ((size_t)smax + 2) * 8 + ((size_t)E + 1) * 8);
     const size_t ic = ic_scratch_bytes(nmax, fft_work);
     const size_t srt = align256(sort_scratch_ints(nmax * nmax) * 4);
     L.scratch = std::max(ic, srt) + 256;
@@ -195,24 +187,9 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
     b->gtiles_dev = A.take((size_t)4 << 20);
     b->pitems_dev = A.take((size_t)4 << 20);
     b->scratch = A.take(std::max(ic_scratch_bytes(nmax, b->fft_work), align256(sort_scratch_ints(nmax * nmax) * 4)));
-    {
-        size_t tiles = 0, parts = 0;
-        const int tx = field_tile_x(b->prec), ty = field_tile_y(b->prec);
-        for (const auto& x : b->ev) {
-            tiles += (size_t)((x.n + tx - 1) / tx) * ((x.n + ty - 1) / ty);
-            parts += (size_t)x.np;
-        }
-        b->n_tiles = (int)tiles;
-        b->bins_dev = A.take((size_t)E * sizeof(BinArgs));
-        b->bin_count = (int*)A.take(tiles * 4);
-        b->bin_fill = (int*)A.take(tiles * 4);
-        b->bin_start = (int*)A.take(tiles * 4);
-        b->bin_totals = (int*)A.take((tiles / 1024 + 2) * 4);
-        b->bin_perm = (int*)A.take(parts * 4 + 4);
-        b->pers_ctrl = A.take(256 + ((size_t)std::max(1, b->max_iter) + 2) * 8 + ((size_t)E + 1) * 8);
-    }
-    if (!b->step_args || !b->push_args || !b->tiles_dev || !b->gtiles_dev || !b->pitems_dev || !b->scratch || !b->bins_dev ||
-        !b->bin_count || !b->bin_fill || !b->bin_start || !b->bin_totals || !b->bin_perm || !b->pers_ctrl) {
+    b->pers_ctrl = A.take(256 + ((size_t)std::max(1, b->max_iter) + 2) * 8 + ((size_t)E + 1) * 8);
+    if (!b->step_args || !b->push_args || !b->tiles_dev || !b->gtiles_dev || !b->pitems_dev || !b->scratch ||
+        !b->pers_ctrl) {
         delete b;
         return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
     }
@@ -262,16 +239,6 @@ static glasma_status build_tables(glasma_batch* b) {
     }
     if (tiles.size() * sizeof(TileItemH) > ((size_t)4 << 20) || pits.size() * sizeof(PushItemH) > ((size_t)4 << 20))
         return bfail(GLASMA_ERR_NOSPACE, "item tables exceed their reserve");
-    if (fused_tile_x(b->prec) != tx || fused_tile_y(b->prec) != ty)
-        return bfail(GLASMA_ERR_INVALID, "fused and field tiles differ");
-    {
-        std::vector<BinArgs> ba(E);
-        for (int i = 0; i < E; i++) {
-            const BatchEvent& x = b->ev[i];
-            ba[i] = BinArgs{x.P.cell, x.np, x.n, (x.n + tx - 1) / tx, tx, ty, b->tiles_upto[i]};
-        }
-        BCK(cudaMemcpyAsync(b->bins_dev, ba.data(), ba.size() * sizeof(BinArgs), cudaMemcpyHostToDevice, b->st));
-    }
     BCK(cudaMemcpyAsync(b->tiles_dev, tiles.data(), tiles.size() * sizeof(TileItemH), cudaMemcpyHostToDevice, b->st));
     BCK(prepare_field_variants(b->prec));
     BCK(prepare_push_staged());
@@ -314,7 +281,6 @@ static glasma_status build_tables(glasma_batch* b) {
     }
     // first launch outside any stream capture sets the kernels' shared-memory attribute
     BCK(launch_field_step_batched(b->prec, nullptr, nullptr, 0, b->st));
-    BCK(launch_fused_batched(b->prec, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, b->st));
     {
         // persistent-kernel control block: 256 B of counters, then work counters [K + 1],
         // active [K], tiles_upto [E + 1], pitems_upto [E + 1]
@@ -387,24 +353,6 @@ static cudaError_t enqueue_restore(glasma_batch* b) {
 // the graph and eager modes run the record push (and the field kernels that write its
 // records) when it is the chosen push kernel and no event needs the sub-stepped push
 static bool batch_records(const glasma_batch* b) { return !b->any_sub && b->pvar == PUSH_VARIANT_RECORD; }
-
-static cudaError_t enqueue_fused(glasma_batch* b) {
-    cudaError_t e = enqueue_restore(b);
-    if (e != cudaSuccess) return e;
-    const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
-    for (int k = 0; k < b->max_iter; k++) {
-        const int act = b->active[k];
-        if (act == 0) break;
-        e = launch_rebin(b->bins_dev, b->pitems_dev, b->pitems_upto[act], b->tiles_upto[act], b->bin_count,
-                         b->bin_fill, b->bin_start, b->bin_totals, b->bin_perm, b->st);
-        if (e != cudaSuccess) return e;
-        e = launch_fused_batched(b->prec, (char*)b->step_args + (size_t)k * b->E * sa,
-                                 (char*)b->push_args + (size_t)k * b->E * pa, b->tiles_dev, b->tiles_upto[act],
-                                 b->bin_start, b->bin_count, b->bin_perm, b->st);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
 
 static cudaError_t enqueue_batched(glasma_batch* b) {
     cudaError_t e = enqueue_restore(b);
@@ -488,15 +436,15 @@ static cudaError_t enqueue_per_event(glasma_batch* b) {
     return cudaSuccess;
 }
 
-static glasma_status run_graph(glasma_batch* b, bool fused) {
+static glasma_status run_graph(glasma_batch* b) {
     if (b->st == nullptr || b->st == cudaStreamLegacy || b->st == cudaStreamPerThread)
         return bfail(GLASMA_ERR_INVALID, "graph mode needs a created stream (the default stream cannot be captured)");
-    cudaGraphExec_t& exec = fused ? b->exec : b->exec_unfused;
-    bool& ready = fused ? b->graph_ready : b->graph_unfused_ready;
+    cudaGraphExec_t& exec = b->exec;
+    bool& ready = b->graph_ready;
     if (!ready) {
         cudaGraph_t g = nullptr;
         BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = fused ? enqueue_fused(b) : enqueue_batched(b);
+        cudaError_t e = enqueue_batched(b);
         cudaError_t e2 = cudaStreamEndCapture(b->st, &g);  // always end the capture
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -520,11 +468,7 @@ extern "C" glasma_status glasma_batch_run(glasma_batch* b, int32_t mode) {
         case GLASMA_BATCH_PERSISTENT:
             if (b->any_sub) return bfail(GLASMA_ERR_INVALID, "the persistent mode does not take sub-stepped or cloud-in-cell particles");
             return batch_run_persistent(b);
-        case GLASMA_BATCH_GRAPH: return run_graph(b, false);
-        case GLASMA_BATCH_FUSED:
-            // a fused tile holds the fields of its own cells only; sub-steps may leave them
-            if (b->any_sub) return bfail(GLASMA_ERR_INVALID, "the fused mode does not take sub-stepped or cloud-in-cell particles");
-            return run_graph(b, true);
+        case GLASMA_BATCH_GRAPH: return run_graph(b);
         default: return bfail(GLASMA_ERR_INVALID, "unknown mode");
     }
 }
@@ -616,45 +560,32 @@ extern "C" glasma_status glasma_batch_import_state(glasma_batch* b, const void* 
     return GLASMA_OK;
 }
 
-// one eager run with CUDA events around every launch (on the batch stream)
-// one eager run with CUDA events around every launch (on the batch stream).  mode
-// GLASMA_BATCH_FUSED: the fused kernel is the main kernel and the binning kernels the
-// others; any other mode: the batched field kernel is the main kernel and the push the other.
+// one eager run of the graph mode's launches with CUDA events around every launch (on the
+// batch stream): the batched field kernel is the main kernel, the push the other
 extern "C" glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, double* main_ms, int64_t* main_launches,
                                               int64_t* main_sites, int64_t* main_particle_steps, double* other_ms) {
     if (!b || !b->initialised) return bfail(GLASMA_ERR_INVALID, "batch not initialised");
-    const bool fused = mode == GLASMA_BATCH_FUSED;
-    if (fused && b->any_sub) return bfail(GLASMA_ERR_INVALID, "the fused mode does not take sub-stepped or cloud-in-cell particles");
+    (void)mode;
     BCK(enqueue_restore(b));
     const size_t sa = step_args_size(b->prec), pa = push_args_size(b->prec);
     const int K = b->max_iter;
     std::vector<cudaEvent_t> ev(4 * (size_t)K);
     for (auto& e : ev) BCK(cudaEventCreate(&e));
-    int64_t sites = 0, parts = 0;
+    int64_t sites = 0;
     int used = 0;
     for (int k = 0; k < K; k++) {
         const int act = b->active[k];
         if (act == 0) break;
-        for (int i = 0; i < act; i++) {
-            sites += (int64_t)b->ev[i].ns;
-            if (k + 1 >= b->ev[i].n_form) parts += b->ev[i].np;
-        }
+        for (int i = 0; i < act; i++) sites += (int64_t)b->ev[i].ns;
         const void* sargs = (char*)b->step_args + (size_t)k * b->E * sa;
         const void* pargs = (char*)b->push_args + (size_t)k * b->E * pa;
         BCK(cudaEventRecord(ev[4 * k + 0], b->st));
-        if (fused)
-            BCK(launch_fused_batched(b->prec, sargs, pargs, b->tiles_dev, b->tiles_upto[act], b->bin_start,
-                                     b->bin_count, b->bin_perm, b->st));
-        else
-            BCK(launch_field_step_variant(b->prec, b->fvar, sargs, b->gtiles_dev, b->gtiles_upto[act], b->st,
-                                          batch_records(b)));
+        BCK(launch_field_step_variant(b->prec, b->fvar, sargs, b->gtiles_dev, b->gtiles_upto[act], b->st,
+                                      batch_records(b)));
         BCK(cudaEventRecord(ev[4 * k + 1], b->st));
         BCK(cudaEventRecord(ev[4 * k + 2], b->st));
-        if (fused)
-            BCK(launch_rebin(b->bins_dev, b->pitems_dev, b->pitems_upto[act], b->tiles_upto[act], b->bin_count,
-                             b->bin_fill, b->bin_start, b->bin_totals, b->bin_perm, b->st));
-        else
-            BCK(launch_push_batched(b->prec, b->any_sub ? PUSH_VARIANT_SUB : b->pvar, pargs, b->pitems_dev, b->pitems_upto[act], b->st));
+        BCK(launch_push_batched(b->prec, b->any_sub ? PUSH_VARIANT_SUB : b->pvar, pargs, b->pitems_dev,
+                                b->pitems_upto[act], b->st));
         BCK(cudaEventRecord(ev[4 * k + 3], b->st));
         used = k + 1;
     }
@@ -671,7 +602,7 @@ extern "C" glasma_status glasma_batch_profile(glasma_batch* b, int32_t mode, dou
     if (main_ms) *main_ms = mm;
     if (main_launches) *main_launches = used;
     if (main_sites) *main_sites = sites;
-    if (main_particle_steps) *main_particle_steps = fused ? parts : 0;
+    if (main_particle_steps) *main_particle_steps = 0;
     if (other_ms) *other_ms = om;
     return GLASMA_OK;
 }
@@ -694,9 +625,9 @@ extern "C" glasma_status glasma_batch_set_variant(glasma_batch* b, int32_t v) {
     if (v < 0 || v >= field_variants(b->prec)) return bfail(GLASMA_ERR_INVALID, "no such tile variant");
     if (v == b->fvar) return GLASMA_OK;
     b->fvar = v;
-    if (b->graph_unfused_ready) {
-        cudaGraphExecDestroy(b->exec_unfused);
-        b->graph_unfused_ready = false;
+    if (b->graph_ready) {
+        cudaGraphExecDestroy(b->exec);
+        b->graph_ready = false;
     }
     return build_gtiles(b);
 }
@@ -709,9 +640,9 @@ extern "C" glasma_status glasma_batch_set_push_stream(glasma_batch* b, int32_t s
         for (auto& e : b->sev) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     b->two_streams = separate != 0;
-    if (b->graph_unfused_ready) {  // captured again with (or without) the second stream
-        cudaGraphExecDestroy(b->exec_unfused);
-        b->graph_unfused_ready = false;
+    if (b->graph_ready) {  // captured again with (or without) the second stream
+        cudaGraphExecDestroy(b->exec);
+        b->graph_ready = false;
     }
     return GLASMA_OK;
 }
@@ -723,9 +654,9 @@ extern "C" glasma_status glasma_batch_set_graph_timing(glasma_batch* b, int32_t 
         for (auto& e : b->tev) BCK(cudaEventCreate(&e));
     }
     b->timing = on != 0;
-    if (b->graph_unfused_ready) {  // captured again with (or without) the event nodes
-        cudaGraphExecDestroy(b->exec_unfused);
-        b->graph_unfused_ready = false;
+    if (b->graph_ready) {  // captured again with (or without) the event nodes
+        cudaGraphExecDestroy(b->exec);
+        b->graph_ready = false;
     }
     return GLASMA_OK;
 }
@@ -754,9 +685,9 @@ extern "C" glasma_status glasma_batch_set_push_variant(glasma_batch* b, int32_t 
     if (v < 0 || v >= push_variants()) return bfail(GLASMA_ERR_INVALID, "no such push variant");
     if (v == b->pvar) return GLASMA_OK;
     b->pvar = v;
-    if (b->graph_unfused_ready) {
-        cudaGraphExecDestroy(b->exec_unfused);
-        b->graph_unfused_ready = false;
+    if (b->graph_ready) {
+        cudaGraphExecDestroy(b->exec);
+        b->graph_ready = false;
     }
     return GLASMA_OK;
 }
@@ -864,8 +795,6 @@ extern "C" int64_t glasma_batch_launches(const glasma_batch* b, int32_t mode) {
         for (const auto& x : b->ev) L += (x.n_steps - 1) + std::max(0, x.n_steps - x.n_form) * (x.np > 0);
     } else if (mode == GLASMA_BATCH_PERSISTENT) {
         L = 1;
-    } else if (mode == GLASMA_BATCH_FUSED) {  // count, 3 scan passes, scatter, fused kernel
-        for (int k = 0; k < b->max_iter; k++) L += b->active[k] ? 6 : 0;
     } else {
         for (int k = 0; k < b->max_iter; k++) L += b->active[k] ? 2 : 0;
     }
@@ -875,7 +804,6 @@ extern "C" int64_t glasma_batch_launches(const glasma_batch* b, int32_t mode) {
 extern "C" void glasma_batch_destroy(glasma_batch* b) {
     if (!b) return;
     if (b->graph_ready) cudaGraphExecDestroy(b->exec);
-    if (b->graph_unfused_ready) cudaGraphExecDestroy(b->exec_unfused);
     for (auto& e : b->tev)
         if (e) cudaEventDestroy(e);
     for (auto& e : b->sev)

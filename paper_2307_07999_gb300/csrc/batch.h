@@ -38,7 +38,7 @@ struct glasma_batch {
     std::vector<int> pos;         // caller's event index -> position in ev
     void* step_args = nullptr;    // [max_iter][E] StepArgs
     void* push_args = nullptr;    // [max_iter][E] PushArgs
-    void* tiles_dev = nullptr;    // TileItem list, grouped by event (fused and persistent paths)
+    void* tiles_dev = nullptr;    // TileItem list, grouped by event (persistent path)
     void* gtiles_dev = nullptr;   // TileItem list of the chosen field variant (graph and eager paths)
     int fvar = 0;                 // FP32 field tile variant of the graph and eager paths
     int pvar = 0;                 // batched push kernel of the graph and eager paths
@@ -55,16 +55,8 @@ struct glasma_batch {
     void* pitems_dev = nullptr;   // PushItem list, grouped by event
     void* scratch = nullptr;      // initial-condition / sort scratch
     std::vector<int> tiles_upto, gtiles_upto, pitems_upto, active;
-    // tile bins of the fused path
-    void* bins_dev = nullptr;     // BinArgs per event
-    int* bin_count = nullptr;
-    int* bin_fill = nullptr;
-    int* bin_start = nullptr;
-    int* bin_totals = nullptr;
-    int* bin_perm = nullptr;
-    int n_tiles = 0;
-    bool initialised = false, graph_ready = false, graph_unfused_ready = false;
-    cudaGraphExec_t exec = nullptr, exec_unfused = nullptr;
+    bool initialised = false, graph_ready = false;
+    cudaGraphExec_t exec = nullptr;
     // persistent mode
     void* pers_ctrl = nullptr;    // barrier counters + error word + per-iteration prefixes (device)
     int pers_blocks = 0;

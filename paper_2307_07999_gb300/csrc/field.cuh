@@ -201,23 +201,6 @@ template <class T> DEV void store_alg(T* __restrict__ f, size_t ns, int plane0, 
 }
 DEV int wrapi(int v, int n) { v %= n; return v < 0 ? v + n : v; }
 
-// SoA tile staging (one plane per entry): used by the fused field + push kernel
-template <class T, int HS> DEV M3<T> sm_link(const T* sU, int d, int h) {
-    M3<T> U;
-    const T* b = sU + d * 18 * HS + h;
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) U.m[r][c] = mk(b[(2 * (3 * r + c)) * HS], b[(2 * (3 * r + c) + 1) * HS]);
-    return U;
-}
-template <class T, int S> DEV Al<T> sm_alg(const T* s, int h) {
-    Al<T> x;
-#pragma unroll
-    for (int a = 0; a < 8; a++) x.a[a] = s[a * S + h];
-    return x;
-}
-
 // Record tile staging of the field step: per site, a link as 20 reals (its 9 complex
 // entries and two of padding) and an algebra field as 12 reals (8 and four of padding),
 // moved as 16-byte vectors.  Record strides of 20 and 12 words put the eight threads

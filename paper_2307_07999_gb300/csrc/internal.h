@@ -122,14 +122,6 @@ cudaError_t launch_push_batched(int prec, int variant, const void* args_dev, con
                                 cudaStream_t st);
 struct PushItemH { int ev, j0; };
 struct TileItemH { int ev, x0, y0; };
-// fused field step + push (one CTA per tile; particles listed per tile by perm/start/count)
-struct BinArgs { const int* cell; int np, n, ntx, tx, ty, tile_base; };
-int fused_tile_x(int prec);
-int fused_tile_y(int prec);
-cudaError_t launch_fused_batched(int prec, const void* step_args, const void* push_args, const void* items, int n_items,
-                                 const int* start, const int* count, const int* perm, cudaStream_t st);
-cudaError_t launch_rebin(const void* bins, const void* pitems, int n_pitems, int n_tiles, int* count, int* fill,
-                         int* start, int* totals, int* perm, cudaStream_t st);
 cudaError_t launch_sort(int prec, const PartHost& a, const PartHost& b, int np, int ncell, int* count,
                         int* start, int* totals, cudaStream_t st);
 size_t sort_scratch_ints(int ncell);

@@ -65,11 +65,11 @@ def fp64_batch():
 def test_batch_modes_agree(fp64_batch):
     B, evs, pps = fp64_batch
     tabs = {}
-    for mode in ("graph", "eager", "per_event", "fused", "persistent", "graph"):
+    for mode in ("graph", "eager", "per_event", "persistent", "graph"):
         B.run(mode)
         tabs[mode] = [B.broadening(e) for e in range(len(evs))]
     errs = {m: max(rel_err(tabs[m][e][:, 1:4], tabs["graph"][e][:, 1:4]) for e in range(len(evs)))
-            for m in ("eager", "per_event", "fused", "persistent")}
+            for m in ("eager", "per_event", "persistent")}
     print("mode errors vs graph:", errs)
     for m, v in errs.items():
         assert v < 1e-13, (m, v)

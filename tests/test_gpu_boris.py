@@ -144,10 +144,10 @@ def test_boris_batch_modes_agree():
     B = G.Batch(evs, pps)
     assert B.init() == 0
     tabs = {}
-    for mode in ("graph", "eager", "per_event", "fused", "persistent"):
+    for mode in ("graph", "eager", "per_event", "persistent"):
         B.run(mode)
         tabs[mode] = [B.broadening(e) for e in range(len(evs))]
-    for m in ("eager", "per_event", "fused", "persistent"):
+    for m in ("eager", "per_event", "persistent"):
         for e in range(len(evs)):
             assert rel_err(tabs[m][e][:, 1:4], tabs["graph"][e][:, 1:4]) < 1e-13, (m, e)
     for e, (gp, pp) in enumerate(zip(evs, pps)):

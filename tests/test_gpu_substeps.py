@@ -62,7 +62,7 @@ def test_substeps_and_cic_fp32(s, interp):
 def test_substeps_batch():
     """A three-event FP64 batch with special ensembles (explicit, s = 3; Boris, s = 2;
     Boris with the cloud-in-cell gather): graph, eager and per-event modes agree to 1e-13
-    and with the oracle to 1e-10; the persistent and fused modes refuse it."""
+    and with the oracle to 1e-10; the persistent mode refuses it."""
     spec = [(24, 2.4, 1.8, 0, 3, 0), (32, 2.6, 2.0, 1, 2, 0), (28, 2.5, 1.9, 1, 1, 1)]
     evs, pps = [], []
     for e, (n, L, g2mu, integ, s, interp) in enumerate(spec):
@@ -83,9 +83,8 @@ def test_substeps_batch():
     for m in ("eager", "per_event"):
         for e in range(len(evs)):
             assert rel_err(tabs[m][e][:, 1:4], tabs["graph"][e][:, 1:4]) < 1e-13, (m, e)
-    for mode in ("persistent", "fused"):
-        with pytest.raises(G.GlasmaError):
-            B.run(mode)
+    with pytest.raises(G.GlasmaError):
+        B.run("persistent")
     for e, (gp, pp) in enumerate(zip(evs, pps)):
         n = gp.n
         a_fm = gp.L_fm / n
