@@ -123,3 +123,26 @@ def test_record_push_with_empty_and_crowded_events():
     assert rel_err(B.broadening(0)[:, 1:4], want[:, 1:4]) < 1e-10
     t1 = B.broadening(1)
     assert np.all(t1[:, 1:4] == 0)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_record_push_on_the_smallest_lattices(prec, tol):
+    """Lattices of 2 and 3 sites per side: the neighbour cells +x and -x (and +y, -y) of a
+    cell coincide or wrap at once, so one site writes several neighbour pieces of the same
+    record; a 5^2 lattice ragged against every tile shape beside them."""
+    evs, pps = [], []
+    for e, (n, L) in enumerate([(2, 0.2), (3, 0.3), (5, 0.5)]):  # a = 0.1 fm: g^2 mu a ~ 1
+        s = W.event_seed(9, 40 + e)
+        gp = W.glasma_params(n, L, 2.0, s, prec, tau_end_fm=0.08, reunit_every=(0 if prec == 0 else 16))
+        gp.newton_tol = 1e-14
+        evs.append(gp)
+        pps.append(W.charm_params(50, s, mass=1.5, p_max=3.0, tau_form=0.01))
+    B = G.Batch(evs, pps)
+    assert B.init() == 0
+    B.set_push_variant(RECORD)
+    B.run("graph")
+    for e in range(len(evs)):
+        want, P, st = oracle_event(evs[e], pps[e], 1e-14)
+        got = B.broadening(e)
+        assert got.shape == want.shape
+        assert rel_err(got[:, 1:4], want[:, 1:4]) < tol, e
