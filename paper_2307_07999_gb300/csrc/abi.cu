@@ -389,7 +389,7 @@ extern "C" glasma_status cpic_get_particles(cpic_ctx* c, double* x, double* y, d
 static glasma_status push_ensemble(cpic_ctx* c, int n, const void* fo) {
     glasma_ctx* g = c->g;
     if (n < c->first_step || c->np == 0) return GLASMA_OK;
-    PushHost a;
+    PushHost a{};
     a.fo = fo;
     a.fn = g->buf[g->cur];
     a.n = g->n;

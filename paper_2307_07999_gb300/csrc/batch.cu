@@ -64,6 +64,7 @@ static Layout layout(const glasma_params* ev, const cpic_params* pp, int E, size
         const size_t ns = (size_t)ev[e].n * ev[e].n;
         L.fields += align256(ns * record_bytes(ev[e].precision)) + align256(ns * 4);
         L.parts += 2 * part_bytes(pp[e].n_particles, ev[e].precision);
+        L.parts += 6 * align256((size_t)pp[e].n_particles * (ev[e].precision ? 4 : 8)) + 256;
         L.accs += align256(((size_t)steps_of(ev[e]) + 2) * 4 * 8);
         nmax = std::max(nmax, ev[e].n);
         smax = std::max(smax, steps_of(ev[e]));
@@ -171,10 +172,11 @@ extern "C" glasma_status glasma_batch_create(const glasma_params* ev, const cpic
         x.part_base = A.take(pb);
         x.part_init = A.take(pb);
         x.P = part_layout(x.part_base, x.np, b->prec);
+        x.frc = A.take(6 * x.P.pstride * (b->prec ? 4 : 8));
         x.acc_rows = x.n_steps + 2;
         x.acc = (double*)A.take((size_t)x.acc_rows * 4 * 8);
         x.mon = (double*)A.take(256);
-        if (!x.buf[0] || !x.buf[1] || !x.buf[2] || !x.init_buf || !x.rec || !x.occ || !x.part_base || !x.part_init || !x.acc || !x.mon) {
+        if (!x.buf[0] || !x.buf[1] || !x.buf[2] || !x.init_buf || !x.rec || !x.occ || !x.frc || !x.part_base || !x.part_init || !x.acc || !x.mon) {
             delete b;
             return bfail(GLASMA_ERR_NOSPACE, "workspace too small");
         }
@@ -267,7 +269,7 @@ static glasma_status build_tables(glasma_batch* b) {
             st.occ = x.occ;
             st.all_rec = s == x.n_form ? 1 : 0;
             pack_step_args(b->prec, st, hs.data() + ((size_t)k * E + i) * sa);
-            PushHost ph;
+            PushHost ph{};
             ph.fo = src; ph.fn = dst; ph.n = x.n; ph.np = x.np;
             push_coeffs(ph, s, x.dtau, 1, x.pp.integrator, x.pp.substeps, x.pp.interp);
             ph.mass = x.mass;
@@ -275,6 +277,7 @@ static glasma_status build_tables(glasma_batch* b) {
             ph.rec = x.rec;
             ph.occ = x.occ;
             ph.epoch_next = s + 1;
+            ph.frc = x.frc;
             pack_push_args(b->prec, ph, x.P, hp.data() + ((size_t)k * E + i) * pa);
         }
         b->active[k] = act;
@@ -423,7 +426,7 @@ static cudaError_t enqueue_per_event(glasma_batch* b) {
             e = launch_field_step(b->prec, st, b->st);
             if (e != cudaSuccess) return e;
             if (s >= x.n_form && x.np > 0) {
-                PushHost ph;
+                PushHost ph{};
                 ph.fo = x.buf[k % 3]; ph.fn = x.buf[(k + 1) % 3]; ph.n = x.n; ph.np = x.np;
                 push_coeffs(ph, s, x.dtau, 1, x.pp.integrator, x.pp.substeps, x.pp.interp);
                 ph.mass = x.mass;

@@ -19,6 +19,7 @@ struct BatchEvent {
     void* init_buf;
     void* rec;           // gather records of the record push, REC_STRIDE groups per cell
     int* occ;            // occupancy stamps of the record push, one per cell
+    void* frc;           // contracted fields of the split push, 6 particle planes
     void* part_base;
     void* part_init;
     size_t part_bytes;

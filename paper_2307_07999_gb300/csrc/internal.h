@@ -85,6 +85,7 @@ struct PushHost {
     const void* rec;     // record push: the gather records of this step
     int* occ;            // record push: occupancy stamps, set to epoch_next at the new cells
     int epoch_next;
+    void* frc;           // split push: 6 planes of np reals (particle plane stride) of contracted fields
 };
 // the step-dependent coefficients of the push from tau_n = step * dtau to tau_{n+1}
 inline void push_coeffs(PushHost& a, int step, double dtau, int expanding, int integrator, int substeps,
@@ -113,6 +114,9 @@ int push_variants();
 constexpr int PUSH_VARIANT_SUB = 99;
 // the record push (tuned variant 2): the field launches of the same run write gather records
 constexpr int PUSH_VARIANT_RECORD = 2;
+// the split push (tuned variant 3): a force kernel (gather, contracted fields stored per
+// particle) and a move kernel
+constexpr int PUSH_VARIANT_SPLIT = 3;
 // lattice-correlator estimators (kernels_corr.cu): state = I [24][ns], J [24][ns], W [18][ns]
 size_t corr_state_bytes(int prec, int n);
 cudaError_t launch_corr_reset(int prec, void* state, int n, cudaStream_t st);

@@ -42,6 +42,7 @@ template <class T> static PushArgs<T> push_args(const PushHost& a, const PartHos
     A.boris = a.boris; A.dec0 = (T)a.dec0; A.dec1 = (T)a.dec1;
     A.nsub = a.nsub; A.hsub = (T)a.hsub; A.tau0 = (T)a.tau0; A.interp = a.interp;
     A.rec = (const T*)a.rec; A.occ = a.occ; A.epoch_next = a.epoch_next;
+    A.frc = (T*)a.frc;
     return A;
 }
 size_t record_bytes(int prec) { return (size_t)REC_STRIDE * 8 * (prec ? 4 : 8); }
@@ -54,7 +55,15 @@ void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out) {
 //   0: 128-thread blocks, 3 per SM, fields read through L1
 //   1: 32-thread blocks, 6 per SM, each particle's fields staged in shared memory first
 //   2: the fields from the gather records the field launch wrote (PUSH_VARIANT_RECORD)
-int push_variants() { return 3; }
+//   3: split into a force kernel and a move kernel (PUSH_VARIANT_SPLIT)
+int push_variants() { return 4; }
+#ifndef GLASMA_SPLIT_FORCE_MINB
+#define GLASMA_SPLIT_FORCE_MINB 4
+#endif
+#ifndef GLASMA_SPLIT_MOVE_MINB
+#define GLASMA_SPLIT_MOVE_MINB 4
+#endif
+constexpr int SPLIT_FORCE_MINB = GLASMA_SPLIT_FORCE_MINB, SPLIT_MOVE_MINB = GLASMA_SPLIT_MOVE_MINB;
 // shared-memory limit of the staged push (call outside stream capture)
 cudaError_t prepare_push_staged() {
     static bool done = false;
@@ -77,6 +86,10 @@ static cudaError_t push_batched_impl(int v, const void* args, const void* items,
         k_push_batched<T, 128, 3, true><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
     else if (v == PUSH_VARIANT_RECORD)
         k_push_record<T, 128, 4><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
+    else if (v == PUSH_VARIANT_SPLIT) {
+        k_push_force<T, 128, SPLIT_FORCE_MINB><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
+        k_push_move<T, 128, SPLIT_MOVE_MINB><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
+    }
     else
         k_push_batched<T, 128, 3><<<(unsigned)n_items * 2, 128, 0, st>>>(a, it);
     return cudaGetLastError();

@@ -42,6 +42,9 @@ template <class T> struct PushArgs {
     const T* rec;
     int* occ;
     int epoch_next;
+    // split push (ForceSrc): the Q-contracted fields of every particle, written by the force
+    // kernel: 6 planes of np reals (plane stride P.qs) {Q.E_x, Q.E_y, Q.E_z, Q.B_x, Q.B_y, Q.B_z}
+    T* frc;
 };
 
 template <class T> DEV M3<T> dagger(const M3<T>& A) {
@@ -81,7 +84,7 @@ template <> DEV double clamp_below_one<double>(double v) { return fmin(v, 0.9999
 //                                            the link site -> site + i, pi likewise at c
 // Global source of the unfused push: the two field buffers of step n.
 template <class T, bool CG = false> struct GlobalSrc {
-    static constexpr bool kRecord = false;
+    static constexpr bool kRecord = false, kForce = false;
     const T* fo;
     const T* fn;
     int n;
@@ -155,7 +158,7 @@ __host__ __device__ constexpr int stage_slot(int dx, int dy, int g, int b) {
     return -1;
 }
 template <class T> struct StagedSrc {
-    static constexpr bool kRecord = false;
+    static constexpr bool kRecord = false, kForce = false;
     static constexpr int STRIDE = STAGE_SLOTS * 8 + (sizeof(T) == 4 ? 4 : 2);  // bank-spread record stride
     const T* rec;  // this thread's record
     struct View {
@@ -254,7 +257,7 @@ DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
 // there instead: Q.(U^dag X U) = (U Q U^dag).X.  Links for cell crossings and phi at
 // the cell come from the field buffer and the record.
 template <class T> struct RecordSrc {
-    static constexpr bool kRecord = true;
+    static constexpr bool kRecord = true, kForce = false;
     const T* rec;
     GlobalSrc<T> g;
     struct View {
@@ -300,6 +303,13 @@ template <class T> struct RecordSrc {
     DEV View view(int cx, int cy) const {
         return View{rec + ((size_t)cx + (size_t)g.n * cy) * REC_STRIDE * 8, g.view(cx, cy)};
     }
+};
+
+// Force source (second kernel of the split push): the Q-contracted fields of the particle,
+// gathered by the force kernel and stored per particle (PushArgs::frc); phi at the cell and
+// the links of cell crossings come from the field buffer as in the unfused push.
+template <class T> struct ForceSrc : GlobalSrc<T> {
+    static constexpr bool kRecord = false, kForce = true;
 };
 
 // Cloud-in-cell gather: the Q-contracted fields of the four sites around the particle
@@ -412,7 +422,13 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, T& sx, T& sy, T& 
         }
         T qE[3], qB[3];
         const auto C = F.view(cx, cy);
-        if constexpr (S::kRecord)
+        if constexpr (S::kForce) {
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                qE[i] = A.frc[(size_t)i * P.qs + j];
+                qB[i] = A.frc[(size_t)(3 + i) * P.qs + j];
+            }
+        } else if constexpr (S::kRecord)
             C.gather(A.te, q, qE, qB);
         else if (SUB && A.interp)
             gather_qf_cic(F, n, cx, cy, ox, oy, A.te, q, qE, qB);
@@ -631,6 +647,52 @@ __global__ void __launch_bounds__(NT, MINB) k_push_record(const PushArgs<T>* __r
     if (j < A.np) {
         const RecordSrc<T> F{A.rec, GlobalSrc<T>{A.fo, A.fn, A.n, (size_t)A.n * A.n}};
         push_one_src<T, RecordSrc<T>>(A, F, j, sx, sy, sz, sc);
+    }
+    block_acc4(sx, sy, sz, sc, A.acc);
+}
+
+// Split push: the force kernel gathers the fields of each particle's cell and stores their
+// Q-contractions (6 reals per particle); the move kernel then kicks, drifts and rotates the
+// particle from them.  The gather, the part that waits on scattered loads, runs in a kernel
+// with fewer registers and so more resident warps than the whole push.
+template <class T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_push_force(const PushArgs<T>* __restrict__ args,
+                                                         const PushItem* __restrict__ items) {
+    static_assert(256 % NT == 0 && NT % 32 == 0, "push block");
+    constexpr int SUB = 256 / NT;
+    const PushItem it = items[blockIdx.x / SUB];
+    const PushArgs<T>& A = args[it.ev];
+    if (A.acc == nullptr) return;
+    const int j = it.j0 + (int)(blockIdx.x % SUB) * NT + threadIdx.x;
+    if (j >= A.np) return;
+    const PartSoA<T>& P = A.P;
+    const int n = A.n;
+    const int cell = P.cell[j];
+    Al<T> q;
+#pragma unroll
+    for (int a = 0; a < 8; a++) q.a[a] = P.Q[(size_t)a * P.qs + j];
+    const GlobalSrc<T> F{A.fo, A.fn, n, (size_t)n * n};
+    T qE[3], qB[3];
+    gather_qf_view(F.view(cell % n, cell / n), A.te, q, qE, qB);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        A.frc[(size_t)i * P.qs + j] = qE[i];
+        A.frc[(size_t)(3 + i) * P.qs + j] = qB[i];
+    }
+}
+template <class T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_push_move(const PushArgs<T>* __restrict__ args,
+                                                        const PushItem* __restrict__ items) {
+    static_assert(256 % NT == 0 && NT % 32 == 0, "push block");
+    constexpr int SUB = 256 / NT;
+    const PushItem it = items[blockIdx.x / SUB];
+    const PushArgs<T> A = args[it.ev];
+    if (A.acc == nullptr) return;
+    const int j = it.j0 + (int)(blockIdx.x % SUB) * NT + threadIdx.x;
+    T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
+    if (j < A.np) {
+        const ForceSrc<T> F{{A.fo, A.fn, A.n, (size_t)A.n * A.n}};
+        push_one_src<T, ForceSrc<T>>(A, F, j, sx, sy, sz, sc);
     }
     block_acc4(sx, sy, sz, sc, A.acc);
 }

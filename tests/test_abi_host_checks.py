@@ -70,7 +70,7 @@ def test_compiled_variants_are_reported(lib):
         shapes.add((a.value, b.value, c.value))
     assert len(shapes) == nv
     assert lib.glasma_field_tile_shape(L.GLASMA_FP32, nv, C.byref(a), C.byref(b), C.byref(c)) == INVALID
-    assert lib.glasma_push_variants() == 3  # fields through L1, staged, record
+    assert lib.glasma_push_variants() == 4  # fields through L1, staged, record, split
 
 
 def test_network_and_monitor_entry_points_check_their_buffers(lib):

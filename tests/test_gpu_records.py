@@ -1,4 +1,5 @@
-"""The record push (batched push variant 2): the batched field launch writes, for every
+"""The record push (batched push variant 2; the split push, variant 3, is checked here too):
+the batched field launch writes, for every
 cell a particle occupies, the pieces of the site-centred fields it computes anyway
 (time-centred E and pi, phi, the phi transports, three clover leaves, and the neighbour
 pieces of the cells +x, +y), and the push reads that one record instead of gathering 35
@@ -17,6 +18,7 @@ G = pytest.importorskip("paper_2307_07999_gb300")
 W = pytest.importorskip("paper_2307_07999_gb300.workloads")
 
 RECORD = 2
+SPLIT = 3   # the split push: force kernel (gather) + move kernel
 
 
 def oracle_event_int(gp, pp, tol, integrator):
@@ -42,15 +44,16 @@ def oracle_event_int(gp, pp, tol, integrator):
     return np.array(rows), P, st
 
 
+@pytest.mark.parametrize("pv", [RECORD, SPLIT])
 @pytest.mark.parametrize("integrator", [0, 1])
-def test_record_push_fp64_matches_oracle(integrator):
+def test_record_push_fp64_matches_oracle(integrator, pv):
     evs, pps = small_events(0)
     for pp in pps:
         pp.integrator = integrator
     B = G.Batch(evs, pps)
     assert B.init() == 0
-    B.set_push_variant(RECORD)
-    assert B.push_variant == RECORD
+    B.set_push_variant(pv)
+    assert B.push_variant == pv
     for mode in ("graph", "eager"):
         B.run(mode)
         for e in range(len(evs)):
@@ -68,11 +71,12 @@ def test_record_push_fp64_matches_oracle(integrator):
                 assert np.minimum(d, n - d).max() < 1e-10, (mode, e, k)
 
 
-def test_record_push_fp32_matches_oracle():
+@pytest.mark.parametrize("pv", [RECORD, SPLIT])
+def test_record_push_fp32_matches_oracle(pv):
     evs, pps = small_events(1, tol=1e-14)
     B = G.Batch(evs, pps)
     B.init()
-    B.set_push_variant(RECORD)
+    B.set_push_variant(pv)
     B.run("graph")
     for e in range(len(evs)):
         want, P, st = oracle_event(evs[e], pps[e], 1e-14)
