@@ -450,12 +450,13 @@ glasma_status glasma_batch_tune(glasma_batch* b, int32_t steps, int32_t* chosen,
  * each step also writes, for every cell a particle occupies (cells stamped by the previous
  * push; every cell at the particles' first step), the pieces of the site-centred fields it
  * computes anyway, and the push reads that one contiguous record; the pushes and field
- * launches then stay on one stream (glasma_batch_set_push_stream has no effect).  Same
- * physics (results equal to rounding: FP64 runs agree with the oracle to 1e-10 in every
- * variant).  Events with sub-steps or the cloud-in-cell gather always use a push of their
- * own.  glasma_batch_tune also times the three, each with the field launches of its
- * iterations, over `steps` iterations after the particles of every event are formed, and
- * keeps the fastest. */
+ * launches then stay on one stream (glasma_batch_set_push_stream has no effect).  3, the
+ * split push: a force kernel gathers the fields and stores the six Q-contracted forces of
+ * each particle, a move kernel kicks, drifts and rotates from them.  Same physics (results
+ * equal to rounding: FP64 runs agree with the oracle to 1e-10 in every variant).  Events
+ * with sub-steps or the cloud-in-cell gather always use a push of their own.
+ * glasma_batch_tune also times them, each with the field launches of its iterations, over
+ * `steps` iterations after the particles of every event are formed, and keeps the fastest. */
 int32_t glasma_push_variants(void);
 int32_t glasma_batch_push_variant(const glasma_batch* b);
 glasma_status glasma_batch_set_push_variant(glasma_batch* b, int32_t variant);
