@@ -58,7 +58,7 @@ void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out) {
 //   3: split into a force kernel and a move kernel (PUSH_VARIANT_SPLIT)
 int push_variants() { return 4; }
 #ifndef GLASMA_SPLIT_FORCE_MINB
-#define GLASMA_SPLIT_FORCE_MINB 4
+#define GLASMA_SPLIT_FORCE_MINB 3
 #endif
 #ifndef GLASMA_SPLIT_MOVE_MINB
 #define GLASMA_SPLIT_MOVE_MINB 4
