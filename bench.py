@@ -477,7 +477,8 @@ def run_ours(args, ws, rank, local):
                        "field_tile": f"{tile[0]}x{tile[1]}, {tile[2]} CTAs/SM " + ("(fixed)" if args.field_variant >= 0 else "(autotuned)"),
                        "push_kernel": {0: "fields through L1 (128-thread blocks, 3 per SM)",
                                        1: "fields staged in shared memory (32-thread blocks)",
-                                       2: "gather records written by the field launch (128-thread blocks, 4 per SM)"}
+                                       2: "gather records written by the field launch (128-thread blocks, 4 per SM)",
+                                       3: "split: gather + contracted forces (3 blocks per SM), then the move (4 per SM)"}
                        .get(B.push_variant, "?")
                                       + (" (fixed)" if args.field_variant >= 0 else " (autotuned)"),
                        "tile_tuning_ms_per_8_steps": ({f"{a}x{b}/{c}": round(t, 3) for (a, b, c), t in zip(shapes, tile_ms)}
@@ -887,11 +888,16 @@ def run_scans(args, ws, rank, local):
 
 
 # ---------------------------------------------------------------- jets at 1024^2
+JETS_SORT_EVERY = 16  # counting sort of the partons by cell, every 16 steps
+
+
 def run_jets(args, ws, rank, local):
     """Jets: 4 MV events of 1024^2 (L = 10 fm, g2mu = 2 GeV, m = 0.2 GeV, 10 sheets), each
     probed by 1M massless partons along +x in three ensembles of |p_x| = 2, 5, 10 GeV
     (333,334 / 333,333 / 333,333), formed at 0.3 fm/c, FP32 (FP64 sums) to 1 fm/c: 819
-    coupled steps per event, the partons pushed from step 246.  A step is the whole job
+    coupled steps per event, the partons pushed from step 246 and sorted by cell every 16
+    steps (a field buffer is larger than L2 here; sorted, neighbouring partons share the
+    field lines of their gathers).  A step is the whole job
     (all 4 events from their initial states, uploaded untimed); value = site-updates/s,
     particle-steps/s beside it; q^_y, q^_z at tau = 0.5 fm/c and their peak."""
     import torch
@@ -910,7 +916,7 @@ def run_jets(args, ws, rank, local):
         g.init()
         states.append(g.export_state())
     g = G.Glasma(n, L, precision=G.GLASMA_FP32, tau_end_fm=1.0, seed=4 << 32, reunit_every=64, stream=stream)
-    cs = [G.CPIC(g, cnt, 0.0, 0.3, p_min_GeV=p, p_max_GeV=p, init_kind=1,
+    cs = [G.CPIC(g, cnt, 0.0, 0.3, p_min_GeV=p, p_max_GeV=p, init_kind=1, bin_every=JETS_SORT_EVERY,
                  seed=((4 << 32) + 7919 * (k + 1) + 1000 * rank) ^ 0x5A5A5A5A5A5A5A5A)
           for k, (p, cnt) in enumerate(zip((2.0, 5.0, 10.0), counts))]
 
@@ -973,6 +979,7 @@ def run_jets(args, ws, rank, local):
             "particle_steps_per_s": ps * ws / (ms / 1000.0),
             "config": {"workload": "4 MV events of 1024^2 (L=10 fm, g2mu=2 GeV), 1M massless partons each along +x, "
                                    "|p_x| in {2,5,10} GeV by thirds, tau_form=0.3 fm/c, FP32 to 1 fm/c (819 steps)",
+                       "sort_every": JETS_SORT_EVERY,
                        "l2": "inputs larger than L2 (235 MB per FP32 field buffer, 60 MB of partons per event)"},
             "site_updates_per_step": su, "particle_steps_per_step": ps,
             "roofline": {"bound": "hbm", "achieved": field_bw, "peak": peak, "unit": "GB/s", "frac": field_bw / peak,

@@ -100,15 +100,21 @@ cudaError_t launch_push_batched(int prec, int v, const void* args, const void* i
     return prec ? push_batched_impl<float>(v, args, items, n_items, st)
                 : push_batched_impl<double>(v, args, items, n_items, st);
 }
+// The push waits on scattered field loads (long-scoreboard stalls), so resident warps
+// decide its speed.  The FP32 push of the default path fits 164 registers at 3 blocks of
+// 128 threads per SM (12 warps; 256-thread blocks at 172 registers leave 8): 1M partons on
+// 1024^2, sorted by cell, 328 instead of 414 us per step.  The FP32 sub-cycled / cloud-in-
+// cell push at 3 such blocks spills 160 B and still gains (106.6 against 109.3 ms for 409
+// steps of 200k quarks on 512^2); 4 blocks (128 registers) lose.  FP64 stays at 8 warps.
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st) {
     if (a.np <= 0) return cudaSuccess;
     const int nb = (a.np + 255) / 256;
     if (a.nsub > 1 || a.interp) {
-        if (prec) k_push<float, true><<<nb, 256, 0, st>>>(push_args<float>(a, P));
-        else k_push<double, true><<<nb, 256, 0, st>>>(push_args<double>(a, P));
+        if (prec) k_push<float, true, 128, 3><<<(a.np + 127) / 128, 128, 0, st>>>(push_args<float>(a, P));
+        else k_push<double, true, 256, 1><<<nb, 256, 0, st>>>(push_args<double>(a, P));
     } else {
-        if (prec) k_push<float><<<nb, 256, 0, st>>>(push_args<float>(a, P));
-        else k_push<double><<<nb, 256, 0, st>>>(push_args<double>(a, P));
+        if (prec) k_push<float, false, 128, 3><<<(a.np + 127) / 128, 128, 0, st>>>(push_args<float>(a, P));
+        else k_push<double, false, 256, 1><<<nb, 256, 0, st>>>(push_args<double>(a, P));
     }
     return cudaGetLastError();
 }

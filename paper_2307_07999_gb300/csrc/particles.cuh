@@ -607,8 +607,9 @@ DEV void block_acc4(float tx, float ty, float tz, float tc, double* acc) {
     }
 }
 
-template <class T, bool SUB = false>
-__global__ void __launch_bounds__(256) k_push(PushArgs<T> A) {
+// one event's push, NT threads per block and at least MINB blocks per SM (see launch_push)
+template <class T, bool SUB, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_push(PushArgs<T> A) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
     if (j < A.np) push_one<T, false, SUB>(A, j, sx, sy, sz, sc);

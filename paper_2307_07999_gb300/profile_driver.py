@@ -2,6 +2,8 @@
 
   python -m paper_2307_07999_gb300.profile_driver field 512          # 4 FP32 field steps on 512^2
   python -m paper_2307_07999_gb300.profile_driver push 512 100000    # + a 100k-particle push
+  python -m paper_2307_07999_gb300.profile_driver jets 1024 1000000 16   # 40 coupled steps of 1M
+    massless partons (|p_x| = 5 GeV, formed at tau = 0) sorted by cell every 16 steps
   python -m paper_2307_07999_gb300.profile_driver batch              # one graph run of the 64-event batch
   python -m paper_2307_07999_gb300.profile_driver batch8             # 8 events of 384^2, 10k charm each
     (both batch workloads tune the field tile shape first: 8 variants x 5 field launches;
@@ -46,6 +48,16 @@ def main(argv):
         net.fit_scales(X, T)
         net.train(X, T, epochs=2, batch=16384, lr=2e-3)
         init_warm(Glasma(n, 10.0, precision=1, tau_end_fm=1.0, seed=3), net)
+        torch.cuda.synchronize()
+        print("ok")
+        return
+    if what == "jets":
+        g = Glasma(n, 10.0, precision=1, tau_end_fm=1.0, seed=3, reunit_every=64)
+        g.init()
+        c = CPIC(g, int(argv[3]) if len(argv) > 3 else 1000000, 0.0, 0.0, p_min_GeV=5.0, p_max_GeV=5.0,
+                 init_kind=1, bin_every=int(argv[4]) if len(argv) > 4 else 16, seed=4)
+        c.init()
+        c.push(40)
         torch.cuda.synchronize()
         print("ok")
         return
