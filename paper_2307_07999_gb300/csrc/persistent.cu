@@ -2,10 +2,13 @@
 // batch through its whole evolution (the coupled field + particle steps of
 // Sec. 1 of arXiv:2307.07999 for all events of the Sec. 2 event average).
 //
-// Phase p hands out, through an atomic work counter, the field tiles of
-// iteration p and the particle blocks of iteration p-1.  The three rotating
-// field buffers keep the two apart: iteration p reads buf[p%3] and writes
-// buf[(p+1)%3]; the push of iteration p-1 reads buf[(p-1)%3] and buf[p%3].
+// Phase p runs the field tiles of iteration p and the particle blocks of
+// iteration p-1.  The tiles are dealt out statically (CTA b takes tiles b,
+// b + grid, ...: equal shares, no atomic per tile); then each CTA takes particle
+// blocks from an atomic work counter, so the CTAs that finish their tiles first
+// push while the others still step fields.  The three rotating field buffers keep
+// the two apart: iteration p reads buf[p%3] and writes buf[(p+1)%3]; the push of
+// iteration p-1 reads buf[(p-1)%3] and buf[p%3].
 // Phases are separated by a grid barrier whose wait is bounded: when it runs out
 // the kernel raises an error word and returns, and the host reports
 // GLASMA_ERR_TIMEOUT.  Field and particle loads go through L2 (ld.global.cg)
@@ -39,8 +42,10 @@ template <class T> struct PersArgs {
     unsigned long long spin_limit;
 };
 
+// Three CTAs of 128 threads per SM (168 registers, 12 warps): 482 ms for the 64-event
+// batch against 552 at two CTAs (255 registers, 8 warps).
 #ifndef GLASMA_PERS_MINB
-#define GLASMA_PERS_MINB 2
+#define GLASMA_PERS_MINB 3
 #endif
 template <class T> struct PersCfg { static constexpr int TX = 32, TY = 4, MINB = GLASMA_PERS_MINB; };
 template <> struct PersCfg<double> { static constexpr int TX = 32, TY = 4, MINB = 1; };
@@ -89,19 +94,19 @@ k_persistent(PersArgs<T> a) {
         const int actP = p >= 1 ? a.active[p - 1] : 0;    // events pushing at iteration p-1
         const int nt = actF ? a.tiles_upto[actF] : 0;
         const int npi = actP ? a.pitems_upto[actP] : 0;
-        const int total = nt + npi;
+        for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+            const TileItem ti = a.tiles[i];
+            field_tile<T, TX, TY, true>(a.sargs[(size_t)p * a.E + ti.ev], ti.x0, ti.y0, smem);
+            __syncthreads();
+        }
         for (;;) {
             if (tid == 0) s_item = atomicAdd(a.work + p, 1);
             __syncthreads();
             const int i = s_item;
             __syncthreads();
-            if (i >= total) break;
-            if (i < nt) {
-                const TileItem ti = a.tiles[i];
-                field_tile<T, TX, TY, true>(a.sargs[(size_t)p * a.E + ti.ev], ti.x0, ti.y0, smem);
-                __syncthreads();
-            } else {
-                const PushItem it = a.pitems[i - nt];
+            if (i >= npi) break;
+            {
+                const PushItem it = a.pitems[i];
                 const PushArgs<T>& A = a.pargs[(size_t)(p - 1) * a.E + it.ev];
                 if (A.acc != nullptr) {
                     double sx = 0.0, sy = 0.0, sz = 0.0, sc = 0.0;

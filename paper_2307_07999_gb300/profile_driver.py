@@ -8,7 +8,9 @@
   python -m paper_2307_07999_gb300.profile_driver batch8             # 8 events of 384^2, 10k charm each
     (both batch workloads tune the field tile shape first: 8 variants x 5 field launches;
      an argument v=<k> sets field tile variant k instead, without tuning, and p=<k> the
-     batched push kernel k, e.g. p=2 for the record push)
+     batched push kernel k, e.g. p=2 for the record push; m=<mode> runs the batch in that
+     mode (graph, eager, per_event, persistent) and n=<count> gives every event that many
+     particles)
   python -m paper_2307_07999_gb300.profile_driver ic 1024            # tau = 0+ solve: cold, then warm start
   python -m paper_2307_07999_gb300.profile_driver corr 512           # 4 FP32 field steps with both correlators
 """
@@ -23,7 +25,10 @@ from . import workloads as W
 def main(argv):
     what = argv[1] if len(argv) > 1 else "field"
     if what in ("batch", "batch8"):
-        evs, pps = W.batched_uneven() if what == "batch" else W.batched_uneven(n_events=8, sizes=(384,))
+        opt = {a.split("=")[0]: a.split("=")[1] for a in argv[2:] if "=" in a}
+        npart = int(opt.get("n", 10000))
+        evs, pps = (W.batched_uneven(n_particles=npart) if what == "batch"
+                    else W.batched_uneven(n_events=8, sizes=(384,), n_particles=npart))
         B = Batch(evs, pps)
         B.init()
         fixed = [a for a in argv[2:] if a.startswith("v=")]
@@ -34,7 +39,7 @@ def main(argv):
         push = [a for a in argv[2:] if a.startswith("p=")]
         if push:
             B.set_push_variant(int(push[0][2:]))
-        B.run("graph")
+        B.run(opt.get("m", "graph"))
         torch.cuda.synchronize()
         print("ok")
         return
