@@ -481,6 +481,10 @@ def run_ours(args, ws, rank, local):
                                        3: "split: gather + contracted forces (3 blocks per SM), then the move (4 per SM)"}
                        .get(B.push_variant, "?")
                                       + (" (fixed)" if args.field_variant >= 0 else " (autotuned)"),
+                       **({"persistent_kernel": "one cooperative launch: 32x4 field tiles dealt out statically, "
+                                                "particle blocks through an atomic counter, 3 CTAs/SM; the field "
+                                                "tile and push kernel above are the graph path's"}
+                          if mode == "persistent" else {}),
                        "tile_tuning_ms_per_8_steps": ({f"{a}x{b}/{c}": round(t, 3) for (a, b, c), t in zip(shapes, tile_ms)}
                                                       if args.field_variant < 0 else None),
                        "site_updates_per_step": su,
