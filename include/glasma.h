@@ -221,10 +221,15 @@ glasma_status cpic_push(cpic_ctx* c, int32_t n_steps);
 
 /* Coupled step for several ensembles in the same event (Sec. 2: charm and beauty quarks,
  * or jets of several momenta, probing one Glasma): n_steps x (one field step; then the
- * push of cs[0], cs[1], ... in that order, each as in cpic_push).  cs: host array of
- * n_ctx >= 1 distinct ensembles, all created on the same field context; each ensemble
- * keeps its own mass, formation step, integrator and broadening table.  A bad list is
- * rejected with GLASMA_ERR_INVALID before any work is enqueued.  Enqueue only. */
+ * push of every ensemble, each as in cpic_push; then the sorts that are due).  The
+ * ensembles with one particle step per field step and the nearest-grid-point gather are
+ * pushed together, up to eight per launch, their 128-particle blocks interleaved so that
+ * ensembles sorted by cell read the same field lines once; the others are pushed alone.
+ * Each ensemble's particles come out exactly as when it is pushed alone (its table up to
+ * the order of the FP64 block sums).  cs: host array of n_ctx >= 1 distinct ensembles, all
+ * created on the same field context; each ensemble keeps its own mass, formation step,
+ * integrator and broadening table.  A bad list is rejected with GLASMA_ERR_INVALID before
+ * any work is enqueued.  Enqueue only. */
 glasma_status cpic_push_many(cpic_ctx* const* cs, int32_t n_ctx, int32_t n_steps);
 
 /* Broadening table (Sec. 2, "Quantifying the effect of Glasma": dp_i^2(tau) =

@@ -386,9 +386,8 @@ extern "C" glasma_status cpic_get_particles(cpic_ctx* c, double* x, double* y, d
 }
 
 // the push of ensemble c from step n (fields fo) to n+1 (fields in the current buffer)
-static glasma_status push_ensemble(cpic_ctx* c, int n, const void* fo) {
-    glasma_ctx* g = c->g;
-    if (n < c->first_step || c->np == 0) return GLASMA_OK;
+static PushHost push_host(const cpic_ctx* c, int n, const void* fo) {
+    const glasma_ctx* g = c->g;
     PushHost a{};
     a.fo = fo;
     a.fn = g->buf[g->cur];
@@ -397,7 +396,15 @@ static glasma_status push_ensemble(cpic_ctx* c, int n, const void* fo) {
     push_coeffs(a, n, g->dtau, g->p.expanding, c->p.integrator, c->p.substeps, c->p.interp);
     a.mass = c->mass;
     a.acc = c->acc + 4 * (size_t)(n + 1);
-    CK(launch_push(g->prec, a, c->P[c->pcur], g->st));
+    return a;
+}
+static bool pushed_at(const cpic_ctx* c, int n) { return n >= c->first_step && c->np > 0; }
+// ensembles that can share a launch: the default kernel (one particle step per field step,
+// nearest-grid-point gather)
+static bool packable(const cpic_ctx* c) { return c->p.substeps <= 1 && c->p.interp == 0; }
+// the counting sort of ensemble c by cell, when it is due after a push
+static glasma_status sort_if_due(cpic_ctx* c) {
+    glasma_ctx* g = c->g;
     if (c->p.bin_every > 0 && ++c->since_sort >= c->p.bin_every) {
         int* cnt = c->sort_ws;
         int* start = cnt + g->ns;
@@ -425,9 +432,32 @@ extern "C" glasma_status cpic_push_many(cpic_ctx* const* cs, int32_t n_ctx, int3
         const void* fo = g->buf[g->cur];
         glasma_status s = one_field_step(g);
         if (s != GLASMA_OK) return s;
+        // the ensembles on the default kernel share launches (blocks interleaved: each
+        // sorted by cell, they gather from the same field lines); the others go alone
+        PushHost pa[PUSH_PACK_MAX];
+        const PartHost* pp[PUSH_PACK_MAX];
+        int np = 0;
+        const auto flush = [&]() -> glasma_status {
+            if (np == 1) CK(launch_push(g->prec, pa[0], *pp[0], g->st));
+            else if (np > 1) CK(launch_push_pack(g->prec, pa, pp, np, g->st));
+            np = 0;
+            return GLASMA_OK;
+        };
         for (int i = 0; i < n_ctx; i++) {
-            s = push_ensemble(cs[i], n, fo);
-            if (s != GLASMA_OK) return s;
+            cpic_ctx* c = cs[i];
+            if (!pushed_at(c, n)) continue;
+            if (!packable(c)) {
+                CK(launch_push(g->prec, push_host(c, n, fo), c->P[c->pcur], g->st));
+                continue;
+            }
+            pa[np] = push_host(c, n, fo);
+            pp[np] = &c->P[c->pcur];
+            if (++np == PUSH_PACK_MAX && (s = flush()) != GLASMA_OK) return s;
+        }
+        if ((s = flush()) != GLASMA_OK) return s;
+        for (int i = 0; i < n_ctx; i++) {
+            if (!pushed_at(cs[i], n)) continue;
+            if ((s = sort_if_due(cs[i])) != GLASMA_OK) return s;
         }
     }
     return GLASMA_OK;

@@ -105,6 +105,9 @@ inline void push_coeffs(PushHost& a, int step, double dtau, int expanding, int i
     a.interp = interp;
 }
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st);
+// up to PUSH_PACK_MAX ensembles of one event (no sub-steps, nearest grid point) in one launch
+constexpr int PUSH_PACK_MAX = 8;
+cudaError_t launch_push_pack(int prec, const PushHost* a, const PartHost* const* P, int n, cudaStream_t st);
 // batched push: args[n_ev] (acc == nullptr: event idle this step), items {ev, j0} of 256 particles
 size_t push_args_size(int prec);
 void pack_push_args(int prec, const PushHost& a, const PartHost& P, void* out);

@@ -1,6 +1,9 @@
 // Particle kernels: CPIC push with the fused broadening reduction, counting sort
 // by cell, Philox initial state (Sec. 1 "Probes in Glasma" and Sec. 2 of
 // arXiv:2307.07999), host-layout conversion and the Casimir monitor.
+#include <algorithm>
+#include <type_traits>
+
 #include "ic.cuh"
 #include "internal.h"
 #include "particles.cuh"
@@ -117,6 +120,27 @@ cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStre
         else k_push<double, false, 256, 1><<<nb, 256, 0, st>>>(push_args<double>(a, P));
     }
     return cudaGetLastError();
+}
+
+// Ensembles of one event pushed together (default path, no sub-steps, nearest grid
+// point): one launch of 128-thread blocks, 3 per SM, the ensembles' blocks interleaved.
+template <class T>
+static cudaError_t push_pack_impl(const PushHost* a, const PartHost* const* P, int n, cudaStream_t st) {
+    PushPack<T> pk;
+    int nbmax = 0;
+    for (int i = 0; i < n; i++) {
+        pk.a[i] = push_args<T>(a[i], *P[i]);
+        nbmax = std::max(nbmax, (a[i].np + 127) / 128);
+    }
+    pk.n = n;
+    if (nbmax == 0) return cudaSuccess;
+    if constexpr (std::is_same<T, float>::value) k_push_pack<T, 128, 3><<<nbmax * n, 128, 0, st>>>(pk);
+    else k_push_pack<T, 128, 2><<<nbmax * n, 128, 0, st>>>(pk);
+    return cudaGetLastError();
+}
+cudaError_t launch_push_pack(int prec, const PushHost* a, const PartHost* const* P, int n, cudaStream_t st) {
+    if (n < 1 || n > PUSH_PACK) return cudaErrorInvalidValue;
+    return prec ? push_pack_impl<float>(a, P, n, st) : push_pack_impl<double>(a, P, n, st);
 }
 
 __global__ void k_cell_count(const int* __restrict__ cell, int np, int* __restrict__ count) {

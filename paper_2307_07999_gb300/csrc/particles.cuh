@@ -616,6 +616,26 @@ __global__ void __launch_bounds__(NT, MINB) k_push(PushArgs<T> A) {
     block_acc4(sx, sy, sz, sc, A.acc);
 }
 
+// Several ensembles of one event in one launch: block b pushes the particles
+// [(b / n) NT, (b / n + 1) NT) of ensemble b % n, so the ensembles' blocks interleave.
+// Each ensemble sorted by cell, blocks at the same position gather from neighbouring
+// cells, and the field lines they read come from DRAM once for all the ensembles.
+constexpr int PUSH_PACK = 8;
+template <class T> struct PushPack {
+    PushArgs<T> a[PUSH_PACK];
+    int n;
+};
+template <class T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_push_pack(const __grid_constant__ PushPack<T> P) {
+    const int e = (int)(blockIdx.x % (unsigned)P.n), j0 = (int)(blockIdx.x / (unsigned)P.n) * NT;
+    const PushArgs<T>& A = P.a[e];
+    if (j0 >= A.np) return;  // uniform over the block: this ensemble has fewer particles
+    const int j = j0 + (int)threadIdx.x;
+    T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
+    if (j < A.np) push_one<T>(A, j, sx, sy, sz, sc);
+    block_acc4(sx, sy, sz, sc, A.acc);
+}
+
 // batched over events: one item per 256 particles of an event, pushed by 256 / NT blocks
 // of NT threads; args[ev] of this step (acc == nullptr marks an event whose particles
 // are not pushed at this step)
