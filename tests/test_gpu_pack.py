@@ -23,7 +23,8 @@ SPECS = [
     (700, 1.5, 0.03, (0.0, 3.0), 0, 0, 1, 3, 0),
     (90, 4.7, 0.05, (1.0, 4.0), 0, 1, 1, 0, 0),
     (400, 0.0, 0.0, (2.0, 2.0), 1, 0, 1, 0, 0),
-    (333, 1.5, 0.05, (0.0, 3.0), 0, 0, 1, 1, 0),    # the ninth on the default kernel: a second launch
+    (333, 1.5, 0.05, (0.0, 3.0), 0, 0, 1, 1, 0),
+    (64, 4.7, 0.0, (0.0, 1.0), 0, 1, 1, 0, 0),      # the ninth non-empty one on the default kernel: a second launch
     (150, 1.5, 0.05, (0.0, 3.0), 0, 0, 2, 0, 0),    # sub-stepped: pushed alone
     (150, 1.5, 0.05, (0.0, 3.0), 0, 0, 1, 0, 1),    # cloud in cell: pushed alone
 ]
