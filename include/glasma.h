@@ -167,11 +167,13 @@ void glasma_destroy(glasma_ctx* g);
  * reserved): no context, no workspace.  The paper has no counterpart; this is
  * a deployment aid.
  *   fields: device pointer to one field buffer in the library's plane layout
- *           (56 planes of n*n reals of the given precision, site s = x + n*y:
+ *           (56 state planes of n*n reals of the given precision, site s = x + n*y:
  *           U_x rows 0-1 as 12 planes (entry-major, re then im), U_y likewise,
  *           E_x^a, E_y^a, phi^a, pi^a as 8 planes each; the planes are grouped
  *           by eight, interleaved per site: plane p of site s is element
- *           ((p / 8) * n*n + s) * 8 + p % 8), read only, 16-byte aligned.
+ *           ((p / 8) * n*n + s) * 8 + p % 8), read only, 16-byte aligned.  The
+ *           library's own buffers carry an eighth group (planes 56-63: the
+ *           plaquettes a field step leaves for the push), which is not read here.
  *   tau: tau in lattice units (divides E and D phi in the expanding case).
  *   out: host double[8], as glasma_diagnostics.
  *   expanding: 1 the Milne evolution (tau > 0 required), 0 the static box.

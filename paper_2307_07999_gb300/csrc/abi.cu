@@ -504,7 +504,7 @@ struct CkptHeader {
 static void ckpt_header(CkptHeader& h, const char* magic, const glasma_ctx* g) {
     memset(&h, 0, sizeof(h));
     memcpy(h.magic, magic, 8);
-    h.version = 1;
+    h.version = 2;  // 2: field buffers of 64 planes (the plaquette group added)
     h.prec = g->prec;
     h.n = g->n;
     h.dtau = g->dtau;

@@ -263,6 +263,9 @@ static glasma_status build_tables(glasma_batch* b) {
             void* dst = x.buf[(k + 1) % 3];
             const int reunit = reunit_code(x.gp.reunit_every, s);
             StepHost st = step_coeffs(src, dst, x.n, s, x.dtau, 1, reunit);
+            // the batched pushes form the clover themselves (the batched field kernels
+            // store no plaquettes; the per-event mode's one-event kernels do)
+            st.plaq = nullptr;
             // gather records (used by the REC field kernels of the record push): at the
             // particles' first step every cell gets one, later the cells stamped by the push
             st.rec = x.rec;

@@ -2,12 +2,15 @@
 // Glasma leapfrog (Sec. 1 "Glasma" of arXiv:2307.07999: lattice gauge links and
 // plaquettes in Milne coordinates).
 //
-// One field buffer holds 56 planes of n*n reals (site s = x + n*y, x fastest):
+// One field buffer holds 64 planes of n*n reals (site s = x + n*y, x fastest):
 //   planes  0..11 : U_x rows 0,1 (re, im interleaved per entry)
 //   planes 12..23 : U_y rows 0,1
 //   planes 24..31 : E_x^a        planes 32..39 : E_y^a
 //   planes 40..47 : phi^a        planes 48..55 : pi^a
-// The planes come in 7 groups of eight, each group interleaved per site: plane p of
+//   planes 56..63 : F^a = ImTL of the plaquette based at the site, of the links of this
+//                   buffer: not state; written by the one-event field step that reads the
+//                   buffer (it forms them anyway for the staples) for the push of that step
+// The planes come in 8 groups of eight, each group interleaved per site: plane p of
 // site s sits at ((p / 8) * n*n + s) * 8 + p % 8.  A group of one site is one 32-byte
 // sector in FP32, loaded as two 16-byte vectors: a warp of consecutive sites reads
 // contiguous memory, and a particle's scattered gather touches few sectors (both
@@ -18,7 +21,7 @@
 
 namespace glasma {
 
-enum { P_UX = 0, P_UY = 12, P_EX = 24, P_EY = 32, P_PHI = 40, P_PI = 48, N_PLANES = 56 };
+enum { P_UX = 0, P_UY = 12, P_EX = 24, P_EY = 32, P_PHI = 40, P_PI = 48, P_F = 56, N_PLANES = 64 };
 
 template <class T> struct StepArgs {
     const T* src;  // state at step n
@@ -30,6 +33,8 @@ template <class T> struct StepArgs {
     T ue;          // link drift:  dtau / tau_{n+1/2} (or dtau)
     T pe;          // phi drift:   dtau * tau_{n+1/2} (or dtau)
     int reunit;    // re-projection of the new links: 1 FP64 Gram-Schmidt, 2 FP32 renormalisation, 0 none
+    T* plaq;       // the source buffer again, whose group P_F receives ImTL of each site's
+                   // plaquette (kernels compiled with PLAQ: the one-event step)
     // gather records (kernels compiled with REC only): for every cell whose occupancy
     // stamp equals `epoch` (every cell if all_rec), the pieces of the site-centred fields
     // that the push of this step gathers there (layout below)
@@ -295,9 +300,10 @@ template <class T> DEV void rec_store_link(bool p, T* rec, size_t cell, int slot
 }
 
 // One tile [x0, x0+TX) x [y0, y0+TY) of one step: kick at tau_n, drift with tau_{n+1/2}.
-// REC: also the gather records of the occupied cells (StepArgs::rec); the field
-// arithmetic is the same with and without them.
-template <class T, int TX, int TY, bool CG = false, bool REC = false>
+// REC: also the gather records of the occupied cells (StepArgs::rec); PLAQ: also the
+// plaquettes into the source buffer's last group (StepArgs::plaq, the one-event step,
+// whose push reads them); the field arithmetic is the same with and without either.
+template <class T, int TX, int TY, bool CG = false, bool REC = false, bool PLAQ = false>
 DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_raw) {
     using G = RecTile<T, TX, TY>;
     constexpr int HX = G::HX, HS = G::HS, FX = G::FX, FS = G::FS;
@@ -432,6 +438,7 @@ DEV void field_tile(const StepArgs<T>& A, int x0, int y0, unsigned char* smem_ra
     }
     {
         const Al<T> F0 = rec_alg(sF, f);
+        if constexpr (PLAQ) store_alg(A.plaq, ns, P_F, s, F0);  // for the push of this step
         if constexpr (REC) {
             // the same updates, one field at a time, each followed by its time average
             // (E_{n-1/2} + E_{n+1/2}) / 2 formed exactly as the unfused gather forms it

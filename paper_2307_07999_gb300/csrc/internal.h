@@ -9,7 +9,7 @@ struct glasma_mlp;  // the warm-start network (mlp.cu)
 
 namespace glasma {
 
-constexpr int N_FIELD_PLANES = 56;
+constexpr int N_FIELD_PLANES = 64;
 constexpr int N_PART_REAL_PLANES = 17;  // ox oy eta p0x p0y p0z dpx dpy peta Q[8]
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -21,6 +21,7 @@ struct StepHost {
     int n;
     double tb, tp, dtau, ue, pe;
     int reunit;
+    void* plaq;       // the buffer receiving the plaquettes of src's links (src itself)
     void* rec;        // gather records written by the REC kernels (null otherwise)
     const int* occ;   // occupancy stamps they test
     int epoch;        // the step index: a cell whose stamp equals it gets a record

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(TileCfg<T>::TX * TileCfg<T>::TY, TileCfg<T>::M
 k_field_step(StepArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
-    field_tile<T, TX, TY>(A, blockIdx.x * TX, blockIdx.y * TY, smem);
+    field_tile<T, TX, TY, false, false, true>(A, blockIdx.x * TX, blockIdx.y * TY, smem);
 }
 template <class T, bool REC = false>
 __global__ void __launch_bounds__(TileCfg<T>::TX * TileCfg<T>::TY, TileCfg<T>::MINB)
@@ -35,6 +35,7 @@ k_field_step_batched(const StepArgs<T>* __restrict__ args, const TileItem* __res
 StepHost step_coeffs(const void* src, void* dst, int n, int step, double dtau, int expanding, int reunit) {
     StepHost a;
     a.src = src; a.dst = dst; a.n = n; a.dtau = dtau; a.reunit = reunit;
+    a.plaq = const_cast<void*>(src);  // the plaquettes of src's links go into src's last group
     a.rec = nullptr; a.occ = nullptr; a.epoch = step; a.all_rec = 0;
     const double tn = step * dtau, th = (step + 0.5) * dtau;
     a.tb = expanding ? tn : 1.0;
@@ -49,6 +50,7 @@ template <class T> static StepArgs<T> to_args(const StepHost& a) {
     A.src = (const T*)a.src; A.dst = (T*)a.dst; A.n = a.n;
     A.tb = (T)a.tb; A.tp = (T)a.tp; A.dtau = (T)a.dtau; A.ue = (T)a.ue; A.pe = (T)a.pe;
     A.reunit = a.reunit;
+    A.plaq = (T*)a.plaq;
     A.rec = (T*)a.rec; A.occ = a.occ; A.epoch = a.epoch; A.all_rec = a.all_rec;
     return A;
 }
@@ -81,7 +83,7 @@ template <class T> static cudaError_t set_smem() {
 template <int TX, int TY, int MINB>
 __global__ void __launch_bounds__(TX * TY, MINB) k_field_step_grid(StepArgs<float> A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    field_tile<float, TX, TY>(A, blockIdx.x * TX, blockIdx.y * TY, smem);
+    field_tile<float, TX, TY, false, false, true>(A, blockIdx.x * TX, blockIdx.y * TY, smem);
 }
 constexpr int SINGLE_TX = 16, SINGLE_TY = 8, SINGLE_MINB = 4;
 

@@ -82,8 +82,10 @@ template <> DEV double clamp_below_one<double>(double v) { return fmin(v, 0.9999
 //   phi(dx, dy)                              phi at the site (phi_n)
 //   eavg(d, dx, dy), piavg()                 (E_i(tau_{n-1/2}) + E_i(tau_{n+1/2})) / 2 on
 //                                            the link site -> site + i, pi likewise at c
-// Global source of the unfused push: the two field buffers of step n.
-template <class T, bool CG = false> struct GlobalSrc {
+//   plaq(dx, dy) (views with kPlaq)          ImTL of the plaquette based at the site
+// Global source of the unfused push: the two field buffers of step n.  PLAQ: the field
+// step of step n stored the plaquettes in fo's last group (one-event paths).
+template <class T, bool CG = false, bool PLAQ = false> struct GlobalSrc {
     static constexpr bool kRecord = false, kForce = false;
     const T* fo;
     const T* fn;
@@ -101,6 +103,10 @@ template <class T, bool CG = false> struct GlobalSrc {
         DEV M3<T> link(int d, int dx, int dy) const { return load_link<T, CG>(fo, ns, d == 0 ? P_UX : P_UY, at(dx, dy)); }
         DEV void links(int dx, int dy, M3<T>& ux, M3<T>& uy) const { load_links<T, CG>(fo, ns, at(dx, dy), ux, uy); }
         DEV Al<T> phi(int dx, int dy) const { return load_alg<T, CG>(fo, ns, P_PHI, at(dx, dy)); }
+        // ImTL of the plaquette based at the site, of the links of step n (written by the
+        // field step of step n into the buffer it reads)
+        DEV Al<T> plaq(int dx, int dy) const { return load_alg<T, CG>(fo, ns, P_F, at(dx, dy)); }
+        static constexpr bool kPlaq = PLAQ;
         DEV Al<T> eavg(int d, int dx, int dy) const { return avg(d == 0 ? P_EX : P_EY, at(dx, dy)); }
         DEV Al<T> piavg() const { return avg(P_PI, at(0, 0)); }
         DEV Al<T> avg(int p, size_t s) const {
@@ -189,6 +195,7 @@ template <class T> struct StagedSrc {
             uy = link(1, dx, dy);
         }
         DEV Al<T> phi(int dx, int dy) const { return ld(grp(dx, dy, 5)); }
+        static constexpr bool kPlaq = false;  // no plaquettes staged: the clover is formed here
         DEV Al<T> eavg(int d, int dx, int dy) const { return avg(grp(dx, dy, 3 + d, 0), grp(dx, dy, 3 + d, 1)); }
         DEV Al<T> piavg() const { return avg(grp(0, 0, 6, 0), grp(0, 0, 6, 1)); }
         DEV static Al<T> ld(const T* p) {
@@ -226,11 +233,43 @@ template <class T, class V> DEV M3<T> clover_plaquette(const V& C, int k) {
 
 // Q-contracted site-centred fields at the particle's cell for the push of step n:
 // qE = Q.(E_x, E_y, E_z), qB = Q.(B_x, B_y, B_z)
+//
+// Views with the stored plaquettes (kPlaq): the fields at c-x and c-y reach c by a
+// transport U^dag X U with the link from there to c, and Q.(U^dag X U) = (U Q U^dag).X,
+// so Q is carried to c-x and c-y once and contracted there with E, phi and the plaquette.
+// The clover leaves other than the plaquette at c are the plaquettes at c-x, c-y and
+// c-x-y carried to c (cyclic rotations of those loops): by U_x(c-x), by U_y(c-y), and by
+// V = U_x(c-x-y) U_y(c-y) (ImTL commutes with the conjugation), so Q at c-y is carried on
+// by U_x(c-x-y).  Five transports of Q replace six of fields and the twelve products of
+// the four leaves; the gather reads six sites instead of eight.
 template <class T, class V>
 DEV void gather_qf_view(const V& C, T te, const Al<T>& q, T qE[3], T qB[3]) {
+    const T half = T(0.5);
+    if constexpr (V::kPlaq) {
+        T bz;
+        {
+            const Al<T> ql = conj_alg(C.link(0, -1, 0), q);  // Q carried to c-x
+            qE[0] = half * (dot8(q, C.eavg(0, 0, 0)) + dot8(ql, C.eavg(0, -1, 0))) / te;
+            qB[1] = -half * dot8(ql, C.phi(-1, 0));
+            bz = dot8(q, C.plaq(0, 0)) + dot8(ql, C.plaq(-1, 0));
+        }
+        {
+            const Al<T> qb = conj_alg(C.link(1, 0, -1), q);  // Q carried to c-y
+            qE[1] = half * (dot8(q, C.eavg(1, 0, 0)) + dot8(qb, C.eavg(1, 0, -1))) / te;
+            qB[0] = half * dot8(qb, C.phi(0, -1));
+            bz += dot8(qb, C.plaq(0, -1));
+            bz += dot8(conj_alg(C.link(0, -1, -1), qb), C.plaq(-1, -1));  // on to c-x-y
+        }
+        qE[2] = dot8(q, C.piavg());
+        // B_y = +D_x phi / tau,  B_x = -D_y phi / tau (central differences); phi at c+x and
+        // c+y reaches c by U phi U^dag: Q.(U phi U^dag) = (U^dag Q U).phi
+        qB[1] = (qB[1] + half * dot8(transport_alg(C.link(0, 0, 0), q), C.phi(1, 0))) / te;
+        qB[0] = (qB[0] - half * dot8(transport_alg(C.link(1, 0, 0), q), C.phi(0, 1))) / te;
+        qB[2] = -T(0.25) * bz;
+        return;
+    }
     // Every field is read from the view where it is used and contracted with Q at once
     // (Q.X is linear in X), so that few 3x3 matrices are live at a time.
-    const T half = T(0.5);
     // electric: the two links touching c, time-centred, transported to c
     qE[0] = half * (dot8(q, C.eavg(0, 0, 0)) + dot8(q, transport_alg(C.link(0, -1, 0), C.eavg(0, -1, 0)))) / te;
     qE[1] = half * (dot8(q, C.eavg(1, 0, 0)) + dot8(q, transport_alg(C.link(1, 0, -1), C.eavg(1, 0, -1)))) / te;
@@ -538,10 +577,10 @@ DEV void push_one_src(const PushArgs<T>& A, const S& F, int j, T& sx, T& sy, T& 
     sc = T(1);
 }
 
-template <class T, bool CG = false, bool SUB = false>
+template <class T, bool CG = false, bool SUB = false, bool PLAQ = false>
 DEV void push_one(const PushArgs<T>& A, int j, T& sx, T& sy, T& sz, T& sc) {
-    GlobalSrc<T, CG> F{A.fo, A.fn, A.n, (size_t)A.n * A.n};
-    push_one_src<T, GlobalSrc<T, CG>, CG, SUB>(A, F, j, sx, sy, sz, sc);
+    GlobalSrc<T, CG, PLAQ> F{A.fo, A.fn, A.n, (size_t)A.n * A.n};
+    push_one_src<T, GlobalSrc<T, CG, PLAQ>, CG, SUB>(A, F, j, sx, sy, sz, sc);
 }
 
 // warp -> block -> one FP64 atomic per block and term (any block shape, at most 256
@@ -612,7 +651,7 @@ template <class T, bool SUB, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_push(PushArgs<T> A) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
-    if (j < A.np) push_one<T, false, SUB>(A, j, sx, sy, sz, sc);
+    if (j < A.np) push_one<T, false, SUB, true>(A, j, sx, sy, sz, sc);
     block_acc4(sx, sy, sz, sc, A.acc);
 }
 
@@ -632,7 +671,7 @@ __global__ void __launch_bounds__(NT, MINB) k_push_pack(const __grid_constant__ 
     if (j0 >= A.np) return;  // uniform over the block: this ensemble has fewer particles
     const int j = j0 + (int)threadIdx.x;
     T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
-    if (j < A.np) push_one<T>(A, j, sx, sy, sz, sc);
+    if (j < A.np) push_one<T, false, false, true>(A, j, sx, sy, sz, sc);
     block_acc4(sx, sy, sz, sc, A.acc);
 }
 

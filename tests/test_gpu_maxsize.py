@@ -1,15 +1,16 @@
 """Large lattices, past 2^31 field elements (the plane offsets and the Fourier transforms
 of the initial condition need 64-bit sizes), through the C ABI.
 
-- 8192^2 in FP32 (56 planes x 67M sites = 3.8e9 reals per buffer): MV initial condition
+- 8192^2 in FP32 (64 planes x 67M sites = 4.3e9 reals per buffer): MV initial condition
   (FP64 Newton solve, 64-bit cuFFT plans), 12 field steps, monitors: every link solved,
   Gauss law and unitarity at FP32 rounding, finite energies.
-- Translation invariance at 6200^2 (2.15e9 reals per buffer): a state that repeats a
+- Translation invariance at 6200^2 (2.46e9 reals per buffer, 2.15e9 of them state): a state that repeats a
   10 x 10 random state 620 times in each direction evolves into the repetition of the
   oracle's evolution of the 10 x 10 state (FP32 2e-5 on sites sampled across the whole
   lattice, ragged tile edges and the periodic seams included).  The repeated state is
   written into a checkpoint blob of the large context (its body is the field buffer in
-  the library's documented layout: 7 groups of 8 planes, interleaved per site); the result
+  the library's documented layout: 8 groups of 8 planes, interleaved per site, the last
+  holding the plaquettes the next step rewrites); the result
   is read back in the canonical layout and compared with the oracle's small state.
 """
 import ctypes as C
@@ -47,9 +48,9 @@ def test_8192_fp32_initial_condition_and_steps():
 
 
 def field_body(blob, n, nbytes):
-    """The field buffer (7 groups, n, n, 8 FP32 reals) of a checkpoint blob."""
+    """The field buffer (8 groups, n, n, 8 FP32 reals) of a checkpoint blob."""
     hdr = blob.size - nbytes
-    return hdr, blob[hdr:hdr + 56 * n * n * 4].view(np.float32).reshape(7, n, n, 8)
+    return hdr, blob[hdr:hdr + 64 * n * n * 4].view(np.float32).reshape(8, n, n, 8)
 
 
 def test_6200_translation_invariance_fp32():
@@ -61,12 +62,12 @@ def test_6200_translation_invariance_fp32():
     small = random_state(p, seed=71, step=1)
     gs = G.Glasma(p, 1.0, precision=G.GLASMA_FP32, tau_end_fm=100.0)
     gs.set_state(small.U, small.E, small.phi, small.pi, small.step)
-    _, body_s = field_body(gs.export_state(), p, align(56 * p * p * 4))
+    _, body_s = field_body(gs.export_state(), p, align(64 * p * p * 4))
     gb = G.Glasma(n, 10.0, precision=G.GLASMA_FP32, tau_end_fm=100.0, seed=5)
     gb.init()  # any state at step 1: its blob carries the large context's header
     blob = gb.export_state()
-    _, body_b = field_body(blob, n, align(56 * n * n * 4))
-    for g_ in range(7):  # one group at a time keeps the host copy small
+    _, body_b = field_body(blob, n, align(64 * n * n * 4))
+    for g_ in range(7):  # the state's groups, one at a time (keeps the host copy small)
         body_b[g_] = np.tile(body_s[g_], (reps, reps, 1))
     gb.import_state(blob)
     del blob, body_b
