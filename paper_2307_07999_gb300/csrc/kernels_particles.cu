@@ -104,11 +104,12 @@ cudaError_t launch_push_batched(int prec, int v, const void* args, const void* i
                 : push_batched_impl<double>(v, args, items, n_items, st);
 }
 // The push waits on scattered field loads (long-scoreboard stalls), so resident warps
-// decide its speed.  The FP32 push of the default path fits 164 registers at 3 blocks of
-// 128 threads per SM (12 warps; 256-thread blocks at 172 registers leave 8): 1M partons on
-// 1024^2, sorted by cell, 328 instead of 414 us per step.  The FP32 sub-cycled / cloud-in-
-// cell push at 3 such blocks spills 160 B and still gains (106.6 against 109.3 ms for 409
-// steps of 200k quarks on 512^2); 4 blocks (128 registers) lose.  FP64 stays at 8 warps.
+// decide its speed.  With the stored plaquettes (no clover products) the FP32 push of the
+// default path runs 4 blocks of 128 threads per SM (128 registers, 48 B of spills, 16
+// warps): 1M sorted partons on 1024^2 in 310.5 instead of 328.3 us per coupled step at 3
+// blocks (256-thread blocks, 8 warps, before the plaquettes: 414 us).  The FP32 sub-cycled /
+// cloud-in-cell push stays at 3 blocks (168 registers): at 4 it spills 140 B and loses (87.8
+// against 71.8 ms for 409 steps of 200k quarks on 512^2).  FP64 stays at 8 warps.
 cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStream_t st) {
     if (a.np <= 0) return cudaSuccess;
     const int nb = (a.np + 255) / 256;
@@ -116,14 +117,14 @@ cudaError_t launch_push(int prec, const PushHost& a, const PartHost& P, cudaStre
         if (prec) k_push<float, true, 128, 3><<<(a.np + 127) / 128, 128, 0, st>>>(push_args<float>(a, P));
         else k_push<double, true, 256, 1><<<nb, 256, 0, st>>>(push_args<double>(a, P));
     } else {
-        if (prec) k_push<float, false, 128, 3><<<(a.np + 127) / 128, 128, 0, st>>>(push_args<float>(a, P));
+        if (prec) k_push<float, false, 128, 4><<<(a.np + 127) / 128, 128, 0, st>>>(push_args<float>(a, P));
         else k_push<double, false, 256, 1><<<nb, 256, 0, st>>>(push_args<double>(a, P));
     }
     return cudaGetLastError();
 }
 
 // Ensembles of one event pushed together (default path, no sub-steps, nearest grid
-// point): one launch of 128-thread blocks, 3 per SM, the ensembles' blocks interleaved.
+// point): one launch of 128-thread blocks, 4 per SM in FP32, the ensembles' blocks interleaved.
 template <class T>
 static cudaError_t push_pack_impl(const PushHost* a, const PartHost* const* P, int n, cudaStream_t st) {
     PushPack<T> pk;
@@ -134,7 +135,7 @@ static cudaError_t push_pack_impl(const PushHost* a, const PartHost* const* P, i
     }
     pk.n = n;
     if (nbmax == 0) return cudaSuccess;
-    if constexpr (std::is_same<T, float>::value) k_push_pack<T, 128, 3><<<nbmax * n, 128, 0, st>>>(pk);
+    if constexpr (std::is_same<T, float>::value) k_push_pack<T, 128, 4><<<nbmax * n, 128, 0, st>>>(pk);
     else k_push_pack<T, 128, 2><<<nbmax * n, 128, 0, st>>>(pk);
     return cudaGetLastError();
 }
