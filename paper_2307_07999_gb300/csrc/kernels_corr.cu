@@ -7,10 +7,10 @@
 //                                   J_i(x0) += dtau * W F_i W^dag, W <- W U_x(c) on leaving c,
 //                                   F = (E_x, E_y - B_z, E_z + B_y),
 //                                   <dp_i^2> = < (1/2) sum_a (J_i^a)^2 >_x0
-// with the site-centred fields of the particle push (time-centred E, clover B_z,
-// covariant differences of phi).  One thread per site; accumulators and Wilson lines
-// in planes of n*n (component-major), in the precision of the fields; the six sums of
-// each step reduce in FP64.
+// with the site-centred fields of the particle push (time-centred E, clover B_z from the
+// plaquettes the field step stored, covariant differences of phi).  One thread per site;
+// accumulators and Wilson lines in planes of n*n (component-major), in the precision of
+// the fields; the six sums of each step reduce in FP64.
 #include "internal.h"
 #include "particles.cuh"
 
@@ -29,14 +29,20 @@ template <class T> struct CorrArgs {
     double* acc;   // this step's row: {static x, y, z, lightlike x, y, z}
 };
 
-template <class T> __global__ void __launch_bounds__(128) k_corr_step(CorrArgs<T> A) {
+// Blocks of 128 threads; in FP32 at least 4 per SM (128 registers, 224 B of spills): the
+// step waits on its gathers and its 66 accumulator planes, so resident warps decide it (field
+// step + estimators on 1024^2: 757 us against 866 at 3 blocks and 1149 at the kernel's own
+// 180 registers, 2 blocks).  FP64 keeps its registers.
+template <class T> struct CorrMinb { static constexpr int v = 1; };
+template <> struct CorrMinb<float> { static constexpr int v = 4; };
+template <class T> __global__ void __launch_bounds__(128, CorrMinb<T>::v) k_corr_step(CorrArgs<T> A) {
     const int n = A.n;
     const size_t ns = (size_t)n * n;
     const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     double part[6] = {0, 0, 0, 0, 0, 0};
     if (s < ns) {
         const int x = (int)(s % n), y = (int)(s / n);
-        const GlobalSrc<T> F{A.fo, A.fn, n, ns};
+        const GlobalSrc<T, false, true> F{A.fo, A.fn, n, ns};  // fo holds its plaquettes (one-event step)
         {  // static: the site's own fields
             Al<T> E[3];
             site_E(F.view(x, y), A.te, E);

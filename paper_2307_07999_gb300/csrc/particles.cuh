@@ -408,13 +408,27 @@ template <class T, class V> DEV void site_fields(const V& C, T te, Al<T> E[3], A
         for (int k = 0; k < 8; k++) B[0].a[k] = -half * (fw.a[k] - bw.a[k]) / te;  // -D_y phi / tau
     }
     Al<T> acc;
+    if constexpr (V::kPlaq) {
+        // the stored plaquettes at c, c-x, c-y, c-x-y, the last three carried to c (the clover
+        // leaves, as in gather_qf_view): U^dag F U with U_x(c-x), U_y(c-y), and U_x(c-x-y)
+        // then U_y(c-y)
+        acc = C.plaq(0, 0);
+        const Al<T> t1 = transport_alg(C.link(0, -1, 0), C.plaq(-1, 0));
+        const Al<T> t3 = transport_alg(C.link(1, 0, -1), C.plaq(0, -1));
 #pragma unroll
-    for (int a = 0; a < 8; a++) acc.a[a] = T(0);
+        for (int a = 0; a < 8; a++) acc.a[a] += t1.a[a] + t3.a[a];
+        const Al<T> t2 = transport_alg(C.link(1, 0, -1), transport_alg(C.link(0, -1, -1), C.plaq(-1, -1)));
+#pragma unroll
+        for (int a = 0; a < 8; a++) acc.a[a] += t2.a[a];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 8; a++) acc.a[a] = T(0);
 #pragma unroll 1
-    for (int k = 0; k < 4; k++) {
-        const Al<T> t = im_tl(clover_plaquette<T>(C, k));
+        for (int k = 0; k < 4; k++) {
+            const Al<T> t = im_tl(clover_plaquette<T>(C, k));
 #pragma unroll
-        for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
+            for (int a = 0; a < 8; a++) acc.a[a] += t.a[a];
+        }
     }
 #pragma unroll
     for (int a = 0; a < 8; a++) B[2].a[a] = -T(0.25) * acc.a[a];
