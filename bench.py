@@ -435,7 +435,7 @@ def run_ours(args, ws, rank, local):
                 "share_of_step": share,
                 "other_kernels_ms_per_run": other_ms}
     # the whole step against the same peak, algorithmic bytes 448 per site-update and
-    # 132 per particle-step (BASELINE's count: the gather's field reads not counted)
+    # 132 per particle-step (the particle state; the gather's field reads not counted)
     whole = (BYTES_PER_SITE * su + BYTES_PER_PARTICLE * ps) / (ms / 1000.0) / 1e9
     roofline["whole_step"] = {"achieved": whole, "frac": whole / peak, "unit": "GB/s"}
     # the push's own roofline: its time per run is the step minus the field launches;

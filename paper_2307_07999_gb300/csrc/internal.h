@@ -32,8 +32,9 @@ StepHost step_coeffs(const void* src, void* dst, int n, int step, double dtau, i
 // link re-projection after the drift of step s: 1 the FP64 Gram-Schmidt (every reunit_every
 // steps), 2 the FP32 first-order renormalisation (every RENORM_EVERY steps otherwise;
 // FP32 only), 0 none
-// (measured on the 512^2 configuration: every 2 steps is 1.3 % faster on the benchmark but
-// doubles the FP32-vs-FP64 error of <dp^2> to 1.5e-5 and raises kappa's to 2.2e-4)
+// (every 2 steps: the 64-event batch of 128^2-512^2 lattices runs 1.3 % faster, but on one
+// 512^2 event with 200k quarks the FP32-vs-FP64 error of <dp^2> doubles to 1.5e-5 and
+// kappa's rises to 2.2e-4)
 constexpr int RENORM_EVERY = 1;
 inline int reunit_code(int reunit_every, int s) {
     if (reunit_every > 0 && (s + 1) % reunit_every == 0) return 1;

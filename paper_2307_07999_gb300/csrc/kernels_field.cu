@@ -78,7 +78,8 @@ template <class T> static cudaError_t set_smem() {
     return cudaSuccess;
 }
 
-// single-event FP32 step in the tile shape the batch tuner picks on the benchmark
+// single-event FP32 step in a tile shape the batch tuner picks on the 64-event batch of
+// 128^2-512^2 lattices
 // (16 x 8 sites, 4 CTAs per SM); the per-site arithmetic is that of every shape
 template <int TX, int TY, int MINB>
 __global__ void __launch_bounds__(TX * TY, MINB) k_field_step_grid(StepArgs<float> A) {
