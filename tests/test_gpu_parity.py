@@ -53,6 +53,32 @@ def test_field_steps_fp32(n):
     compare_states(g, st, 2e-5)
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_stored_plaquettes(prec, tol):
+    """The one-event field step stores, in the eighth plane group of the buffer it reads, ImTL
+    of every site's plaquette U_x(x) U_y(x+x) U_x(x+y)^dag U_y(x)^dag of that buffer's
+    links (the push of the step reads them).  A context rotates two buffers, so the buffer
+    a checkpoint exports two steps on is the one the first step read."""
+    n = 8
+    st = random_state(n, seed=414, step=3)
+    g = gpu_fields(n, prec)
+    g.set_state(st.U, st.E, st.phi, st.pi, st.step)
+    g.step(2)
+    blob = g.export_state()
+    rs = 4 if prec else 8
+    body_bytes = (64 * n * n * rs + 255) // 256 * 256
+    body = blob[blob.size - body_bytes: blob.size - body_bytes + 64 * n * n * rs]
+    F = body.view(np.float32 if prec else np.float64).reshape(8, n * n, 8)[7].astype(np.float64)
+    want = np.zeros((n * n, 8))
+    for y in range(n):
+        for x in range(n):
+            s = x + n * y
+            sx, sy = (x + 1) % n + n * y, x + n * ((y + 1) % n)
+            P = st.U[s, 0] @ st.U[sx, 1] @ st.U[sy, 0].conj().T @ st.U[s, 1].conj().T
+            want[s] = O.im_tl(P)
+    assert rel_err(F, want) < tol
+
+
 def test_reunitarisation_fp32_keeps_links_unitary():
     n = 32
     st = random_state(n, seed=7, step=3)
