@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(NT, MINB) k_push_batched(const PushArgs<T>* __
     static_assert(256 % NT == 0 && NT % 32 == 0, "push block");
     constexpr int SUB = 256 / NT;
     const PushItem it = items[blockIdx.x / SUB];
-    const PushArgs<T> A = args[it.ev];
+    const PushArgs<T>& A = args[it.ev];  // read where used: a copy held ~50 registers
     if (A.acc == nullptr) return;
     const int j = it.j0 + (int)(blockIdx.x % SUB) * NT + threadIdx.x;
     T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(NT, MINB) k_push_record(const PushArgs<T>* __r
     static_assert(256 % NT == 0 && NT % 32 == 0, "push block");
     constexpr int SUB = 256 / NT;
     const PushItem it = items[blockIdx.x / SUB];
-    const PushArgs<T> A = args[it.ev];
+    const PushArgs<T>& A = args[it.ev];  // read where used: a copy held ~50 registers
     if (A.acc == nullptr) return;
     const int j = it.j0 + (int)(blockIdx.x % SUB) * NT + threadIdx.x;
     T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(NT, MINB) k_push_move(const PushArgs<T>* __res
     static_assert(256 % NT == 0 && NT % 32 == 0, "push block");
     constexpr int SUB = 256 / NT;
     const PushItem it = items[blockIdx.x / SUB];
-    const PushArgs<T> A = args[it.ev];
+    const PushArgs<T>& A = args[it.ev];  // read where used: a copy held ~50 registers
     if (A.acc == nullptr) return;
     const int j = it.j0 + (int)(blockIdx.x % SUB) * NT + threadIdx.x;
     T sx = T(0), sy = T(0), sz = T(0), sc = T(0);
@@ -815,7 +815,7 @@ k_push_staged(const PushArgs<T>* __restrict__ args, const PushItem* __restrict__
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int SUB = 256 / PUSH_PPB;
     const PushItem it = items[blockIdx.x / SUB];
-    const PushArgs<T> A = args[it.ev];
+    const PushArgs<T>& A = args[it.ev];  // read where used: a copy held ~50 registers
     if (A.acc == nullptr) return;  // uniform over the block
     const int j = it.j0 + (int)(blockIdx.x % SUB) * PUSH_PPB + threadIdx.x;
     T* rec = reinterpret_cast<T*>(smem) + (size_t)threadIdx.x * StagedSrc<T>::STRIDE;
